@@ -1,0 +1,160 @@
+"""Pins for oracle.grid_ops (Eqs. 2.1, 2.5, 2.7, A.5, A.6), oracle.poisson
+and the energy's translation invariance."""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+import workloads as w
+from oracle import basis, dm, grid_ops, poisson, scf
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    s = w.config_system("tiny8")
+    fn = basis.functions(s)
+    S, T = basis.overlap_kinetic(fn)
+    return s, fn, S, T
+
+
+def test_unit_potential_is_grid_overlap(tiny):
+    s, fn, S, _ = tiny
+    ones = np.ones(tuple(int(t) for t in s.grid_n[::-1]))
+    Sg = grid_ops.potential_matrix(s, ones)
+    assert np.max(np.abs(Sg - Sg.T)) < 1e-14
+    # the grid overlap approaches the closed form (h sqrt(zeta_max) = 0.87 here,
+    # so only the smooth functions agree closely)
+    smooth = np.nonzero(fn["zeta"] <= 0.3)[0]
+    assert np.max(np.abs(Sg[np.ix_(smooth, smooth)] - S[np.ix_(smooth, smooth)])) < 2e-3
+
+
+def test_linearity_and_symmetry(tiny):
+    s, fn, _, _ = tiny
+    rng = np.random.default_rng(0)
+    shp = tuple(int(t) for t in s.grid_n[::-1])
+    v1, v2 = rng.normal(size=shp), rng.normal(size=shp)
+    A = grid_ops.potential_matrix(s, v1)
+    B = grid_ops.potential_matrix(s, v2)
+    C = grid_ops.potential_matrix(s, 2.5 * v1 - 0.5 * v2)
+    assert np.max(np.abs(C - (2.5 * A - 0.5 * B))) < 1e-12
+    assert np.max(np.abs(A - A.T)) < 1e-13
+
+
+def test_quadrature_matches_direct_pair_sums(tiny):
+    """Table-based V against a direct evaluation of Eq. A.6 restricted to
+    the window intersection box, pair by pair."""
+    s, fn, _, _ = tiny
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=tuple(int(t) for t in s.grid_n[::-1]))
+    V = grid_ops.potential_matrix(s, v)
+    K = len(fn["zeta"])
+    pairs = [(int(a), int(b)) for a, b in rng.integers(0, K, (25, 2))] + [(0, 0), (3, 77), (44, 45)]
+    got = grid_ops.potential_entries(s, v, pairs)
+    ref = np.array([V[a, b] for a, b in pairs])
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+def test_window_error_bound(tiny):
+    s, fn, _, _ = tiny
+    v = np.cos(np.arange(s.n_grid) * 0.37).reshape(tuple(int(t) for t in s.grid_n[::-1]))
+    for eta in (1e-4, 1e-8):
+        Vw = grid_ops.potential_matrix(s, v, eta=eta)
+        Vf = grid_ops.potential_matrix(s, v, windowed=False)
+        assert np.max(np.abs(Vw - Vf)) <= 3.0 * np.max(np.abs(v)) * math.sqrt(3 * eta)
+    assert np.max(np.abs(grid_ops.potential_matrix(s, v, eta=1e-4) - Vf)) > 1e-9
+
+
+def test_density_count_and_pair_density(tiny):
+    s, fn, _, _ = tiny
+    K = len(fn["zeta"])
+    rng = np.random.default_rng(2)
+    A = rng.normal(size=(K, K)) * 0.1
+    P = A + A.T
+    n = grid_ops.density_on_grid(s, P)
+    ones = np.ones_like(n)
+    Sg = grid_ops.potential_matrix(s, ones)
+    assert abs(s.grid_h ** 3 * n.sum() - 2 * np.sum(P * Sg)) < 1e-10 * max(1.0, abs(n.sum()))
+    # P = e_a e_b^T + e_b e_a^T gives n = 4 phi_a phi_b (windowed) pointwise
+    a, b = 5, 17
+    E = np.zeros((K, K))
+    E[a, b] = E[b, a] = 1.0
+    nab = grid_ops.density_on_grid(s, E)
+    lo, hi = basis.window_ranges(s, fn, 1e-10)
+    xs = [s.grid_origin[d] + s.grid_h * np.arange(s.grid_n[d]) for d in range(3)]
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    ph = basis.phi_at({k: v[[a, b]] for k, v in fn.items()}, pts)
+    iz, iy, ix = np.meshgrid(*[np.arange(s.grid_n[d]) for d in (2, 1, 0)], indexing="ij")
+    idx = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], 1)
+    inside = lambda f: np.all((idx >= lo[f]) & (idx <= hi[f]), axis=1)
+    ref = 4 * ph[:, 0] * ph[:, 1] * inside(a) * inside(b)
+    assert np.max(np.abs(nab.ravel() - ref)) < 1e-13
+    # sampled evaluation agrees with the full grid
+    pick = rng.integers(0, n.size, 40)
+    assert np.max(np.abs(grid_ops.density_at(s, P, pick) - n.ravel()[pick])) < 1e-12
+
+
+def test_cube_constant_closed_form():
+    assert abs(poisson.cube_inv_r_constant() - (3 * math.log(2 + math.sqrt(3)) - math.pi / 2)) < 1e-12
+
+
+def test_fft_size():
+    assert poisson.fft_size(154) == 160 and poisson.fft_size(97) == 98 and poisson.fft_size(1) == 1
+
+
+def test_fft_convolution_equals_direct_sum():
+    s = w.make_system(np.array([[0.0, 0.0, 0.0]]), h=0.5, pad=2.2)
+    rho = np.random.default_rng(3).normal(size=tuple(int(t) for t in s.grid_n[::-1]))
+    a = poisson.hartree(s, rho)
+    b = poisson.hartree_direct(s, rho)
+    assert np.max(np.abs(a - b)) < 1e-12 * np.max(np.abs(b))
+
+
+def test_gaussian_charge_potential():
+    """rho = q (alpha/pi)^(3/2) exp(-alpha r^2) has v = q erf(sqrt(alpha) r)/r;
+    the discrete convolution converges to it as h -> 0."""
+    q, alpha = 2.0, 0.8
+    errs = []
+    for h in (0.4, 0.2):
+        s = w.make_system(np.array([[0.0, 0.0, 0.0]]), h=h, pad=7.0)
+        xs, ys, zs = scf.grid_points(s)
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        r = np.sqrt(X * X + Y * Y + Z * Z)
+        rho = q * (alpha / math.pi) ** 1.5 * np.exp(-alpha * r * r)
+        v = poisson.hartree(s, rho)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            ref = np.where(r > 1e-12, q * special.erf(math.sqrt(alpha) * r) / np.where(r > 0, r, 1), q * 2 * math.sqrt(alpha / math.pi))
+        errs.append(np.max(np.abs(v - ref)) / np.max(ref))
+    assert errs[0] < 1e-2 and errs[1] < 0.3 * errs[0], errs
+
+
+def test_slater_exchange_closed_form():
+    n = np.array([math.pi / 3, 1.0, 8.0, 0.0, -1e-3])
+    vx, ex = poisson.slater_exchange(n)
+    assert abs(vx[0] + 1.0) < 1e-15
+    assert abs(vx[2] - 2 * vx[1]) < 1e-14
+    assert np.allclose(vx[:3], 4.0 / 3.0 * ex[:3], rtol=1e-15)
+    assert vx[3] == 0 and vx[4] == 0 and ex[4] == 0
+
+
+def test_energy_translation_invariance():
+    """Moving every atom and the grid by one grid vector leaves one SCF
+    step's energy unchanged (to roundoff)."""
+    s = w.config_system("tiny8")
+    r1 = scf.step(scf.setup(s), scf.ion_density(s))
+    sh = np.array([s.grid_h, -2 * s.grid_h, s.grid_h])
+    s2 = w.make_system(s.xyz + sh, h=s.grid_h, grid_n=s.grid_n, grid_origin=s.grid_origin + sh)
+    r2 = scf.step(scf.setup(s2), scf.ion_density(s2))
+    assert abs(r1["E"]["total"] - r2["E"]["total"]) < 1e-9 * abs(r1["E"]["total"])
+
+
+def test_band_energy_double_counting_identity():
+    """2 Tr[P V[v]] = h^3 sum v n[P] for any v (quadrature and collocation use
+    the same windowed functions)."""
+    s = w.config_system("tiny8")
+    st = scf.setup(s)
+    n0 = scf.ion_density(s)
+    r = scf.step(st, n0)
+    V = r["F"] - st.T
+    assert abs(2 * np.sum(r["P"] * V) - s.grid_h ** 3 * np.sum(r["v"] * r["n_out"])) < 1e-9

@@ -1,0 +1,151 @@
+"""Synthetic silicon clusters cut from the diamond lattice.
+
+The paper's own geometries (H-terminated Si nanocrystals and water clusters,
+Supp. D, Tables D.1-D.2) are not available, so seeded synthetic clusters stand
+in for them: diamond-cubic silicon (a = 10.26 bohr), either a 2x2x2 supercell
+treated as an isolated cluster or a sphere of lattice sites of radius R around
+an atom at the origin, with every coordinate jittered by a seeded normal draw.
+
+Basis per atom (uncontracted Cartesian primitives, Eq. A.1-A.3 with N_cn = 1):
+four s shells with exponents 0.1, 0.3, 1.0, 3.0 and two p shells with
+exponents 0.2, 0.8, i.e. 10 functions per atom.  The grid is the Cartesian
+grid of Section 2 with spacing h and 6 bohr of vacuum on each side.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SI_A0 = 10.26  # bohr, diamond-cubic lattice constant
+
+# fractional positions of the 8 atoms in the conventional diamond cell
+DIAMOND_BASIS = np.array([
+    [0.0, 0.0, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0],
+    [0.25, 0.25, 0.25], [0.25, 0.75, 0.75], [0.75, 0.25, 0.75], [0.75, 0.75, 0.25],
+])
+
+# (l, exponent) per shell, in function order on every atom; p shells expand to x, y, z
+SHELL_SPEC = ((0, 0.1), (0, 0.3), (0, 1.0), (0, 3.0), (1, 0.2), (1, 0.8))
+
+
+def diamond_supercell(nrep: int = 2, a: float = SI_A0) -> np.ndarray:
+    """All atoms of an nrep^3 supercell of the conventional diamond cell."""
+    pts = []
+    for i in range(nrep):
+        for j in range(nrep):
+            for k in range(nrep):
+                for b in DIAMOND_BASIS:
+                    pts.append((np.array([i, j, k]) + b) * a)
+    return np.array(pts, dtype=np.float64)
+
+
+def diamond_sphere(radius: float, a: float = SI_A0) -> np.ndarray:
+    """Lattice sites with |R| <= radius, centred on the atom at the origin."""
+    n = int(math.ceil(radius / a)) + 1
+    pts = []
+    for i in range(-n, n + 1):
+        for j in range(-n, n + 1):
+            for k in range(-n, n + 1):
+                for b in DIAMOND_BASIS:
+                    p = (np.array([i, j, k]) + b) * a
+                    if p @ p <= radius * radius + 1e-9:
+                        pts.append(p)
+    pts = np.array(pts, dtype=np.float64)
+    # deterministic order: by z, then y, then x (spatial locality of indices)
+    order = np.lexsort((pts[:, 0], pts[:, 1], pts[:, 2]))
+    return pts[order]
+
+
+@dataclass
+class System:
+    """One synthetic cluster and everything needed to set up a calculation.
+
+    Attributes are plain numbers and arrays; nothing here is derived from the
+    method's equations.
+    """
+    xyz: np.ndarray                      # (n_atoms, 3) bohr
+    shell_atom: np.ndarray               # (n_shells,) int32
+    shell_l: np.ndarray                  # (n_shells,) int32, 0 or 1
+    shell_exp: np.ndarray                # (n_shells,) float64
+    grid_origin: np.ndarray              # (3,) bohr
+    grid_h: float
+    grid_n: np.ndarray                   # (3,) int: nx, ny, nz
+    n_electrons: float
+    kT: float
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_atoms(self) -> int:
+        return int(self.xyz.shape[0])
+
+    @property
+    def n_basis(self) -> int:
+        return int(np.sum(np.where(self.shell_l == 0, 1, 3)))
+
+    @property
+    def n_grid(self) -> int:
+        return int(np.prod(self.grid_n))
+
+
+def make_system(xyz: np.ndarray, *, h: float = 0.4, pad: float = 6.0, kT: float = 0.01,
+                electrons_per_atom: float = 4.0, shells=SHELL_SPEC, name: str = "",
+                grid_n=None, grid_origin=None) -> System:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    sa, sl, se = [], [], []
+    for a in range(xyz.shape[0]):
+        for (l, z) in shells:
+            sa.append(a)
+            sl.append(l)
+            se.append(z)
+    lo = xyz.min(axis=0) - pad
+    hi = xyz.max(axis=0) + pad
+    if grid_origin is None:
+        grid_origin = lo
+    if grid_n is None:
+        grid_n = np.array([int(math.ceil((hi[d] - lo[d]) / h)) + 1 for d in range(3)], dtype=np.int64)
+    return System(xyz=xyz, shell_atom=np.array(sa, np.int32), shell_l=np.array(sl, np.int32),
+                  shell_exp=np.array(se, np.float64), grid_origin=np.asarray(grid_origin, np.float64),
+                  grid_h=float(h), grid_n=np.asarray(grid_n, np.int64),
+                  n_electrons=float(electrons_per_atom * xyz.shape[0]), kT=float(kT), name=name)
+
+
+def jitter(xyz: np.ndarray, sigma: float, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return xyz + rng.normal(0.0, sigma, xyz.shape)
+
+
+def config_system(name: str, seed: int = 0, **kw) -> System:
+    """Named workloads.
+
+    cluster64   2x2x2 supercell, sigma 0.05, kT 0.01            (K = 640)
+    sphere25    sphere R = 25 bohr, sigma 0.05, kT 0.01          (K ~ 4.6k)
+    sphere40    sphere R = 40 bohr, sigma 0.1, kT 0.005          (K ~ 19.6k)
+    sphereR<r>  sphere of radius r, sigma 0.1, kT 0.01
+    tiny<n>     the first n atoms of the 64-atom cluster, coarse grid (tests)
+    """
+    if name == "cluster64":
+        xyz = jitter(diamond_supercell(2), 0.05, seed)
+        return make_system(xyz, kT=0.01, name=name, **kw)
+    if name == "sphere25":
+        xyz = jitter(diamond_sphere(25.0), 0.05, seed)
+        return make_system(xyz, kT=0.01, name=name, **kw)
+    if name == "sphere40":
+        xyz = jitter(diamond_sphere(40.0), 0.1, seed)
+        return make_system(xyz, kT=0.005, name=name, **kw)
+    if name.startswith("sphereR"):
+        r = float(name[len("sphereR"):])
+        xyz = jitter(diamond_sphere(r), 0.1, seed)
+        return make_system(xyz, kT=kw.pop("kT", 0.01), name=name, **kw)
+    if name.startswith("tiny"):
+        n = int(name[4:])
+        xyz = jitter(diamond_supercell(2), 0.05, seed)
+        # nearest n atoms to the cluster centre, for small well-conditioned cases
+        c = xyz.mean(axis=0)
+        idx = np.argsort(((xyz - c) ** 2).sum(axis=1), kind="stable")[:n]
+        kw.setdefault("h", 0.5)
+        kw.setdefault("pad", 5.0)
+        return make_system(xyz[np.sort(idx)], kT=kw.pop("kT", 0.01), name=name, **kw)
+    raise ValueError(f"unknown workload {name!r}")
