@@ -1,0 +1,295 @@
+"""Benchmark: SCF steps of the Chebyshev density-matrix DFT on one GB300.
+
+A step is one full SCF cycle through the C ABI (dft_scf_step): Hartree +
+LDA potential, quadrature into the Fock matrix, spectral bounds, Chebyshev
+moments, mu, the Chebyshev density matrix, collocation of n(r), the energy
+and the density mixing.  The metric is P-columns/s: basis functions (columns
+of P) produced per second of SCF wall time, with the SCF-step time beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--precision fp64|bf16x3] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+repository) on a bounded sample of the same workload.  Under torchrun every
+rank runs an independent replica (the path has no cross-GPU exchange here);
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "P-columns/s & SCF-step time, mixed vs FP64 GPU at <=1e-5 Ha/atom error"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 issue rate of GB300: 1.25 TFLOP/s nominal over 152 SMs at 2.07 GHz
+# is 2 DFMA per SM per clock
+FP64_FLOP_PER_SM_CLK = 4.0
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="cluster64")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_PATH))
+    except Exception:
+        return {}
+
+
+def cpu_baseline(sysm, budget_s):
+    """The FP64 oracle, as it stands, on a bounded sample of one SCF step:
+    the eigensolve-based DM and the Poisson solve in full, quadrature and
+    collocation on a slab of z-planes scaled to the whole grid (their cost is
+    uniform per plane), the eigensolve scaled by K^3 when K is too large."""
+    import scipy.linalg as sla  # noqa: F401
+    from oracle import basis, dm, grid_ops, poisson, scf
+    import oracle.grid_ops as go
+    t0 = time.perf_counter()
+    st = scf.setup(sysm)
+    n0 = scf.ion_density(sysm)
+    v, _, _ = scf.potential(st, n0)
+    t_pois = 0.0
+    a = time.perf_counter()
+    poisson.hartree(sysm, n0, st.c0)
+    t_pois = time.perf_counter() - a
+    nz = int(sysm.grid_n[2])
+    per_plane = sysm.n_basis * int(sysm.grid_n[0]) * int(sysm.grid_n[1])
+    planes = max(1, min(nz, int(2e8 // max(1, per_plane * 8)) or 1))
+    planes = min(planes, 8)
+    sub = type(sysm)(**{**sysm.__dict__})
+    sub.grid_n = np.array([sysm.grid_n[0], sysm.grid_n[1], planes])
+    a = time.perf_counter()
+    go.potential_matrix(sub, v[:planes], st.model.eta)
+    t_quad = (time.perf_counter() - a) * nz / planes
+    K = sysm.n_basis
+    P = np.eye(K) * 0.01
+    a = time.perf_counter()
+    go.density_on_grid(sub, P, st.model.eta)
+    t_col = (time.perf_counter() - a) * nz / planes
+    F = st.T + np.diag(np.diag(st.S))
+    ks = min(K, 1500)
+    a = time.perf_counter()
+    dm.dm_exact(F[:ks, :ks] + st.T[:ks, :ks], st.S[:ks, :ks], min(sysm.n_electrons, ks), 1.0 / sysm.kT)
+    t_eig = (time.perf_counter() - a) * (K / ks) ** 3
+    t_step = t_pois * 2 + t_quad + t_col + t_eig
+    return {"value": K / t_step, "unit": "P-columns/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one oracle SCF step of {sysm.name}: eigensolve DM ({'full' if ks == K else f'K={ks} scaled by K^3'}),"
+                       f" 2 Poisson solves in full, quadrature+collocation on {planes}/{nz} z-planes scaled"),
+            "seconds": time.perf_counter() - t0, "stage_s": {"eig": t_eig, "quad": t_quad, "coll": t_col,
+                                                             "poisson": 2 * t_pois}}
+
+
+def run_reference(args, sysm, rank, world):
+    if rank != 0:
+        return
+    res = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(sysm, args.cpu_budget)
+        if i >= args.warmup:
+            res.append(cb)
+    val = statistics.median(r["value"] for r in res)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "P-columns/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sysm.n_basis / val,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": sysm.name, "n_basis": sysm.n_basis,
+                                            "n_atoms": sysm.n_atoms, "grid": [int(x) for x in sysm.grid_n]},
+            "cpu_baseline": {"kind": "oracle", "cores": res[0]["cores"], "sample": res[0]["sample"], "value": val,
+                             "unit": "P-columns/s"},
+            "e2e": {"value": val, "unit": "P-columns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import workloads as w
+    sysm = w.config_system(args.workload)
+    if args.impl == "reference":
+        run_reference(args, sysm, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    import paper_2108_13478_gb300 as dft
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    prec = dft.DFT_PREC_FP64 if args.precision == "fp64" else dft.DFT_PREC_BF16X3
+    stream = torch.cuda.current_stream()
+    ctx = dft.Context(sysm, device=f"cuda:{local}", precision=prec, cheb_tail_tol=1e-10, mix_alpha=0.3)
+    ctx.overlap_kinetic()
+    n = ctx.initial_density()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{local}")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        ctx.scf_step(n)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = dft.dft_kernel_launches()
+    step_ms, infos = [], []
+    for _ in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (outside the events)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = ctx.scf_step(n)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        infos.append(info)
+    barrier()
+    launches = (dft.dft_kernel_launches() - launches0) / args.steps
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    K = ctx.K
+    value = world * K * args.steps / (total_ms / 1000.0)
+    # end to end through the public API with host buffers: pinned n_in -> device,
+    # step, next density and energies back to the host
+    n_host = torch.empty(ctx.grid_shape, dtype=torch.float64, pin_memory=True)
+    n_host.copy_(n.cpu())
+    out_host = torch.empty_like(n_host).pin_memory()
+    dev_n = ctx.grid_array()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        dev_n.copy_(n_host, non_blocking=True)
+        info = ctx.scf_step(dev_n)
+        out_host.copy_(dev_n, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        n_host.copy_(out_host)
+    t = torch.tensor([e2e_ms], device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * K * args.steps / (float(t.item()) / 1000.0)
+    # roofline of the dominant kernel: the Chebyshev step (one launch per term of pass 2)
+    pk = peaks()
+    n_c = infos[-1].n_cheb
+    cheb_ms = statistics.median(i.ms_stage[4] for i in infos)
+    per_launch_s = cheb_ms / 1000.0 / max(1, n_c - 2)
+    sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    if prec == dft.DFT_PREC_FP64:
+        flops = 2.0 * K ** 3
+        peak = FP64_FLOP_PER_SM_CLK * N_SM * sm_mhz * 1e6 / 1e12
+        roof = {"kernel": "k_cheb_step_fp64", "bound": "alu", "achieved": flops / per_launch_s / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "frac": (flops / per_launch_s / 1e12) / peak,
+                "traffic": None, "peak_source": "FP64 issue rate 4 flop/SM/clk x 152 SMs x median SM clock"}
+        dtype = "f64"
+    else:
+        flops = 3 * 2.0 * K ** 3
+        peak = pk.get("bf16_tflops_sustained", 1700.0)
+        roof = {"kernel": "cheb_step_bf16x3", "bound": "tensor", "achieved": flops / per_launch_s / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "frac": (flops / per_launch_s / 1e12) / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
+        dtype = "bf16x3"
+    line = {"metric": METRIC, "value": value, "unit": "P-columns/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": sysm.name, "n_basis": K, "n_atoms": sysm.n_atoms,
+                       "grid": [int(x) for x in sysm.grid_n], "kT": sysm.kT, "n_cheb": n_c,
+                       "precision": args.precision, "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": "P-columns/s",
+                    "h2d_bytes_per_step": int(n_host.numel() * 8), "d2h_bytes_per_step": int(n_host.numel() * 8)},
+            "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+            "stages_ms": [round(x, 3) for x in infos[-1].ms_stage],
+            "energy_per_atom": infos[-1].e_total / sysm.n_atoms}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(sysm, args.cpu_budget).items()
+                                if k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * dft.h -- C ABI of the GB300 Chebyshev density-matrix DFT library (libdft).
+ *
+ * Method: Fabian, Shpiro, Baer, "Linear weak scalability of density
+ * functional theory calculations without imposing electron localization"
+ * (arXiv 2108.13478).  Gaussian basis functions phi_alpha live on a
+ * Cartesian grid of spacing h; the density matrix is the Fermi-Dirac
+ * matrix function P = f_FD(S^-1 F) S^-1 (Eq. 2.9) expanded in Chebyshev
+ * polynomials (Supp. B); the density is collocated on the grid (Eq. 2.7),
+ * the Kohn-Sham potential is built there (Eq. 2.6) and integrated back into
+ * the Fock matrix (Eq. 2.5), which closes the SCF cycle (Supp. A.3).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns a dft_status; nothing throws across the ABI.
+ *    On failure dft_last_error(ctx) returns a message owned by the context.
+ *  - Units are atomic units (bohr, hartree).
+ *  - Matrices are K x K, row-major, double precision, symmetric, on the
+ *    device.  Grids are double [nz][ny][nx] (x fastest) on the device.
+ *  - P is per spin: n(r) = 2 sum_ab P_ab phi_a phi_b and N_e = 2 Tr[P S]
+ *    (Eqs. 2.7, 2.8).
+ *  - The caller owns every buffer it passes.  The context keeps pointers
+ *    into the caller's workspace (sized by dft_workspace_bytes), which must
+ *    stay allocated until dft_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; functions that need a result on the
+ *    host (spectral bounds to fix the Chebyshev order, the info struct)
+ *    synchronise that stream before returning.
+ *  - Device pointers must be 16-byte aligned.
+ */
+#ifndef DFT_H
+#define DFT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dft_status {
+    DFT_OK = 0,
+    DFT_EINVAL = 1,       /* bad argument: null pointer, size, unsupported shell */
+    DFT_ENOMEM = 2,       /* workspace too small */
+    DFT_ECUDA = 3,        /* a CUDA runtime or cuFFT call failed */
+    DFT_ESPECTRUM = 4,    /* Chebyshev iterates grew: spectrum outside [E_min, E_max] */
+    DFT_ENOTCONV = 5,     /* mu bisection did not bracket N_e; Cholesky of S failed */
+    DFT_ETIMEOUT = 6,     /* a bounded device wait gave up */
+    DFT_EINTERNAL = 7,
+    DFT_EUNSUPPORTED = 8  /* feature not built in this library */
+} dft_status;
+
+enum { DFT_PREC_FP64 = 0, DFT_PREC_BF16X3 = 1 };
+enum { DFT_MODEL_LITERAL = 0, DFT_MODEL_NEUTRAL = 1 };
+enum { DFT_MIX_LINEAR = 0, DFT_MIX_KERKER = 1 };
+
+typedef struct dft_ctx dft_ctx;
+
+/* Atoms and uncontracted Cartesian Gaussian shells (Eqs. A.1-A.3 with one
+ * primitive per shell).  Host pointers, read during dft_init_basis only.
+ * Shell s sits on atom shell_atom[s], has angular momentum shell_l[s] in
+ * {0, 1} and exponent shell_exp[s] > 0.  Basis functions are numbered shell
+ * by shell; a p shell contributes x, y, z in that order.  Each function is
+ * normalised to unit self-overlap. */
+typedef struct dft_basis_desc {
+    int n_atoms;
+    const double* xyz;        /* n_atoms * 3, bohr */
+    int n_shells;
+    const int* shell_atom;
+    const int* shell_l;
+    const double* shell_exp;
+} dft_basis_desc;
+
+/* Grid point (i, j, k) sits at origin + h * (i, j, k), 0 <= i < n[0] (x),
+ * 0 <= j < n[1] (y), 0 <= k < n[2] (z). */
+typedef struct dft_grid_desc {
+    double origin[3];
+    double h;
+    int n[3];
+} dft_grid_desc;
+
+typedef struct dft_params {
+    double beta;            /* inverse temperature 1/kT, 1/hartree (> 0) */
+    double n_electrons;     /* N_e, fixes mu through Eq. 2.8 */
+    double eta;             /* window charge cutoff of Eq. A.4 (e.g. 1e-10) */
+    double cheb_tail_tol;   /* N_C = smallest order whose coefficient tail sum |a_l| is below this */
+    int    cheb_order;      /* > 0: use this N_C instead of the tail rule */
+    int    precision;       /* DFT_PREC_FP64 or DFT_PREC_BF16X3 (Chebyshev products) */
+    double e_min, e_max;    /* if e_max > e_min: fixed spectral bounds, no Lanczos */
+    int    lanczos_steps;   /* Lanczos steps for the bounds (0 -> 64) */
+    int    model;           /* DFT_MODEL_LITERAL: Hartree of the electrons only;
+                               DFT_MODEL_NEUTRAL: plus Gaussian ionic charges */
+    double vloc_depth;      /* v_loc = -depth exp(-r^2 / width^2) per atom */
+    double vloc_width;
+    double ion_charge;      /* ionic charge per atom in the neutral model */
+    int    mixer;           /* DFT_MIX_LINEAR or DFT_MIX_KERKER (density mixing) */
+    double mix_alpha;       /* mixing fraction of the output density */
+    double kerker_q0;       /* Kerker wave number (bohr^-1) for DFT_MIX_KERKER */
+    unsigned long long seed;/* Lanczos start vector */
+} dft_params;
+
+/* Results of dft_density_matrix / dft_scf_step.  ms_stage: CUDA-event
+ * times of the stages of the last call, in the order quadrature,
+ * transform (F -> H_N), Lanczos, moments pass, Chebyshev pass,
+ * back-transform, collocation, Poisson+LDA. */
+typedef struct dft_info {
+    double mu, e_min, e_max, n_e_trace;  /* n_e_trace = 2 Tr[P S] */
+    double e_total, e_kin, e_loc, e_hartree, e_xc;
+    double de_per_atom;                  /* (E - E_previous step) / n_atoms */
+    double residual;                     /* max |n_out - n_in| */
+    int n_cheb;                          /* N_C used */
+    int iter;                            /* SCF steps taken by this context */
+    int spectrum_ok;                     /* 1 if every iterate stayed bounded */
+    int reserved;
+    float ms_stage[8];
+} dft_info;
+
+/* Bytes of device workspace dft_init_basis needs for this problem.
+ * Returns 0 on invalid input. */
+size_t dft_workspace_bytes(const dft_basis_desc* basis, const dft_grid_desc* grid,
+                           const dft_params* params);
+
+/* Set up a context: basis functions, cubic windows W_alpha (Eq. A.4,
+ * Supp. A.1.1), separable 1D tables (Supp. A.1), grid-tile function lists,
+ * v_loc on the grid (Eq. 2.6) and the FFT Poisson plan.  workspace is a
+ * device buffer of at least dft_workspace_bytes() bytes, 256-byte aligned;
+ * cuFFT allocates its own plan work areas here.  On failure *ctx is still
+ * set (when possible) so that dft_last_error can report the reason; it must
+ * be released with dft_destroy. */
+dft_status dft_init_basis(dft_ctx** ctx, const dft_basis_desc* basis, const dft_grid_desc* grid,
+                          const dft_params* params, void* workspace, size_t ws_bytes, void* stream);
+
+/* Closed-form overlap S and kinetic T = <-1/2 laplacian> (the continuum
+ * limits of Eqs. 2.1, 2.2), written to S and T (device, K x K; either may be
+ * NULL).  Also factors S = L L^T (FP64 Cholesky; the paper applies S^-1 by
+ * PCG, footnote 2) and keeps L^-1 and T in the context.  Must be called
+ * before dft_density_matrix and dft_scf_step.  DFT_ENOTCONV if S is not
+ * positive definite. */
+dft_status dft_overlap_kinetic(dft_ctx* ctx, double* S, double* T, void* stream);
+
+/* P = f_FD(S^-1 F) S^-1 (Eq. 2.9) for the Fock matrix F (device, K x K),
+ * by the Chebyshev recurrence of Supp. B in the symmetric form
+ * F~ = L^-1 F L^-T, X_0 = I, X_{l+1} = 2 H_N X_l - X_{l-1}, H_N = (F~ - Ebar)/dE,
+ * P = L^-T (sum_l a_l(mu) X_l) L^-1, with mu fixed by 2 Tr[P S] = N_e
+ * (Eq. 2.8) from the Chebyshev moments.  P (device, K x K) is written;
+ * info (host, may be NULL) receives mu, the bounds and N_C. */
+dft_status dft_density_matrix(dft_ctx* ctx, const double* F, double* P, dft_info* info, void* stream);
+
+/* n(r_g) = 2 sum_ab P_ab phi_a(r_g) phi_b(r_g) over the windows (Eq. 2.7,
+ * Supp. A.1.2).  P device K x K; n_grid device [nz][ny][nx], overwritten. */
+dft_status dft_density_on_grid(dft_ctx* ctx, const double* P, double* n_grid, void* stream);
+
+/* V_ab = h^3 sum_{g in W_a and W_b} phi_a v phi_b (Eq. 2.5 / A.6).
+ * v_grid device [nz][ny][nx]; V device K x K, overwritten. */
+dft_status dft_potential_matrix(dft_ctx* ctx, const double* v_grid, double* V, void* stream);
+
+/* Kohn-Sham potential of a density (Eq. 2.6): v_ks = v_loc + v_H[n - n_ion]
+ * + v_x[n], with v_H the free-space Hartree potential (zero-padded FFT
+ * convolution) and v_x the LDA (Slater) exchange potential.  n_grid, v_ks
+ * device grids.  energies (host, may be NULL) receives 3 doubles:
+ * h^3 sum v_loc n, 1/2 h^3 sum v_H rho, h^3 sum eps_x n. */
+dft_status dft_hartree_xc(dft_ctx* ctx, const double* n_grid, double* v_ks, double* energies,
+                          void* stream);
+
+/* One SCF cycle (Supp. A.3): from the input density n_in (device grid),
+ * v_KS[n_in] -> V^KS -> F = T + V^KS -> P -> n_out -> energy of n_out ->
+ * mixing.  n_in_out is overwritten with the next input density; v_ks_out
+ * (device grid, may be NULL) receives v_KS[n_in]; P_out (device K x K, may
+ * be NULL) receives P; info (host, may be NULL) receives the energies,
+ * mu, N_C and the density residual. */
+dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double* P_out,
+                        dft_info* info, void* stream);
+
+/* Superposition-of-atoms start density (Supp. A.3: "sum of atomic
+ * densities"): a normalised Gaussian of ion_charge electrons and width
+ * vloc_width on every atom.  n_grid device grid, overwritten. */
+dft_status dft_initial_density(dft_ctx* ctx, double* n_grid, void* stream);
+
+/* Release the context (not the caller's workspace). */
+dft_status dft_destroy(dft_ctx* ctx);
+
+/* Message for the last failure on this context ("" if none). */
+const char* dft_last_error(const dft_ctx* ctx);
+
+/* Library version string. */
+const char* dft_version(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (cuFFT's own kernels not included); for launch accounting in benchmarks. */
+unsigned long long dft_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFT_H */

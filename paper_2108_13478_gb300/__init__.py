@@ -1,0 +1,134 @@
+"""GB300 Chebyshev density-matrix DFT (arXiv 2108.13478), Python side.
+
+`_binding` mirrors the C ABI of include/dft.h one function per entry point.
+`Context` below bundles the descriptors and the device workspace so that a
+caller can go from atoms and shells to SCF steps in a few lines; it only
+marshals arguments, every step runs in libdft's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _binding as B
+from ._binding import (  # noqa: F401
+    DftError, dft_basis_desc, dft_grid_desc, dft_info, dft_params,
+    DFT_PREC_FP64, DFT_PREC_BF16X3, DFT_MODEL_LITERAL, DFT_MODEL_NEUTRAL, DFT_MIX_LINEAR, DFT_MIX_KERKER,
+    dft_workspace_bytes, dft_init_basis, dft_overlap_kinetic, dft_density_matrix, dft_density_on_grid,
+    dft_potential_matrix, dft_hartree_xc, dft_scf_step, dft_initial_density, dft_destroy, dft_last_error,
+    dft_version, dft_kernel_launches,
+)
+
+
+def make_params(*, kT, n_electrons, eta=1e-10, cheb_tail_tol=1e-10, cheb_order=0, precision=DFT_PREC_FP64,
+                e_min=0.0, e_max=0.0, lanczos_steps=64, model=DFT_MODEL_LITERAL, vloc_depth=4.0, vloc_width=1.5,
+                ion_charge=4.0, mixer=DFT_MIX_LINEAR, mix_alpha=0.3, kerker_q0=0.8, seed=1234) -> dft_params:
+    p = dft_params()
+    p.beta = 1.0 / kT
+    p.n_electrons = n_electrons
+    p.eta = eta
+    p.cheb_tail_tol = cheb_tail_tol
+    p.cheb_order = cheb_order
+    p.precision = precision
+    p.e_min, p.e_max = e_min, e_max
+    p.lanczos_steps = lanczos_steps
+    p.model = model
+    p.vloc_depth, p.vloc_width, p.ion_charge = vloc_depth, vloc_width, ion_charge
+    p.mixer, p.mix_alpha, p.kerker_q0 = mixer, mix_alpha, kerker_q0
+    p.seed = seed
+    return p
+
+
+class Context:
+    """One system on one GPU: descriptors, workspace and the libdft context.
+
+    system: any object with xyz (n,3), shell_atom, shell_l, shell_exp,
+    grid_origin (3,), grid_h, grid_n (3,) (nx, ny, nz), n_electrons, kT.
+    """
+
+    def __init__(self, system, device="cuda", stream=None, **param_kw):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self._xyz = np.ascontiguousarray(system.xyz, dtype=np.float64)
+        self._sa = np.ascontiguousarray(system.shell_atom, dtype=np.int32)
+        self._sl = np.ascontiguousarray(system.shell_l, dtype=np.int32)
+        self._se = np.ascontiguousarray(system.shell_exp, dtype=np.float64)
+        b = dft_basis_desc()
+        b.n_atoms = int(self._xyz.shape[0])
+        b.xyz = self._xyz.ctypes.data_as(C.POINTER(C.c_double))
+        b.n_shells = int(self._sa.shape[0])
+        b.shell_atom = self._sa.ctypes.data_as(C.POINTER(C.c_int))
+        b.shell_l = self._sl.ctypes.data_as(C.POINTER(C.c_int))
+        b.shell_exp = self._se.ctypes.data_as(C.POINTER(C.c_double))
+        g = dft_grid_desc()
+        for d in range(3):
+            g.origin[d] = float(system.grid_origin[d])
+            g.n[d] = int(system.grid_n[d])
+        g.h = float(system.grid_h)
+        param_kw.setdefault("kT", system.kT)
+        param_kw.setdefault("n_electrons", system.n_electrons)
+        self.params = make_params(**param_kw)
+        self.basis, self.grid = b, g
+        nbytes = dft_workspace_bytes(b, g, self.params)
+        if nbytes == 0:
+            raise DftError(B.DFT_EINVAL, "invalid system description")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws = self.workspace[off:off + nbytes]
+        self.ctx = dft_init_basis(b, g, self.params, self._ws, stream)
+        self.K = int(np.sum(np.where(self._sl == 0, 1, 3)))
+        self.grid_shape = (int(g.n[2]), int(g.n[1]), int(g.n[0]))
+        self.n_atoms = b.n_atoms
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            dft_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # allocation helpers (device memory through torch)
+    def matrix(self):
+        return self.torch.zeros((self.K, self.K), dtype=self.torch.float64, device=self.device)
+
+    def grid_array(self):
+        return self.torch.zeros(self.grid_shape, dtype=self.torch.float64, device=self.device)
+
+    def overlap_kinetic(self, stream=None):
+        S, T = self.matrix(), self.matrix()
+        dft_overlap_kinetic(self.ctx, S, T, stream)
+        return S, T
+
+    def density_matrix(self, F, stream=None):
+        P = self.matrix()
+        info = dft_density_matrix(self.ctx, F.contiguous(), P, stream)
+        return P, info
+
+    def density_on_grid(self, P, stream=None):
+        n = self.grid_array()
+        dft_density_on_grid(self.ctx, P.contiguous(), n, stream)
+        return n
+
+    def potential_matrix(self, v, stream=None):
+        V = self.matrix()
+        dft_potential_matrix(self.ctx, v.contiguous(), V, stream)
+        return V
+
+    def hartree_xc(self, n, stream=None):
+        v = self.grid_array()
+        e = dft_hartree_xc(self.ctx, n.contiguous(), v, stream)
+        return v, e
+
+    def initial_density(self, stream=None):
+        n = self.grid_array()
+        dft_initial_density(self.ctx, n, stream)
+        return n
+
+    def scf_step(self, n_in_out, v_ks_out=None, P_out=None, stream=None):
+        return dft_scf_step(self.ctx, n_in_out, v_ks_out, P_out, stream)

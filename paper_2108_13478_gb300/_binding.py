@@ -1,0 +1,178 @@
+"""ctypes binding of libdft (include/dft.h): argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch supplies device memory
+and the current stream.  Importing this module fails loudly when the shared
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdft.so")
+
+DFT_OK, DFT_EINVAL, DFT_ENOMEM, DFT_ECUDA, DFT_ESPECTRUM, DFT_ENOTCONV, DFT_ETIMEOUT, DFT_EINTERNAL, \
+    DFT_EUNSUPPORTED = range(9)
+STATUS_NAMES = {0: "DFT_OK", 1: "DFT_EINVAL", 2: "DFT_ENOMEM", 3: "DFT_ECUDA", 4: "DFT_ESPECTRUM",
+                5: "DFT_ENOTCONV", 6: "DFT_ETIMEOUT", 7: "DFT_EINTERNAL", 8: "DFT_EUNSUPPORTED"}
+DFT_PREC_FP64, DFT_PREC_BF16X3 = 0, 1
+DFT_MODEL_LITERAL, DFT_MODEL_NEUTRAL = 0, 1
+DFT_MIX_LINEAR, DFT_MIX_KERKER = 0, 1
+
+
+class dft_basis_desc(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("xyz", C.POINTER(C.c_double)), ("n_shells", C.c_int),
+                ("shell_atom", C.POINTER(C.c_int)), ("shell_l", C.POINTER(C.c_int)),
+                ("shell_exp", C.POINTER(C.c_double))]
+
+
+class dft_grid_desc(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("h", C.c_double), ("n", C.c_int * 3)]
+
+
+class dft_params(C.Structure):
+    _fields_ = [("beta", C.c_double), ("n_electrons", C.c_double), ("eta", C.c_double),
+                ("cheb_tail_tol", C.c_double), ("cheb_order", C.c_int), ("precision", C.c_int),
+                ("e_min", C.c_double), ("e_max", C.c_double), ("lanczos_steps", C.c_int), ("model", C.c_int),
+                ("vloc_depth", C.c_double), ("vloc_width", C.c_double), ("ion_charge", C.c_double),
+                ("mixer", C.c_int), ("mix_alpha", C.c_double), ("kerker_q0", C.c_double),
+                ("seed", C.c_ulonglong)]
+
+
+class dft_info(C.Structure):
+    _fields_ = [("mu", C.c_double), ("e_min", C.c_double), ("e_max", C.c_double), ("n_e_trace", C.c_double),
+                ("e_total", C.c_double), ("e_kin", C.c_double), ("e_loc", C.c_double), ("e_hartree", C.c_double),
+                ("e_xc", C.c_double), ("de_per_atom", C.c_double), ("residual", C.c_double),
+                ("n_cheb", C.c_int), ("iter", C.c_int), ("spectrum_ok", C.c_int), ("reserved", C.c_int),
+                ("ms_stage", C.c_float * 8)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("ms_stage", "reserved")}
+        d["ms_stage"] = list(self.ms_stage)
+        return d
+
+
+# (name, restype, argtypes) for every entry point of include/dft.h
+_P = C.c_void_p
+SIGNATURES = [
+    ("dft_workspace_bytes", C.c_size_t, [C.POINTER(dft_basis_desc), C.POINTER(dft_grid_desc), C.POINTER(dft_params)]),
+    ("dft_init_basis", C.c_int, [C.POINTER(_P), C.POINTER(dft_basis_desc), C.POINTER(dft_grid_desc),
+                                 C.POINTER(dft_params), _P, C.c_size_t, _P]),
+    ("dft_overlap_kinetic", C.c_int, [_P, _P, _P, _P]),
+    ("dft_density_matrix", C.c_int, [_P, _P, _P, C.POINTER(dft_info), _P]),
+    ("dft_density_on_grid", C.c_int, [_P, _P, _P, _P]),
+    ("dft_potential_matrix", C.c_int, [_P, _P, _P, _P]),
+    ("dft_hartree_xc", C.c_int, [_P, _P, _P, C.POINTER(C.c_double), _P]),
+    ("dft_scf_step", C.c_int, [_P, _P, _P, _P, C.POINTER(dft_info), _P]),
+    ("dft_initial_density", C.c_int, [_P, _P, _P]),
+    ("dft_destroy", C.c_int, [_P]),
+    ("dft_last_error", C.c_char_p, [_P]),
+    ("dft_version", C.c_char_p, []),
+    ("dft_kernel_launches", C.c_ulonglong, []),
+]
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libdft.so is not built ({path}); run __graft_entry__.build() or "
+                          "python paper_2108_13478_gb300/build.py")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = load()
+
+
+class DftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---- thin wrappers with the ABI's names (torch tensors in, status checked) ----
+
+def _check(ctx, st):
+    if st != DFT_OK:
+        msg = lib.dft_last_error(ctx).decode() if ctx else ""
+        raise DftError(st, msg)
+
+
+def dft_workspace_bytes(basis, grid, params) -> int:
+    return int(lib.dft_workspace_bytes(C.byref(basis), C.byref(grid), C.byref(params)))
+
+
+def dft_init_basis(basis, grid, params, workspace, stream=None):
+    ctx = C.c_void_p()
+    st = lib.dft_init_basis(C.byref(ctx), C.byref(basis), C.byref(grid), C.byref(params),
+                            _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream))
+    if st != DFT_OK:
+        msg = lib.dft_last_error(ctx).decode() if ctx.value else ""
+        if ctx.value:
+            lib.dft_destroy(ctx)
+        raise DftError(st, msg)
+    return ctx
+
+
+def dft_overlap_kinetic(ctx, S=None, T=None, stream=None):
+    _check(ctx, lib.dft_overlap_kinetic(ctx, _ptr(S), _ptr(T), _stream(stream)))
+
+
+def dft_density_matrix(ctx, F, P, stream=None) -> dft_info:
+    info = dft_info()
+    _check(ctx, lib.dft_density_matrix(ctx, _ptr(F), _ptr(P), C.byref(info), _stream(stream)))
+    return info
+
+
+def dft_density_on_grid(ctx, P, n_grid, stream=None):
+    _check(ctx, lib.dft_density_on_grid(ctx, _ptr(P), _ptr(n_grid), _stream(stream)))
+
+
+def dft_potential_matrix(ctx, v_grid, V, stream=None):
+    _check(ctx, lib.dft_potential_matrix(ctx, _ptr(v_grid), _ptr(V), _stream(stream)))
+
+
+def dft_hartree_xc(ctx, n_grid, v_ks, stream=None):
+    e = (C.c_double * 3)()
+    _check(ctx, lib.dft_hartree_xc(ctx, _ptr(n_grid), _ptr(v_ks), e, _stream(stream)))
+    return tuple(e)
+
+
+def dft_scf_step(ctx, n_in_out, v_ks_out=None, P_out=None, stream=None) -> dft_info:
+    info = dft_info()
+    _check(ctx, lib.dft_scf_step(ctx, _ptr(n_in_out), _ptr(v_ks_out), _ptr(P_out), C.byref(info), _stream(stream)))
+    return info
+
+
+def dft_initial_density(ctx, n_grid, stream=None):
+    _check(ctx, lib.dft_initial_density(ctx, _ptr(n_grid), _stream(stream)))
+
+
+def dft_destroy(ctx):
+    lib.dft_destroy(ctx)
+
+
+def dft_last_error(ctx) -> str:
+    return lib.dft_last_error(ctx).decode()
+
+
+def dft_version() -> str:
+    return lib.dft_version().decode()
+
+
+def dft_kernel_launches() -> int:
+    return int(lib.dft_kernel_launches())

@@ -1,0 +1,542 @@
+// C ABI of libdft (include/dft.h): context set-up, workspace layout and the
+// host-side orchestration of the SCF cycle (Supp. A.3).  Every numerical
+// step runs in the kernels of k_*.cu; the host only sizes the problem, picks
+// the Chebyshev order and enqueues work.
+#include "dft_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+using namespace dft;
+
+unsigned long long dft::g_launches = 0;
+
+namespace {
+
+const char* kVersion = "libdft 0.1 (sm_103a)";
+
+// Window half-length L solving c(L sqrt(zeta), l) = 1 - eta (Eq. A.4).
+// c(d, 0) = erf(d), c(d, 1) = 1 - exp(-d^2).
+double window_halfwidth(double zeta, int l, double eta) {
+    double d;
+    if (l == 1) {
+        d = std::sqrt(-std::log(eta));
+    } else {
+        double lo = 0.0, hi = 40.0;
+        for (int it = 0; it < 400; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (std::erfc(mid) > eta) lo = mid; else hi = mid;
+        }
+        d = 0.5 * (lo + hi);
+    }
+    return d / std::sqrt(zeta);
+}
+
+struct Layout {
+    size_t total = 0;
+    size_t off(size_t bytes) {
+        size_t o = total;
+        total += (bytes + 255) & ~size_t(255);
+        return o;
+    }
+};
+
+void validate(const dft_basis_desc* b, const dft_grid_desc* g, const dft_params* p) {
+    if (!b || !g || !p) throw Error(DFT_EINVAL, "null descriptor");
+    if (b->n_atoms <= 0 || !b->xyz) throw Error(DFT_EINVAL, "no atoms");
+    if (b->n_shells <= 0 || !b->shell_atom || !b->shell_l || !b->shell_exp) throw Error(DFT_EINVAL, "no shells");
+    for (int s = 0; s < b->n_shells; ++s) {
+        if (b->shell_atom[s] < 0 || b->shell_atom[s] >= b->n_atoms) throw Error(DFT_EINVAL, "shell_atom out of range");
+        if (b->shell_l[s] < 0 || b->shell_l[s] > 1) throw Error(DFT_EINVAL, "only s and p shells are supported");
+        if (!(b->shell_exp[s] > 0.0)) throw Error(DFT_EINVAL, "shell exponent must be positive");
+    }
+    if (!(g->h > 0.0)) throw Error(DFT_EINVAL, "grid spacing must be positive");
+    for (int d = 0; d < 3; ++d)
+        if (g->n[d] <= 0 || g->n[d] > 4096) throw Error(DFT_EINVAL, "grid size out of range");
+    if (!(p->beta > 0.0)) throw Error(DFT_EINVAL, "beta must be positive");
+    if (!(p->eta > 0.0 && p->eta < 1.0)) throw Error(DFT_EINVAL, "eta must be in (0, 1)");
+    if (p->precision != DFT_PREC_FP64 && p->precision != DFT_PREC_BF16X3)
+        throw Error(DFT_EINVAL, "unknown precision");
+}
+
+// functions, windows, tables and tile lists (host part of the set-up)
+void build_basis(Ctx& c, const dft_basis_desc* b, const dft_grid_desc* g, const dft_params* p,
+                 std::vector<int>* tile_ptr, std::vector<int>* tile_fn) {
+    c.n_atoms = b->n_atoms;
+    c.h = g->h;
+    for (int d = 0; d < 3; ++d) { c.n[d] = g->n[d]; c.origin[d] = g->origin[d]; }
+    c.ng = (long long)c.n[0] * c.n[1] * c.n[2];
+    c.p = *p;
+    c.xyz_host.assign(b->xyz, b->xyz + 3 * b->n_atoms);
+    c.fn_host.clear();
+    int wmax = 1;
+    for (int s = 0; s < b->n_shells; ++s) {
+        int a = b->shell_atom[s], l = b->shell_l[s];
+        double z = b->shell_exp[s];
+        double base = std::pow(2.0 * z / M_PI, 0.75);
+        double L = window_halfwidth(z, l, p->eta);
+        int ncomp = l == 0 ? 1 : 3;
+        for (int q = 0; q < ncomp; ++q) {
+            Fn f{};
+            f.cx = b->xyz[3 * a]; f.cy = b->xyz[3 * a + 1]; f.cz = b->xyz[3 * a + 2];
+            f.zeta = z;
+            f.norm = l == 0 ? base : base * 2.0 * std::sqrt(z);
+            f.px = (l == 1 && q == 0); f.py = (l == 1 && q == 1); f.pz = (l == 1 && q == 2);
+            const double cc[3] = {f.cx, f.cy, f.cz};
+            for (int d = 0; d < 3; ++d) {
+                long long lo = (long long)std::ceil((cc[d] - L - c.origin[d]) / c.h);
+                long long hi = (long long)std::floor((cc[d] + L - c.origin[d]) / c.h);
+                lo = std::max<long long>(lo, 0);
+                hi = std::min<long long>(hi, c.n[d] - 1);
+                f.lo[d] = (int)std::min<long long>(lo, c.n[d]);
+                f.hi[d] = (int)std::max<long long>(hi, -1);
+                wmax = std::max(wmax, f.hi[d] - f.lo[d] + 1);
+            }
+            c.fn_host.push_back(f);
+        }
+    }
+    c.K = (int)c.fn_host.size();
+    c.tab_w = wmax;
+    for (int d = 0; d < 3; ++d) c.ntile[d] = (c.n[d] + TILE - 1) / TILE;
+    c.n_tiles = (long long)c.ntile[0] * c.ntile[1] * c.ntile[2];
+    std::vector<int> cnt(c.n_tiles + 1, 0);
+    auto each_tile = [&](const Fn& f, auto&& fun) {
+        for (int d = 0; d < 3; ++d)
+            if (f.lo[d] > f.hi[d]) return;
+        for (int tz = f.lo[2] / TILE; tz <= f.hi[2] / TILE; ++tz)
+            for (int ty = f.lo[1] / TILE; ty <= f.hi[1] / TILE; ++ty)
+                for (int tx = f.lo[0] / TILE; tx <= f.hi[0] / TILE; ++tx)
+                    fun(((long long)tz * c.ntile[1] + ty) * c.ntile[0] + tx);
+    };
+    for (const Fn& f : c.fn_host) each_tile(f, [&](long long t) { cnt[t + 1]++; });
+    for (long long t = 0; t < c.n_tiles; ++t) cnt[t + 1] += cnt[t];
+    c.tile_nnz = cnt[c.n_tiles];
+    c.tile_max = 0;
+    for (long long t = 0; t < c.n_tiles; ++t) c.tile_max = std::max(c.tile_max, cnt[t + 1] - cnt[t]);
+    if (tile_ptr) {
+        *tile_ptr = cnt;
+        tile_fn->assign(c.tile_nnz, 0);
+        std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+        for (int f = 0; f < c.K; ++f) each_tile(c.fn_host[f], [&](long long t) { (*tile_fn)[pos[t]++] = f; });
+    }
+    for (int d = 0; d < 3; ++d) c.Nfft[d] = fft_size(2 * c.n[d]);
+    c.nfft_r = (long long)c.Nfft[0] * c.Nfft[1] * c.Nfft[2];
+    c.nfft_c = (long long)(c.Nfft[0] / 2 + 1) * c.Nfft[1] * c.Nfft[2];
+    c.cheb_cap = 1 << 16;
+    c.part_cap = std::max<long long>({2LL * cheb_step_parts(c.K), 3LL * 1184, 2048}) + 64;
+}
+
+// carve the workspace; with base == nullptr only the size is computed
+size_t carve(Ctx& c, char* base) {
+    Layout L;
+    size_t K2 = (size_t)c.K * c.K * sizeof(double);
+    size_t G = (size_t)c.ng * sizeof(double);
+    long long nkc = (long long)(c.n[0] / 2 + 1) * c.n[1] * c.n[2];
+    size_t o_fn = L.off(sizeof(Fn) * c.K);
+    size_t o_tab = L.off(sizeof(double) * (size_t)c.K * 3 * c.tab_w);
+    size_t o_tp = L.off(sizeof(int) * (c.n_tiles + 1));
+    size_t o_tf = L.off(sizeof(int) * std::max<long long>(1, c.tile_nnz));
+    size_t o_xyz = L.off(sizeof(double) * 3 * c.n_atoms);
+    size_t o_S = L.off(K2), o_T = L.off(K2), o_Li = L.off(K2), o_A = L.off(K2), o_H = L.off(K2);
+    size_t o_X0 = L.off(K2), o_X1 = L.off(K2), o_rho = L.off(K2), o_B = L.off(K2), o_P = L.off(K2);
+    size_t o_F = L.off(K2);
+    size_t o_vec = L.off(sizeof(double) * 4 * c.K);
+    size_t o_scal = L.off(sizeof(double) * SCAL_COUNT);
+    size_t o_coef = L.off(sizeof(double) * (5 * (size_t)c.cheb_cap + 64));
+    size_t o_mom = L.off(sizeof(double) * c.cheb_cap);
+    size_t o_cos = L.off(sizeof(double) * 16 * (size_t)c.cheb_cap);
+    size_t o_wk = L.off(sizeof(double) * 4 * (size_t)c.cheb_cap);
+    size_t o_part = L.off(sizeof(double) * c.part_cap);
+    size_t o_flags = L.off(sizeof(int) * FLAG_COUNT);
+    size_t o_vloc = L.off(G), o_nion = L.off(G), o_vks = L.off(G), o_nout = L.off(G), o_gtmp = L.off(G);
+    size_t o_fr = L.off(sizeof(double) * c.nfft_r);
+    size_t o_gh = L.off(sizeof(double) * c.nfft_c);
+    size_t o_fc = L.off(sizeof(cufftDoubleComplex) * c.nfft_c);
+    size_t o_kw = L.off(sizeof(double) * nkc);
+    size_t o_kc = L.off(sizeof(cufftDoubleComplex) * nkc);
+    if (base) {
+        c.d_fn = (Fn*)(base + o_fn);
+        c.d_tab = (double*)(base + o_tab);
+        c.d_tile_ptr = (int*)(base + o_tp);
+        c.d_tile_fn = (int*)(base + o_tf);
+        c.d_xyz = (double*)(base + o_xyz);
+        c.d_S = (double*)(base + o_S); c.d_T = (double*)(base + o_T); c.d_Linv = (double*)(base + o_Li);
+        c.d_A = (double*)(base + o_A); c.d_H = (double*)(base + o_H);
+        c.d_X0 = (double*)(base + o_X0); c.d_X1 = (double*)(base + o_X1); c.d_rho = (double*)(base + o_rho);
+        c.d_B = (double*)(base + o_B); c.d_P = (double*)(base + o_P); c.d_F = (double*)(base + o_F);
+        c.d_vec = (double*)(base + o_vec);
+        c.d_scal = (double*)(base + o_scal);
+        c.d_coef = (double*)(base + o_coef);
+        c.d_mom = (double*)(base + o_mom);
+        c.d_cos = (double*)(base + o_cos);
+        c.d_wk = (double*)(base + o_wk);
+        c.d_part = (double*)(base + o_part);
+        c.d_flags = (int*)(base + o_flags);
+        c.d_vloc = (double*)(base + o_vloc); c.d_nion = (double*)(base + o_nion);
+        c.d_vks = (double*)(base + o_vks); c.d_nout = (double*)(base + o_nout); c.d_gtmp = (double*)(base + o_gtmp);
+        c.d_fft_r = (double*)(base + o_fr);
+        c.d_ghat = (double*)(base + o_gh);
+        c.d_fft_c = (cufftDoubleComplex*)(base + o_fc);
+        c.d_kerker = (double*)(base + o_kw);
+        c.d_kc = (cufftDoubleComplex*)(base + o_kc);
+    }
+    return L.total;
+}
+
+template <class F>
+dft_status guarded(dft_ctx* ctx, F&& f) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    try {
+        f();
+        if (c) c->err.clear();
+        return DFT_OK;
+    } catch (const Error& e) {
+        if (c) c->err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (c) c->err = "host allocation failed";
+        return DFT_ENOMEM;
+    } catch (...) {
+        if (c) c->err = "internal error";
+        return DFT_EINTERNAL;
+    }
+}
+
+struct Timer {
+    cudaEvent_t ev[9];
+    cudaStream_t s;
+    explicit Timer(cudaStream_t st) : s(st) {
+        for (auto& e : ev) cudaEventCreate(&e);
+    }
+    ~Timer() {
+        for (auto& e : ev) cudaEventDestroy(e);
+    }
+    void mark(int i) { cudaEventRecord(ev[i], s); }
+    float ms(int a, int b) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, ev[a], ev[b]) != cudaSuccess) t = 0.f;
+        return t;
+    }
+};
+
+void read_flags(Ctx& c, cudaStream_t s, int* flags) {
+    DFT_CUDA_CHECK(cudaMemcpyAsync(flags, c.d_flags, sizeof(int) * FLAG_COUNT, cudaMemcpyDeviceToHost, s));
+    DFT_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+// N_C = smallest order whose coefficient tail (at mu = Ebar, the slowest
+// decay) sums below tol (the paper's N_C ~ 2 dE beta is the same order)
+int auto_order(Ctx& c, double emin, double emax, cudaStream_t s) {
+    double de = 0.5 * (emax - emin);
+    long long ntry = (long long)std::ceil(12.0 * c.p.beta * de) + 64;
+    ntry = std::min<long long>(ntry, c.cheb_cap);
+    int M = 4 * (int)ntry;
+    launch_cos_table(M, c.d_cos, s);
+    launch_cheb_coeffs((int)ntry, M, c.d_cos, c.d_scal, c.p.beta, 0.5 * (emax + emin), true, c.d_coef, s);
+    std::vector<double> a(ntry);
+    DFT_CUDA_CHECK(cudaMemcpyAsync(a.data(), c.d_coef, sizeof(double) * ntry, cudaMemcpyDeviceToHost, s));
+    DFT_CUDA_CHECK(cudaStreamSynchronize(s));
+    double tail = 0.0;
+    int nc = (int)ntry;
+    for (long long l = ntry - 1; l >= 0; --l) {
+        tail += std::fabs(a[l]);
+        if (tail >= c.p.cheb_tail_tol) { nc = (int)(l + 1); break; }
+        if (l == 0) nc = 1;
+    }
+    return std::max(nc, 2);
+}
+
+// P = f(S^-1 F) S^-1 through the symmetric Chebyshev recurrence (Supp. B)
+void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cudaStream_t s, Timer* tm,
+                         int t0) {
+    if (!c.have_chol) throw Error(DFT_EINVAL, "call dft_overlap_kinetic first");
+    if (c.p.precision != DFT_PREC_FP64) throw Error(DFT_EUNSUPPORTED, "this build runs the FP64 path only");
+    const int K = c.K;
+    DFT_CUDA_CHECK(cudaMemsetAsync(c.d_flags, 0, sizeof(int) * FLAG_COUNT, s));
+    if (tm) tm->mark(t0);
+    // F~ = L^-1 F L^-T
+    dgemm('N', 'N', K, K, K, 1.0, c.d_Linv, K, F, K, 0.0, c.d_B, K, s);
+    dgemm('N', 'T', K, K, K, 1.0, c.d_B, K, c.d_Linv, K, 0.0, c.d_A, K, s);
+    if (tm) tm->mark(t0 + 1);
+    // spectral bounds of S^-1 F
+    if (c.p.e_max > c.p.e_min) {
+        double b[2] = {c.p.e_min, c.p.e_max};
+        DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_scal + SCAL_EMIN, b, sizeof(b), cudaMemcpyHostToDevice, s));
+    } else {
+        lanczos_bounds(c, c.d_A, c.p.lanczos_steps > 0 ? c.p.lanczos_steps : 64, s);
+    }
+    double eb[2];
+    DFT_CUDA_CHECK(cudaMemcpyAsync(eb, c.d_scal + SCAL_EMIN, sizeof(eb), cudaMemcpyDeviceToHost, s));
+    DFT_CUDA_CHECK(cudaStreamSynchronize(s));
+    if (!(eb[1] > eb[0])) throw Error(DFT_ESPECTRUM, "degenerate spectral bounds");
+    launch_normalise_h(K, c.d_A, c.d_scal, c.d_H, s);
+    int n_c = c.p.cheb_order > 0 ? c.p.cheb_order : auto_order(c, eb[0], eb[1], s);
+    if (n_c < 2 || n_c > c.cheb_cap) throw Error(DFT_EINVAL, "Chebyshev order out of range");
+    const int M = 4 * n_c;
+    launch_cos_table(M, c.d_cos, s);
+    if (tm) tm->mark(t0 + 2);
+    // pass 1: moments m_l = Tr T_l(H_N), l < N_C, by doubling
+    launch_cheb_init(K, c.d_H, c.d_X0, c.d_X1, nullptr, nullptr, s);
+    double m0 = (double)K;
+    DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_mom, &m0, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_trace(K, c.d_H, c.d_mom + 1, s);
+    launch_frob_dot((long long)K * K, c.d_H, c.d_H, c.d_part, c.d_scal + SCAL_TRACE, s);
+    DFT_CUDA_CHECK(cudaMemsetAsync(c.d_scal + SCAL_TRACE + 1, 0, sizeof(double), s));
+    if (n_c > 2) launch_moment_reduce(1, c.d_scal + SCAL_TRACE, c.d_mom, 2, -1, m0, c.d_mom + 1, s);
+    int nparts = cheb_step_parts(K);
+    double* cur = c.d_X1;
+    double* prev = c.d_X0;
+    for (int j = 1; 2 * j + 1 <= n_c - 1; ++j) {
+        launch_cheb_step_fp64(K, c.d_H, cur, prev, nullptr, nullptr, 0, c.d_part, c.d_flags, s);
+        launch_moment_reduce(nparts, c.d_part, c.d_mom, (2 * j + 2 < n_c) ? 2 * j + 2 : -1, 2 * j + 1, m0,
+                             c.d_mom + 1, s);
+        std::swap(cur, prev);
+    }
+    // mu from 2 sum_l a_l(mu) m_l = N_e (Eq. 2.8), then the coefficients
+    launch_moment_weights(n_c, M, c.d_cos, c.d_mom, c.d_wk, s);
+    launch_mu_bisect(M, c.d_cos, c.d_wk, c.p.beta, c.p.n_electrons, c.d_scal, c.d_flags, s);
+    launch_cheb_coeffs(n_c, M, c.d_cos, c.d_scal, c.p.beta, 0.0, false, c.d_coef, s);
+    if (tm) tm->mark(t0 + 3);
+    // pass 2: rho = sum_l a_l X_l
+    launch_cheb_init(K, c.d_H, c.d_X0, c.d_X1, c.d_rho, c.d_coef, s);
+    cur = c.d_X1;
+    prev = c.d_X0;
+    for (int l = 2; l < n_c; ++l) {
+        launch_cheb_step_fp64(K, c.d_H, cur, prev, c.d_rho, c.d_coef, l, nullptr, c.d_flags, s);
+        std::swap(cur, prev);
+    }
+    if (tm) tm->mark(t0 + 4);
+    // P = L^-T rho L^-1
+    dgemm('T', 'N', K, K, K, 1.0, c.d_Linv, K, c.d_rho, K, 0.0, c.d_B, K, s);
+    dgemm('N', 'N', K, K, K, 1.0, c.d_B, K, c.d_Linv, K, 0.0, P, K, s);
+    if (tm) tm->mark(t0 + 5);
+    launch_frob_dot((long long)K * K, P, c.d_S, c.d_part, c.d_scal + SCAL_NE, s);
+    int flags[FLAG_COUNT];
+    read_flags(c, s, flags);
+    double sc[2];
+    DFT_CUDA_CHECK(cudaMemcpy(sc, c.d_scal + SCAL_MU, sizeof(double), cudaMemcpyDeviceToHost));
+    DFT_CUDA_CHECK(cudaMemcpy(sc + 1, c.d_scal + SCAL_NE, sizeof(double), cudaMemcpyDeviceToHost));
+    if (info) {
+        info->mu = sc[0];
+        info->e_min = eb[0];
+        info->e_max = eb[1];
+        info->n_e_trace = 2.0 * sc[1];
+        info->n_cheb = n_c;
+        info->spectrum_ok = flags[FLAG_SPECTRUM] ? 0 : 1;
+    }
+    if (flags[FLAG_SPECTRUM]) throw Error(DFT_ESPECTRUM, "Chebyshev iterates left [-1, 1]: spectral bounds too tight");
+    if (flags[FLAG_MU]) throw Error(DFT_ENOTCONV, "mu bisection: the bracket does not contain N_e");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dft_version(void) { return kVersion; }
+
+unsigned long long dft_kernel_launches(void) { return g_launches; }
+
+size_t dft_workspace_bytes(const dft_basis_desc* basis, const dft_grid_desc* grid, const dft_params* params) {
+    try {
+        validate(basis, grid, params);
+        Ctx c;
+        build_basis(c, basis, grid, params, nullptr, nullptr);
+        return carve(c, nullptr);
+    } catch (...) {
+        return 0;
+    }
+}
+
+dft_status dft_init_basis(dft_ctx** ctx, const dft_basis_desc* basis, const dft_grid_desc* grid,
+                          const dft_params* params, void* workspace, size_t ws_bytes, void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    *ctx = nullptr;
+    Ctx* c = new (std::nothrow) Ctx();
+    if (!c) return DFT_ENOMEM;
+    dft_status st = guarded(reinterpret_cast<dft_ctx*>(c), [&] {
+        validate(basis, grid, params);
+        if (!workspace) throw Error(DFT_EINVAL, "null workspace");
+        if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) throw Error(DFT_EINVAL, "workspace must be 256-byte aligned");
+        std::vector<int> tp, tf;
+        build_basis(*c, basis, grid, params, &tp, &tf);
+        size_t need = carve(*c, nullptr);
+        if (ws_bytes < need) throw Error(DFT_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
+        carve(*c, static_cast<char*>(workspace));
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_fn, c->fn_host.data(), sizeof(Fn) * c->K, cudaMemcpyHostToDevice, s));
+        DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_tile_ptr, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice, s));
+        if (!tf.empty())
+            DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_tile_fn, tf.data(), sizeof(int) * tf.size(), cudaMemcpyHostToDevice, s));
+        DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_xyz, c->xyz_host.data(), sizeof(double) * c->xyz_host.size(),
+                                       cudaMemcpyHostToDevice, s));
+        DFT_CUDA_CHECK(cudaMemsetAsync(c->d_scal, 0, sizeof(double) * SCAL_COUNT, s));
+        DFT_CUDA_CHECK(cudaMemsetAsync(c->d_flags, 0, sizeof(int) * FLAG_COUNT, s));
+        launch_build_tables(*c, s);
+        launch_gaussian_sum(*c, -c->p.vloc_depth, c->p.vloc_width, c->d_vloc, s);
+        double w = c->p.vloc_width;
+        launch_gaussian_sum(*c, c->p.ion_charge * std::pow(M_PI * w * w, -1.5), w, c->d_nion, s);
+        poisson_setup(*c, s);
+        if (c->p.mixer == DFT_MIX_KERKER) kerker_setup(*c, s);
+        DFT_CUDA_CHECK(cudaStreamSynchronize(s));
+    });
+    if (st != DFT_OK) {
+        // keep the context so the caller can read the message, but mark it unusable
+        c->K = 0;
+        *ctx = reinterpret_cast<dft_ctx*>(c);
+        return st;
+    }
+    *ctx = reinterpret_cast<dft_ctx*>(c);
+    return DFT_OK;
+}
+
+dft_status dft_overlap_kinetic(dft_ctx* ctx, double* S, double* T, void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0) throw Error(DFT_EINVAL, "context not initialised");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        size_t K2 = sizeof(double) * (size_t)c.K * c.K;
+        launch_overlap_kinetic(c, c.d_S, c.d_T, s);
+        if (S) DFT_CUDA_CHECK(cudaMemcpyAsync(S, c.d_S, K2, cudaMemcpyDeviceToDevice, s));
+        if (T) DFT_CUDA_CHECK(cudaMemcpyAsync(T, c.d_T, K2, cudaMemcpyDeviceToDevice, s));
+        DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_A, c.d_S, K2, cudaMemcpyDeviceToDevice, s));
+        DFT_CUDA_CHECK(cudaMemsetAsync(c.d_flags, 0, sizeof(int) * FLAG_COUNT, s));
+        cholesky_inplace(c.d_A, c.K, c.d_flags + FLAG_CHOL, s);
+        tri_inverse_lower(c.d_A, c.d_Linv, c.K, s);
+        int flags[FLAG_COUNT];
+        read_flags(c, s, flags);
+        if (flags[FLAG_CHOL]) throw Error(DFT_ENOTCONV, "overlap matrix is not positive definite");
+        c.have_chol = true;
+    });
+}
+
+dft_status dft_density_matrix(dft_ctx* ctx, const double* F, double* P, dft_info* info, void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0 || !F || !P) throw Error(DFT_EINVAL, "null argument");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        Timer tm(s);
+        density_matrix_impl(c, F, P, info, s, &tm, 0);
+        if (info) {
+            std::memset(info->ms_stage, 0, sizeof(info->ms_stage));
+            for (int i = 0; i < 5; ++i) info->ms_stage[1 + i] = tm.ms(i, i + 1);
+        }
+    });
+}
+
+dft_status dft_density_on_grid(dft_ctx* ctx, const double* P, double* n_grid, void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0 || !P || !n_grid) throw Error(DFT_EINVAL, "null argument");
+        launch_collocate_fp64(c, P, n_grid, static_cast<cudaStream_t>(stream));
+    });
+}
+
+dft_status dft_potential_matrix(dft_ctx* ctx, const double* v_grid, double* V, void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0 || !v_grid || !V) throw Error(DFT_EINVAL, "null argument");
+        launch_quadrature_fp64(c, v_grid, V, static_cast<cudaStream_t>(stream));
+    });
+}
+
+dft_status dft_hartree_xc(dft_ctx* ctx, const double* n_grid, double* v_ks, double* energies, void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0 || !n_grid) throw Error(DFT_EINVAL, "null argument");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        hartree_xc(c, n_grid, v_ks, energies != nullptr, s);
+        if (energies) {
+            DFT_CUDA_CHECK(cudaMemcpyAsync(energies, c.d_scal + SCAL_E0, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            DFT_CUDA_CHECK(cudaStreamSynchronize(s));
+        }
+    });
+}
+
+dft_status dft_initial_density(dft_ctx* ctx, double* n_grid, void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0 || !n_grid) throw Error(DFT_EINVAL, "null argument");
+        double w = c.p.vloc_width;
+        launch_gaussian_sum(c, c.p.ion_charge * std::pow(M_PI * w * w, -1.5), w, n_grid,
+                            static_cast<cudaStream_t>(stream));
+    });
+}
+
+dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double* P_out, dft_info* info,
+                        void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0 || !n_in_out) throw Error(DFT_EINVAL, "null argument");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int K = c.K;
+        Timer tm(s);
+        dft_info loc{};
+        tm.mark(0);
+        // v_KS[n_in] -> V^KS -> F = T + V^KS
+        hartree_xc(c, n_in_out, c.d_vks, false, s);
+        launch_quadrature_fp64(c, c.d_vks, c.d_F, s);
+        launch_axpby_mat(K, 1.0, c.d_T, 1.0, c.d_F, c.d_F, s);
+        tm.mark(1);
+        // P, then n_out
+        density_matrix_impl(c, c.d_F, c.d_P, &loc, s, &tm, 1);
+        tm.mark(7);
+        launch_collocate_fp64(c, c.d_P, c.d_nout, s);
+        tm.mark(8);
+        // energy of n_out
+        hartree_xc(c, c.d_nout, nullptr, true, s);
+        launch_frob_dot((long long)K * K, c.d_P, c.d_T, c.d_part, c.d_scal + SCAL_EKIN, s);
+        launch_maxabs_diff(c.ng, c.d_nout, n_in_out, c.d_part, c.d_scal + SCAL_RES, s);
+        if (v_ks_out) DFT_CUDA_CHECK(cudaMemcpyAsync(v_ks_out, c.d_vks, sizeof(double) * c.ng, cudaMemcpyDeviceToDevice, s));
+        if (P_out) DFT_CUDA_CHECK(cudaMemcpyAsync(P_out, c.d_P, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
+        // mixing
+        if (c.p.mixer == DFT_MIX_KERKER) kerker_mix(c, n_in_out, c.d_nout, c.p.mix_alpha, s);
+        else launch_linear_mix(c.ng, n_in_out, c.d_nout, c.p.mix_alpha, s);
+        double sc[SCAL_COUNT];
+        DFT_CUDA_CHECK(cudaMemcpyAsync(sc, c.d_scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
+        DFT_CUDA_CHECK(cudaStreamSynchronize(s));
+        loc.e_kin = 2.0 * sc[SCAL_EKIN];
+        loc.e_loc = sc[SCAL_E0];
+        loc.e_hartree = sc[SCAL_E1];
+        loc.e_xc = sc[SCAL_E2];
+        loc.e_total = loc.e_kin + loc.e_loc + loc.e_hartree + loc.e_xc;
+        loc.residual = sc[SCAL_RES];
+        loc.de_per_atom = c.have_prev ? (loc.e_total - c.e_prev) / c.n_atoms : 0.0;
+        c.e_prev = loc.e_total;
+        c.have_prev = true;
+        loc.iter = ++c.iter;
+        // stage times: quadrature, transform, Lanczos, moments, Chebyshev, back-transform, collocation
+        loc.ms_stage[0] = tm.ms(0, 1);
+        for (int i = 1; i < 6; ++i) loc.ms_stage[i] = tm.ms(i, i + 1);
+        loc.ms_stage[6] = tm.ms(7, 8);
+        loc.ms_stage[7] = 0.f;
+        if (info) *info = loc;
+    });
+}
+
+dft_status dft_destroy(dft_ctx* ctx) {
+    if (!ctx) return DFT_OK;
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (c->plan_f) cufftDestroy(c->plan_f);
+    if (c->plan_b) cufftDestroy(c->plan_b);
+    if (c->kplan_f) cufftDestroy(c->kplan_f);
+    if (c->kplan_b) cufftDestroy(c->kplan_b);
+    delete c;
+    return DFT_OK;
+}
+
+const char* dft_last_error(const dft_ctx* ctx) {
+    if (!ctx) return "null context";
+    return reinterpret_cast<const Ctx*>(ctx)->err.c_str();
+}
+
+}  // extern "C"

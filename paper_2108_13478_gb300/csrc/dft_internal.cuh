@@ -1,0 +1,180 @@
+// Internal declarations of libdft: the context, the workspace layout and the
+// kernel launchers shared by the translation units.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/dft.h"
+
+namespace dft {
+
+// grid tile edge (points per axis) used by collocation and quadrature
+constexpr int TILE = 8;
+constexpr int TILE_PTS = TILE * TILE * TILE;
+// functions per chunk staged in shared memory
+constexpr int FCH = 32;
+
+// one basis function (a Cartesian primitive), device layout
+struct Fn {
+    double cx, cy, cz;   // centre
+    double zeta;
+    double norm;
+    int px, py, pz;      // Cartesian powers
+    int lo[3], hi[3];    // window index range per axis (inclusive, clipped)
+    int pad;
+};
+
+struct Ctx {
+    // problem
+    int K = 0, n_atoms = 0;
+    int n[3] = {0, 0, 0};
+    long long ng = 0;
+    double origin[3] = {0, 0, 0}, h = 0;
+    dft_params p{};
+    std::vector<Fn> fn_host;
+    std::vector<double> xyz_host;
+    int tab_w = 0;               // table width per function and axis
+    int ntile[3] = {0, 0, 0};
+    long long n_tiles = 0, tile_nnz = 0;
+    int tile_max = 0;
+    int Nfft[3] = {0, 0, 0};     // padded FFT sizes (x, y, z)
+    long long nfft_r = 0, nfft_c = 0;
+
+    // device buffers (carved from the caller's workspace)
+    Fn* d_fn = nullptr;
+    double* d_tab = nullptr;     // [K][3][tab_w]
+    int* d_tile_ptr = nullptr;   // [n_tiles + 1]
+    int* d_tile_fn = nullptr;    // [tile_nnz]
+    double* d_xyz = nullptr;     // [n_atoms * 3]
+    double* d_S = nullptr;       // K x K
+    double* d_T = nullptr;
+    double* d_Linv = nullptr;
+    double* d_A = nullptr;       // K x K scratch (Fock / transformed Fock)
+    double* d_H = nullptr;       // normalised Hamiltonian H_N
+    double* d_X0 = nullptr;
+    double* d_X1 = nullptr;
+    double* d_rho = nullptr;
+    double* d_B = nullptr;       // K x K scratch
+    double* d_P = nullptr;       // K x K density matrix of the last SCF step
+    double* d_F = nullptr;       // K x K Fock matrix of the SCF step
+    double* d_vec = nullptr;     // Lanczos vectors, 4 x K
+    double* d_scal = nullptr;    // device scalars (see SCAL_* below)
+    double* d_coef = nullptr;    // Chebyshev coefficients [cheb_cap]
+    double* d_mom = nullptr;     // moments [cheb_cap]
+    double* d_cos = nullptr;     // cos(pi j / 2M), j < 4M, M = 4 cheb_cap
+    double* d_wk = nullptr;      // [M]
+    double* d_part = nullptr;    // reduction partials [part_cap]
+    int* d_flags = nullptr;      // device status flags [8]
+    double* d_vloc = nullptr;    // grids [ng]
+    double* d_nion = nullptr;
+    double* d_vks = nullptr;
+    double* d_nout = nullptr;
+    double* d_gtmp = nullptr;
+    double* d_fft_r = nullptr;   // [nfft_r]
+    double* d_ghat = nullptr;    // [nfft_c] real spectrum of the Coulomb kernel
+    cufftDoubleComplex* d_fft_c = nullptr;  // [nfft_c]
+    double* d_kerker = nullptr;  // Kerker weights on the unpadded box [nz][ny][nx/2+1]
+    cufftDoubleComplex* d_kc = nullptr;
+
+    int cheb_cap = 0;            // capacity of coefficient arrays
+    long long part_cap = 0;
+
+    cufftHandle plan_f = 0, plan_b = 0;
+    cufftHandle kplan_f = 0, kplan_b = 0;
+    bool have_chol = false;
+    double e_prev = 0;
+    bool have_prev = false;
+    int iter = 0;
+    std::string err;
+};
+
+// indices into d_scal
+enum {
+    SCAL_ALPHA = 0,      // Lanczos alpha_j at SCAL_ALPHA + j (j < 128)
+    SCAL_BETA = 128,     // Lanczos beta_j
+    SCAL_MU = 256,
+    SCAL_EMIN, SCAL_EMAX, SCAL_NE, SCAL_TRACE, SCAL_EKIN, SCAL_RES,
+    SCAL_E0, SCAL_E1, SCAL_E2,        // grid energy terms
+    SCAL_COUNT = 300
+};
+enum { FLAG_SPECTRUM = 0, FLAG_CHOL = 1, FLAG_MU = 2, FLAG_COUNT = 8 };
+
+// ---- grid kernels (k_grid.cu) ----
+void launch_build_tables(const Ctx& c, cudaStream_t s);
+void launch_collocate_fp64(const Ctx& c, const double* P, double* n, cudaStream_t s);
+void launch_quadrature_fp64(const Ctx& c, const double* v, double* V, cudaStream_t s);
+void launch_gaussian_sum(const Ctx& c, double amp, double width, double* out, cudaStream_t s);
+
+// ---- dense FP64 linear algebra (k_linalg.cu) ----
+// C[M x N] = alpha op(A) op(B) + beta C, row-major, op = 'N' or 'T'
+void dgemm(char ta, char tb, int M, int N, int Kd, double alpha, const double* A, int lda,
+           const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s);
+int cholesky_inplace(double* A, int K, int* d_flag, cudaStream_t s);   // lower L, upper zeroed
+void tri_inverse_lower(const double* L, double* Linv, int K, cudaStream_t s);
+void launch_overlap_kinetic(const Ctx& c, double* S, double* T, cudaStream_t s);
+void launch_axpby_mat(int K, double a, const double* X, double b, const double* Y, double* Z,
+                      cudaStream_t s);   // Z = a X + b Y
+void launch_normalise_h(int K, const double* Ft, const double* scal, double* H, cudaStream_t s);
+void launch_frob_dot(long long n, const double* X, const double* Y, double* part, double* out,
+                     cudaStream_t s);    // out = sum X*Y (deterministic)
+void launch_trace(int K, const double* X, double* out, cudaStream_t s);
+void launch_identity(int K, double* X, cudaStream_t s);
+// Lanczos on symmetric A: writes padded bounds to scal[SCAL_EMIN], scal[SCAL_EMAX]
+void lanczos_bounds(const Ctx& c, const double* A, int steps, cudaStream_t s);
+
+// ---- Chebyshev engine (k_cheb.cu) ----
+void launch_cos_table(int M, double* cos_tab, cudaStream_t s);
+void launch_cheb_coeffs(int n_c, int M, const double* cos_tab, const double* scal, double beta,
+                        double mu_override, bool use_override, double* coef, cudaStream_t s);
+void launch_moment_weights(int n_c, int M, const double* cos_tab, const double* mom, double* wk,
+                           cudaStream_t s);
+void launch_mu_bisect(int M, const double* cos_tab, const double* wk, double beta, double n_e,
+                      double* scal, int* flags, cudaStream_t s);
+void launch_cheb_init(int K, const double* H, double* X0, double* X1, double* rho,
+                      const double* coef, cudaStream_t s);
+// X_next (written over Xprev) = 2 H Xcur - Xprev; rho += coef[l] X_next (if rho);
+// moment partials (if part): <Xn, Xn>, <Xn, Xcur>
+void launch_cheb_step_fp64(int K, const double* H, const double* Xcur, double* Xprev, double* rho,
+                           const double* coef, int l, double* part, int* flags, cudaStream_t s);
+int cheb_step_parts(int K);
+void launch_moment_reduce(int nparts, const double* part, double* mom, int idx_even, int idx_odd,
+                          double m0, const double* m1, cudaStream_t s);
+
+// ---- Poisson + LDA (k_poisson.cu) ----
+void poisson_setup(Ctx& c, cudaStream_t s);
+void hartree_xc(Ctx& c, const double* n, double* vks, bool energies, cudaStream_t s);
+void kerker_setup(Ctx& c, cudaStream_t s);
+void kerker_mix(Ctx& c, double* n_in, const double* n_out, double alpha, cudaStream_t s);
+void launch_linear_mix(long long ng, double* n_in, const double* n_out, double alpha, cudaStream_t s);
+void launch_maxabs_diff(long long ng, const double* a, const double* b, double* part, double* out,
+                        cudaStream_t s);
+
+int fft_size(int n);
+
+}  // namespace dft
+
+#define DFT_CUDA_CHECK(call)                                                        \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) throw dft::Error(DFT_ECUDA, std::string(#call) + ": " + \
+                                                cudaGetErrorString(e_));            \
+    } while (0)
+
+namespace dft {
+struct Error {
+    dft_status code;
+    std::string msg;
+    Error(dft_status c, std::string m) : code(c), msg(std::move(m)) {}
+};
+// process-wide count of kernels this library has launched (diagnostics)
+extern unsigned long long g_launches;
+inline void check_launch(const char* what, int kernels = 1) {
+    g_launches += (unsigned long long)kernels;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error(DFT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+}  // namespace dft

@@ -1,0 +1,237 @@
+// Grid <-> basis kernels: separable tables (Supp. A.1), collocation of the
+// density (Eq. 2.7, Supp. A.1.2) and quadrature of a grid potential into a
+// matrix (Eq. 2.5 / A.6), plus Gaussian sums on the grid (v_loc, Eq. 2.6).
+//
+// Work is organised by grid tiles of 8x8x8 points.  Every tile carries the
+// list of basis functions whose cubic window W_a (Supp. A.1.1) meets it;
+// the per-tile slices of the 1D tables are staged in shared memory so that
+// phi_a(r_g) costs two multiplications (Supp. A.1).
+#include "dft_internal.cuh"
+
+namespace dft {
+namespace {
+
+__global__ void k_build_tables(const Fn* __restrict__ fn, int K, int W, double ox, double oy,
+                               double oz, double h, double* __restrict__ tab) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long total = (long long)K * 3 * W;
+    if (idx >= total) return;
+    int t = (int)(idx % W);
+    int d = (int)((idx / W) % 3);
+    int f = (int)(idx / (3LL * W));
+    const Fn F = fn[f];
+    int i = F.lo[d] + t;
+    double val = 0.0;
+    if (i <= F.hi[d]) {
+        double o = d == 0 ? ox : (d == 1 ? oy : oz);
+        double c = d == 0 ? F.cx : (d == 1 ? F.cy : F.cz);
+        int pw = d == 0 ? F.px : (d == 1 ? F.py : F.pz);
+        double x = (o + h * i) - c;
+        val = exp(-F.zeta * x * x);
+        if (pw == 1) val *= x;
+        if (d == 0) val *= F.norm;
+    }
+    tab[idx] = val;
+}
+
+// stage the 8-point slices of FCH functions' tables for the tile at t0
+__device__ __forceinline__ void stage_slices(const Fn* __restrict__ fn, const double* __restrict__ tab,
+                                             int W, const int* __restrict__ list, int n_t, int c0,
+                                             const int t0[3], double (*sx)[TILE], double (*sy)[TILE],
+                                             double (*sz)[TILE]) {
+    for (int e = threadIdx.x; e < FCH * 3 * TILE; e += blockDim.x) {
+        int fl = e / (3 * TILE);
+        int d = (e / TILE) % 3;
+        int q = e % TILE;
+        double val = 0.0;
+        if (c0 + fl < n_t) {
+            int f = list[c0 + fl];
+            int i = t0[d] + q;
+            int lo = fn[f].lo[d], hi = fn[f].hi[d];
+            if (i >= lo && i <= hi) val = tab[((long long)f * 3 + d) * W + (i - lo)];
+        }
+        if (d == 0) sx[fl][q] = val;
+        else if (d == 1) sy[fl][q] = val;
+        else sz[fl][q] = val;
+    }
+}
+
+// n(r_g) = sum_a 2 phi_a(r_g) sum_b phi_b(r_g) P_ba for the points of one tile
+// (Eq. A.5 summed over the columns a).  256 threads, 2 points each.
+__global__ void __launch_bounds__(256) k_collocate_fp64(
+    const Fn* __restrict__ fn, const double* __restrict__ tab, int W, const int* __restrict__ tile_ptr,
+    const int* __restrict__ tile_fn, int ntx, int nty, int nx, int ny, int nz, int K,
+    const double* __restrict__ P, double* __restrict__ n_out) {
+    __shared__ double sxa[FCH][TILE], sya[FCH][TILE], sza[FCH][TILE];
+    __shared__ double sxb[FCH][TILE], syb[FCH][TILE], szb[FCH][TILE];
+    __shared__ double sP[FCH][FCH];
+    const int t = blockIdx.x;
+    const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
+    const int t0[3] = {tx * TILE, ty * TILE, tz * TILE};
+    const int* list = tile_fn + tile_ptr[t];
+    const int n_t = tile_ptr[t + 1] - tile_ptr[t];
+    const int px = threadIdx.x & 7, py = (threadIdx.x >> 3) & 7, pz0 = threadIdx.x >> 6, pz1 = pz0 + 4;
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int ca = 0; ca < n_t; ca += FCH) {
+        double y0[FCH], y1[FCH];
+#pragma unroll
+        for (int j = 0; j < FCH; ++j) { y0[j] = 0.0; y1[j] = 0.0; }
+        for (int cb = 0; cb < n_t; cb += FCH) {
+            __syncthreads();
+            stage_slices(fn, tab, W, list, n_t, cb, t0, sxb, syb, szb);
+            for (int e = threadIdx.x; e < FCH * FCH; e += blockDim.x) {
+                int i = e / FCH, j = e % FCH;
+                double v = 0.0;
+                if (cb + i < n_t && ca + j < n_t) v = P[(long long)list[cb + i] * K + list[ca + j]];
+                sP[i][j] = v;
+            }
+            __syncthreads();
+#pragma unroll 2
+            for (int i = 0; i < FCH; ++i) {
+                double pxy = sxb[i][px] * syb[i][py];
+                double pb0 = pxy * szb[i][pz0];
+                double pb1 = pxy * szb[i][pz1];
+#pragma unroll
+                for (int j = 0; j < FCH; ++j) {
+                    double pv = sP[i][j];
+                    y0[j] = fma(pb0, pv, y0[j]);
+                    y1[j] = fma(pb1, pv, y1[j]);
+                }
+            }
+        }
+        __syncthreads();
+        stage_slices(fn, tab, W, list, n_t, ca, t0, sxa, sya, sza);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < FCH; ++j) {
+            double pxy = sxa[j][px] * sya[j][py];
+            acc0 = fma(pxy * sza[j][pz0], y0[j], acc0);
+            acc1 = fma(pxy * sza[j][pz1], y1[j], acc1);
+        }
+    }
+    int gx = t0[0] + px, gy = t0[1] + py;
+    if (gx < nx && gy < ny) {
+        int gz0 = t0[2] + pz0, gz1 = t0[2] + pz1;
+        if (gz0 < nz) n_out[((long long)gz0 * ny + gy) * nx + gx] = 2.0 * acc0;
+        if (gz1 < nz) n_out[((long long)gz1 * ny + gy) * nx + gx] = 2.0 * acc1;
+    }
+}
+
+// V_ab += h^3 sum_{g in tile} phi_a v phi_b for all pairs of the tile's list
+// (Eq. A.6).  Chunk pairs (ca <= cb); the off-diagonal chunk blocks are
+// mirrored.  Contributions of different tiles meet through FP64 atomics.
+constexpr int QPTS = 64;
+__global__ void __launch_bounds__(256) k_quadrature_fp64(
+    const Fn* __restrict__ fn, const double* __restrict__ tab, int W, const int* __restrict__ tile_ptr,
+    const int* __restrict__ tile_fn, int ntx, int nty, int nx, int ny, int nz, int K, double h3,
+    const double* __restrict__ v, double* __restrict__ V) {
+    __shared__ double sxa[FCH][TILE], sya[FCH][TILE], sza[FCH][TILE];
+    __shared__ double sxb[FCH][TILE], syb[FCH][TILE], szb[FCH][TILE];
+    __shared__ double sv[TILE_PTS];
+    __shared__ double pa[QPTS][FCH + 1], pb[QPTS][FCH + 1];
+    const int t = blockIdx.x;
+    const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
+    const int t0[3] = {tx * TILE, ty * TILE, tz * TILE};
+    const int* list = tile_fn + tile_ptr[t];
+    const int n_t = tile_ptr[t + 1] - tile_ptr[t];
+    if (n_t == 0) return;
+    for (int p = threadIdx.x; p < TILE_PTS; p += blockDim.x) {
+        int gx = t0[0] + (p & 7), gy = t0[1] + ((p >> 3) & 7), gz = t0[2] + (p >> 6);
+        sv[p] = (gx < nx && gy < ny && gz < nz) ? v[((long long)gz * ny + gy) * nx + gx] : 0.0;
+    }
+    const int a = threadIdx.x & 31;
+    const int b0 = (threadIdx.x >> 5) * 4;
+    for (int ca = 0; ca < n_t; ca += FCH) {
+        __syncthreads();
+        stage_slices(fn, tab, W, list, n_t, ca, t0, sxa, sya, sza);
+        for (int cb = ca; cb < n_t; cb += FCH) {
+            __syncthreads();
+            stage_slices(fn, tab, W, list, n_t, cb, t0, sxb, syb, szb);
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int p0 = 0; p0 < TILE_PTS; p0 += QPTS) {
+                __syncthreads();
+                for (int e = threadIdx.x; e < QPTS * FCH; e += blockDim.x) {
+                    int pp = e / FCH, f = e % FCH;
+                    int p = p0 + pp;
+                    int x = p & 7, y = (p >> 3) & 7, z = p >> 6;
+                    pa[pp][f] = sxa[f][x] * sya[f][y] * sza[f][z];
+                    pb[pp][f] = sxb[f][x] * syb[f][y] * szb[f][z] * sv[p];
+                }
+                __syncthreads();
+#pragma unroll 4
+                for (int pp = 0; pp < QPTS; ++pp) {
+                    double va = pa[pp][a];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] = fma(va, pb[pp][b0 + q], acc[q]);
+                }
+            }
+            if (ca + a < n_t) {
+                int fa = list[ca + a];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (cb + b0 + q < n_t) {
+                        int fb = list[cb + b0 + q];
+                        double val = h3 * acc[q];
+                        atomicAdd(&V[(long long)fa * K + fb], val);
+                        if (ca != cb) atomicAdd(&V[(long long)fb * K + fa], val);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// out(r_g) = sum_C amp exp(-|r_g - R_C|^2 / w^2), terms below 1e-30 |amp| dropped
+__global__ void k_gaussian_sum(const double* __restrict__ xyz, int n_atoms, int nx, int ny, int nz,
+                               double ox, double oy, double oz, double h, double amp, double inv_w2,
+                               double rc, double* __restrict__ out) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long ng = (long long)nx * ny * nz;
+    if (g >= ng) return;
+    int ix = (int)(g % nx), iy = (int)((g / nx) % ny), iz = (int)(g / ((long long)nx * ny));
+    double x = ox + h * ix, y = oy + h * iy, z = oz + h * iz;
+    double s = 0.0;
+    for (int a = 0; a < n_atoms; ++a) {
+        double dx = x - xyz[3 * a], dy = y - xyz[3 * a + 1], dz = z - xyz[3 * a + 2];
+        if (fabs(dx) > rc || fabs(dy) > rc || fabs(dz) > rc) continue;
+        s += exp(-dx * dx * inv_w2) * exp(-dy * dy * inv_w2) * exp(-dz * dz * inv_w2);
+    }
+    out[g] = amp * s;
+}
+
+}  // namespace
+
+void launch_build_tables(const Ctx& c, cudaStream_t s) {
+    long long total = (long long)c.K * 3 * c.tab_w;
+    int bs = 256;
+    k_build_tables<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(c.d_fn, c.K, c.tab_w, c.origin[0],
+                                                                    c.origin[1], c.origin[2], c.h, c.d_tab);
+    check_launch("build_tables");
+}
+
+void launch_collocate_fp64(const Ctx& c, const double* P, double* n, cudaStream_t s) {
+    k_collocate_fp64<<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
+                                                         c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K,
+                                                         P, n);
+    check_launch("collocate_fp64");
+}
+
+void launch_quadrature_fp64(const Ctx& c, const double* v, double* V, cudaStream_t s) {
+    DFT_CUDA_CHECK(cudaMemsetAsync(V, 0, sizeof(double) * (size_t)c.K * c.K, s));
+    k_quadrature_fp64<<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
+                                                          c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K,
+                                                          c.h * c.h * c.h, v, V);
+    check_launch("quadrature_fp64");
+}
+
+void launch_gaussian_sum(const Ctx& c, double amp, double width, double* out, cudaStream_t s) {
+    // exp(-r^2/w^2) < 1e-30 beyond r = w sqrt(69.1)
+    double rc = width * 8.32;
+    int bs = 256;
+    k_gaussian_sum<<<(unsigned)((c.ng + bs - 1) / bs), bs, 0, s>>>(c.d_xyz, c.n_atoms, c.n[0], c.n[1], c.n[2],
+                                                                  c.origin[0], c.origin[1], c.origin[2], c.h,
+                                                                  amp, 1.0 / (width * width), rc, out);
+    check_launch("gaussian_sum");
+}
+
+}  // namespace dft

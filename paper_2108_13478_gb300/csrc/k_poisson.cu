@@ -1,0 +1,255 @@
+// Kohn-Sham potential on the grid (Eq. 2.6): free-space Hartree potential
+// by zero-padded FFT convolution with the Coulomb kernel (the paper uses a
+// reciprocal-space method for isolated systems, Section 2), LDA (Slater)
+// exchange fused into the pointwise epilogue, and the density mixing of the
+// SCF cycle (Supp. A.3).
+#include "dft_internal.cuh"
+
+#include <cmath>
+
+namespace dft {
+
+int fft_size(int n) {
+    for (int m = n;; ++m) {
+        int k = m;
+        for (int p : {2, 3, 5, 7})
+            while (k % p == 0) k /= p;
+        if (k == 1) return m;
+    }
+}
+
+namespace {
+
+template <int BS>
+__device__ double block_sum(double v) {
+    __shared__ double red[BS / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = threadIdx.x < BS / 32 ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Coulomb kernel on the padded grid with minimum-image offsets; G(0) is the
+// cube average of 1/r: (3 ln(2 + sqrt 3) - pi/2) / h
+__global__ void k_coulomb_kernel(int Nx, int Ny, int Nz, double h, double* G) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long n = (long long)Nx * Ny * Nz;
+    if (e >= n) return;
+    int ix = (int)(e % Nx), iy = (int)((e / Nx) % Ny), iz = (int)(e / ((long long)Nx * Ny));
+    double x = min(ix, Nx - ix), y = min(iy, Ny - iy), z = min(iz, Nz - iz);
+    double r2 = x * x + y * y + z * z;
+    const double c0 = 3.0 * log(2.0 + sqrt(3.0)) - 0.5 * M_PI;
+    G[e] = r2 > 0.0 ? 1.0 / (h * sqrt(r2)) : c0 / h;
+}
+
+__global__ void k_take_real(long long n, const cufftDoubleComplex* c, double scale, double* r) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) r[e] = c[e].x * scale;
+}
+
+// padded[z][y][x] = n - n_ion inside the box, 0 outside
+__global__ void k_pad(int nx, int ny, int nz, int Nx, int Ny, int Nz, const double* __restrict__ n,
+                      const double* __restrict__ nion, double* __restrict__ out) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long tot = (long long)Nx * Ny * Nz;
+    if (e >= tot) return;
+    int ix = (int)(e % Nx), iy = (int)((e / Nx) % Ny), iz = (int)(e / ((long long)Nx * Ny));
+    double v = 0.0;
+    if (ix < nx && iy < ny && iz < nz) {
+        long long g = ((long long)iz * ny + iy) * nx + ix;
+        v = n[g] - (nion ? nion[g] : 0.0);
+    }
+    out[e] = v;
+}
+
+__global__ void k_mul_real(long long n, cufftDoubleComplex* c, const double* __restrict__ w) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) {
+        double s = w[e];
+        c[e].x *= s;
+        c[e].y *= s;
+    }
+}
+
+constexpr double CX = 0.98474502184269641;   // (3/pi)^(1/3)
+
+// v_ks = v_loc + v_H + v_x; energy partials sum v_loc n, v_H rho, eps_x n
+__global__ void __launch_bounds__(256) k_vks(int nx, int ny, int nz, int Nx, int Ny, const double* __restrict__ pad,
+                                             const double* __restrict__ n, const double* __restrict__ nion,
+                                             const double* __restrict__ vloc, double* __restrict__ vks,
+                                             double* __restrict__ part) {
+    long long ng = (long long)nx * ny * nz;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (long long g = (long long)blockIdx.x * 256 + threadIdx.x; g < ng; g += (long long)gridDim.x * 256) {
+        int ix = (int)(g % nx), iy = (int)((g / nx) % ny), iz = (int)(g / ((long long)nx * ny));
+        double vh = pad[((long long)iz * Ny + iy) * Nx + ix];
+        double d = n[g];
+        double c = d > 1e-30 ? CX * cbrt(d) : 0.0;
+        double vx = -c, ex = -0.75 * c;
+        double vl = vloc[g];
+        if (vks) vks[g] = vl + vh + vx;
+        double rho = d - (nion ? nion[g] : 0.0);
+        s0 = fma(vl, d, s0);
+        s1 = fma(vh, rho, s1);
+        s2 = fma(ex, d, s2);
+    }
+    s0 = block_sum<256>(s0);
+    s1 = block_sum<256>(s1);
+    s2 = block_sum<256>(s2);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = s0;
+        part[3 * blockIdx.x + 1] = s1;
+        part[3 * blockIdx.x + 2] = s2;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_energy_reduce(int np, const double* part, double h3, double* scal) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < np; i += 256) {
+        s0 += part[3 * i];
+        s1 += part[3 * i + 1];
+        s2 += part[3 * i + 2];
+    }
+    s0 = block_sum<256>(s0);
+    s1 = block_sum<256>(s1);
+    s2 = block_sum<256>(s2);
+    if (threadIdx.x == 0) {
+        scal[SCAL_E0] = h3 * s0;
+        scal[SCAL_E1] = 0.5 * h3 * s1;
+        scal[SCAL_E2] = h3 * s2;
+    }
+}
+
+__global__ void k_linear_mix(long long n, double* a, const double* b, double alpha) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) a[e] = (1.0 - alpha) * a[e] + alpha * b[e];
+}
+
+__global__ void k_residual(long long n, const double* a, const double* b, double* r) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) r[e] = b[e] - a[e];
+}
+
+__global__ void k_add_scaled(long long n, double* a, const double* r, double s) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) a[e] += s * r[e];
+}
+
+__global__ void __launch_bounds__(256) k_maxabs_part(long long n, const double* a, const double* b, double* part) {
+    double m = 0.0;
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < n; e += (long long)gridDim.x * 256)
+        m = fmax(m, fabs(a[e] - b[e]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int i = 0; i < 8; ++i) r = fmax(r, red[i]);
+        part[blockIdx.x] = r;
+    }
+}
+
+__global__ void k_max_parts(int np, const double* part, double* out) {
+    if (threadIdx.x != 0) return;
+    double r = 0.0;
+    for (int i = 0; i < np; ++i) r = fmax(r, part[i]);
+    *out = r;
+}
+
+// Kerker weights g^2 / (g^2 + q0^2) over the periodic box, R2C layout
+__global__ void k_kerker_weights(int nx, int ny, int nz, double h, double q0, double* w) {
+    int nxc = nx / 2 + 1;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long tot = (long long)nxc * ny * nz;
+    if (e >= tot) return;
+    int ix = (int)(e % nxc), iy = (int)((e / nxc) % ny), iz = (int)(e / ((long long)nxc * ny));
+    double fy = iy <= ny / 2 ? iy : iy - ny, fz = iz <= nz / 2 ? iz : iz - nz;
+    double gx = 2.0 * M_PI * ix / (nx * h), gy = 2.0 * M_PI * fy / (ny * h), gz = 2.0 * M_PI * fz / (nz * h);
+    double g2 = gx * gx + gy * gy + gz * gz;
+    w[e] = g2 / (g2 + q0 * q0) / ((double)nx * ny * nz);
+}
+
+inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+void cufft_check(cufftResult r, const char* what) {
+    if (r != CUFFT_SUCCESS) throw Error(DFT_ECUDA, std::string("cuFFT ") + what + " failed (" + std::to_string((int)r) + ")");
+}
+
+}  // namespace
+
+void poisson_setup(Ctx& c, cudaStream_t s) {
+    cufft_check(cufftPlan3d(&c.plan_f, c.Nfft[2], c.Nfft[1], c.Nfft[0], CUFFT_D2Z), "plan D2Z");
+    cufft_check(cufftPlan3d(&c.plan_b, c.Nfft[2], c.Nfft[1], c.Nfft[0], CUFFT_Z2D), "plan Z2D");
+    cufft_check(cufftSetStream(c.plan_f, s), "stream");
+    cufft_check(cufftSetStream(c.plan_b, s), "stream");
+    k_coulomb_kernel<<<blocks_for(c.nfft_r, 256), 256, 0, s>>>(c.Nfft[0], c.Nfft[1], c.Nfft[2], c.h, c.d_fft_r);
+    check_launch("coulomb_kernel");
+    cufft_check(cufftExecD2Z(c.plan_f, c.d_fft_r, c.d_fft_c), "exec D2Z");
+    // the spectrum of an even real kernel is real; fold in h^3 and the 1/N of the inverse FFT
+    double scale = c.h * c.h * c.h / (double)c.nfft_r;
+    k_take_real<<<blocks_for(c.nfft_c, 256), 256, 0, s>>>(c.nfft_c, c.d_fft_c, scale, c.d_ghat);
+    check_launch("take_real");
+}
+
+void hartree_xc(Ctx& c, const double* n, double* vks, bool energies, cudaStream_t s) {
+    const double* nion = c.p.model == DFT_MODEL_NEUTRAL ? c.d_nion : nullptr;
+    cufft_check(cufftSetStream(c.plan_f, s), "stream");
+    cufft_check(cufftSetStream(c.plan_b, s), "stream");
+    k_pad<<<blocks_for(c.nfft_r, 256), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.Nfft[2], n,
+                                                     nion, c.d_fft_r);
+    check_launch("pad");
+    cufft_check(cufftExecD2Z(c.plan_f, c.d_fft_r, c.d_fft_c), "exec D2Z");
+    k_mul_real<<<blocks_for(c.nfft_c, 256), 256, 0, s>>>(c.nfft_c, c.d_fft_c, c.d_ghat);
+    check_launch("mul_real");
+    cufft_check(cufftExecZ2D(c.plan_b, c.d_fft_c, c.d_fft_r), "exec Z2D");
+    int np = (int)std::min<long long>(1184, (c.ng + 255) / 256);
+    k_vks<<<np, 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.d_fft_r, n, nion, c.d_vloc, vks,
+                             c.d_part);
+    check_launch("vks");
+    if (energies) {
+        k_energy_reduce<<<1, 256, 0, s>>>(np, c.d_part, c.h * c.h * c.h, c.d_scal);
+        check_launch("energy_reduce");
+    }
+}
+
+void kerker_setup(Ctx& c, cudaStream_t s) {
+    cufft_check(cufftPlan3d(&c.kplan_f, c.n[2], c.n[1], c.n[0], CUFFT_D2Z), "kerker plan D2Z");
+    cufft_check(cufftPlan3d(&c.kplan_b, c.n[2], c.n[1], c.n[0], CUFFT_Z2D), "kerker plan Z2D");
+    long long nc = (long long)(c.n[0] / 2 + 1) * c.n[1] * c.n[2];
+    k_kerker_weights<<<blocks_for(nc, 256), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.h, c.p.kerker_q0, c.d_kerker);
+    check_launch("kerker_weights");
+}
+
+// n_in <- n_in + alpha K[n_out - n_in] with K the Kerker filter
+void kerker_mix(Ctx& c, double* n_in, const double* n_out, double alpha, cudaStream_t s) {
+    cufft_check(cufftSetStream(c.kplan_f, s), "stream");
+    cufft_check(cufftSetStream(c.kplan_b, s), "stream");
+    long long nc = (long long)(c.n[0] / 2 + 1) * c.n[1] * c.n[2];
+    k_residual<<<blocks_for(c.ng, 256), 256, 0, s>>>(c.ng, n_in, n_out, c.d_gtmp);
+    cufft_check(cufftExecD2Z(c.kplan_f, c.d_gtmp, c.d_kc), "kerker D2Z");
+    k_mul_real<<<blocks_for(nc, 256), 256, 0, s>>>(nc, c.d_kc, c.d_kerker);
+    cufft_check(cufftExecZ2D(c.kplan_b, c.d_kc, c.d_gtmp), "kerker Z2D");
+    k_add_scaled<<<blocks_for(c.ng, 256), 256, 0, s>>>(c.ng, n_in, c.d_gtmp, alpha);
+    check_launch("kerker_mix", 3);
+}
+
+void launch_linear_mix(long long ng, double* n_in, const double* n_out, double alpha, cudaStream_t s) {
+    k_linear_mix<<<blocks_for(ng, 256), 256, 0, s>>>(ng, n_in, n_out, alpha);
+    check_launch("linear_mix");
+}
+
+void launch_maxabs_diff(long long ng, const double* a, const double* b, double* part, double* out, cudaStream_t s) {
+    int np = (int)std::min<long long>(1184, (ng + 255) / 256);
+    k_maxabs_part<<<np, 256, 0, s>>>(ng, a, b, part);
+    k_max_parts<<<1, 32, 0, s>>>(np, part, out);
+    check_launch("maxabs", 2);
+}
+
+}  // namespace dft

@@ -1,0 +1,113 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry
+point declared in include/dft.h, and sizes workspaces without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2108_13478_gb300 import build
+    return build.build()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "dft.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dft_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for n in ("dft_init_basis", "dft_overlap_kinetic", "dft_density_matrix", "dft_density_on_grid",
+              "dft_potential_matrix", "dft_scf_step", "dft_workspace_bytes", "dft_destroy", "dft_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    lib = ctypes.CDLL(built)
+    for n in header_functions():
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_header(built):
+    from paper_2108_13478_gb300 import _binding
+    declared = set(header_functions())
+    bound = {s[0] for s in _binding.SIGNATURES}
+    assert declared == bound
+
+
+def test_struct_sizes_match_header(built):
+    """The ctypes mirrors have the C layout (checked against offsets that a
+    C compiler computes from the header)."""
+    import subprocess
+    import tempfile
+    from paper_2108_13478_gb300 import _binding as B
+    code = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "dft.h"
+int main(){printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dft_basis_desc), sizeof(dft_grid_desc),
+ sizeof(dft_params), sizeof(dft_info), offsetof(dft_params, seed), offsetof(dft_info, ms_stage),
+ offsetof(dft_params, kerker_q0));return 0;}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(code)
+        exe = os.path.join(d, "t")
+        subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe])
+        out = [int(x) for x in subprocess.check_output([exe]).split()]
+    got = [ctypes.sizeof(B.dft_basis_desc), ctypes.sizeof(B.dft_grid_desc), ctypes.sizeof(B.dft_params),
+           ctypes.sizeof(B.dft_info), B.dft_params.seed.offset, B.dft_info.ms_stage.offset,
+           B.dft_params.kerker_q0.offset]
+    assert got == out
+
+
+def test_workspace_bytes_and_invalid_input(built):
+    import paper_2108_13478_gb300 as dft
+    import workloads as w
+    s = w.config_system("tiny8")
+    xyz = np.ascontiguousarray(s.xyz)
+    sa = np.ascontiguousarray(s.shell_atom, np.int32)
+    sl = np.ascontiguousarray(s.shell_l, np.int32)
+    se = np.ascontiguousarray(s.shell_exp)
+    b = dft.dft_basis_desc()
+    b.n_atoms, b.n_shells = s.n_atoms, len(sa)
+    b.xyz = xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    b.shell_atom = sa.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    b.shell_l = sl.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    b.shell_exp = se.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    g = dft.dft_grid_desc()
+    for d in range(3):
+        g.origin[d] = s.grid_origin[d]
+        g.n[d] = int(s.grid_n[d])
+    g.h = s.grid_h
+    p = dft.make_params(kT=s.kT, n_electrons=s.n_electrons)
+    nb = dft.dft_workspace_bytes(b, g, p)
+    K = s.n_basis
+    assert nb > 11 * K * K * 8 + 5 * s.n_grid * 8
+    assert nb < 64 * K * K * 8 + 64 * s.n_grid * 8 + (1 << 30)
+    # d shells are not supported
+    sl_bad = sl.copy()
+    sl_bad[0] = 2
+    b.shell_l = sl_bad.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    assert dft.dft_workspace_bytes(b, g, p) == 0
+    b.shell_l = sl.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    p.beta = -1.0
+    assert dft.dft_workspace_bytes(b, g, p) == 0
+    assert "sm_103a" in dft.dft_version()
+
+
+def test_product_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_2108_13478_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), f
+                assert "oracle/" not in txt, f

@@ -1,0 +1,244 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Every test builds the same seeded system on both sides; inputs come from the
+seeded generators or from the oracle, never from the CUDA path.
+Tolerances: the FP64 path must match to roundoff of the operation (1e-12 on
+integrals and grid sums relative to their scale) and to 1e-9 max-abs on P.
+"""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import basis, dm, grid_ops, poisson, scf
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2108_13478_gb300 as dft  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    s = w.config_system("tiny8")
+    st = scf.setup(s)
+    return s, st
+
+
+@pytest.fixture(scope="module")
+def c64():
+    s = w.config_system("cluster64")
+    st = scf.setup(s)
+    return s, st
+
+
+def test_overlap_kinetic_closed_form(tiny):
+    s, st = tiny
+    ctx = dft.Context(s)
+    S, T = ctx.overlap_kinetic()
+    assert np.max(np.abs(host(S) - st.S)) < 1e-13
+    assert np.max(np.abs(host(T) - st.T)) < 1e-12
+    ctx.close()
+
+
+def test_overlap_kinetic_cluster64(c64):
+    s, st = c64
+    ctx = dft.Context(s)
+    S, T = ctx.overlap_kinetic()
+    assert np.max(np.abs(host(S) - st.S)) < 1e-13
+    assert np.max(np.abs(host(T) - st.T)) < 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["tiny8", "tiny5"])
+def test_potential_matrix_random_field(name):
+    """Eq. A.6 on a seeded random field; ragged tiles (grid not a multiple of 8)
+    and K not a multiple of the 32-function chunk."""
+    s = w.config_system(name)
+    rng = np.random.default_rng(11)
+    v = rng.normal(size=tuple(int(t) for t in s.grid_n[::-1]))
+    ref = grid_ops.potential_matrix(s, v)
+    ctx = dft.Context(s)
+    V = host(ctx.potential_matrix(dev(v)))
+    assert np.max(np.abs(V - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["tiny8", "tiny5"])
+def test_density_on_grid_random_P(name):
+    s = w.config_system(name)
+    K = s.n_basis
+    rng = np.random.default_rng(12)
+    A = rng.normal(size=(K, K)) * 0.05
+    P = A + A.T
+    ref = grid_ops.density_on_grid(s, P)
+    ctx = dft.Context(s)
+    n = host(ctx.density_on_grid(dev(P)))
+    assert np.max(np.abs(n - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+    ctx.close()
+
+
+def test_grid_ops_cluster64_sampled(c64):
+    """Full-size 64-atom workload: the whole V and n against the oracle."""
+    s, st = c64
+    rng = np.random.default_rng(13)
+    shp = tuple(int(t) for t in s.grid_n[::-1])
+    v = st.vloc + 0.1 * rng.normal(size=shp)
+    ctx = dft.Context(s)
+    V = host(ctx.potential_matrix(dev(v)))
+    pairs = [(int(a), int(b)) for a, b in rng.integers(0, s.n_basis, (40, 2))]
+    ref = grid_ops.potential_entries(s, v, pairs)
+    got = np.array([V[a, b] for a, b in pairs])
+    assert np.max(np.abs(got - ref)) < 1e-11
+    K = s.n_basis
+    A = rng.normal(size=(K, K)) * 0.01
+    P = A + A.T
+    n = host(ctx.density_on_grid(dev(P))).ravel()
+    pick = rng.integers(0, n.size, 200)
+    refn = grid_ops.density_at(s, P, pick)
+    assert np.max(np.abs(n[pick] - refn)) < 1e-11
+    ctx.close()
+
+
+@pytest.mark.parametrize("neutral", [False, True])
+def test_hartree_xc(tiny, neutral):
+    s, _ = tiny
+    st = scf.setup(s, scf.Model(neutral=neutral))
+    n0 = scf.ion_density(s) * 1.3
+    v_ref, vh, ex = scf.potential(st, n0)
+    ctx = dft.Context(s, model=dft.DFT_MODEL_NEUTRAL if neutral else dft.DFT_MODEL_LITERAL)
+    v, e = ctx.hartree_xc(dev(n0))
+    assert np.max(np.abs(host(v) - v_ref)) < 1e-11 * np.max(np.abs(v_ref))
+    h3 = s.grid_h ** 3
+    rho = n0 - st.nion
+    e_ref = (h3 * np.sum(st.vloc * n0), 0.5 * h3 * np.sum(vh * rho), h3 * np.sum(ex * n0))
+    assert np.allclose(e, e_ref, rtol=1e-11, atol=1e-11)
+    ctx.close()
+
+
+def _fixed_bounds_case(s, st):
+    n0 = scf.ion_density(s)
+    v, _, _ = scf.potential(st, n0)
+    F = scf.fock(st, v)
+    beta = 1.0 / s.kT
+    eps = dm.geneig(F, st.S)[0]
+    lo, hi = eps[0] - 0.05 * (eps[-1] - eps[0]), eps[-1] + 0.05 * (eps[-1] - eps[0])
+    n_c = dm.cheb_order(0.5 * (lo + hi), beta, lo, hi, 1e-10)
+    return F, lo, hi, n_c
+
+
+def test_density_matrix_fixed_bounds_tiny(tiny):
+    s, st = tiny
+    F, lo, hi, n_c = _fixed_bounds_case(s, st)
+    ref = dm.dm_cheb(F, st.S, s.n_electrons, 1.0 / s.kT, lo, hi, n_c)
+    ctx = dft.Context(s, e_min=lo, e_max=hi, cheb_order=n_c)
+    ctx.overlap_kinetic()
+    P, info = ctx.density_matrix(dev(F))
+    P = host(P)
+    assert info.n_cheb == n_c
+    assert abs(info.mu - ref["mu"]) < 1e-8
+    assert np.max(np.abs(P - ref["P"])) < 1e-9
+    assert abs(info.n_e_trace - s.n_electrons) < 1e-8
+    ctx.close()
+
+
+def test_density_matrix_auto_order_matches_tail_rule(tiny):
+    """With given bounds the automatic N_C equals the oracle's tail rule."""
+    s, st = tiny
+    F, lo, hi, n_c = _fixed_bounds_case(s, st)
+    ctx = dft.Context(s, e_min=lo, e_max=hi, cheb_tail_tol=1e-10)
+    ctx.overlap_kinetic()
+    P, info = ctx.density_matrix(dev(F))
+    assert abs(info.n_cheb - n_c) <= 1
+    ctx.close()
+
+
+def test_density_matrix_lanczos_bounds(tiny):
+    """Lanczos bounds must bracket the spectrum of S^-1 F; the resulting P
+    approaches the exact Fermi-Dirac DM within the expansion's accuracy."""
+    s, st = tiny
+    F, _, _, _ = _fixed_bounds_case(s, st)
+    ex = dm.dm_exact(F, st.S, s.n_electrons, 1.0 / s.kT)
+    ctx = dft.Context(s, cheb_tail_tol=1e-10)
+    ctx.overlap_kinetic()
+    P, info = ctx.density_matrix(dev(F))
+    assert info.e_min <= ex["eps"][0] and info.e_max >= ex["eps"][-1]
+    assert info.e_max - info.e_min < 1.2 * (ex["eps"][-1] - ex["eps"][0])
+    assert info.spectrum_ok == 1
+    assert np.max(np.abs(host(P) - ex["P"])) < 1e-7
+    assert abs(info.mu - ex["mu"]) < 1e-4
+    ctx.close()
+
+
+def test_density_matrix_cluster64_fixed_bounds(c64):
+    """Full 64-atom, 640-function workload, FP64 path: P to 1e-9 max-abs."""
+    s, st = c64
+    F, lo, hi, n_c = _fixed_bounds_case(s, st)
+    ref = dm.dm_cheb(F, st.S, s.n_electrons, 1.0 / s.kT, lo, hi, n_c)
+    ctx = dft.Context(s, e_min=lo, e_max=hi, cheb_order=n_c)
+    ctx.overlap_kinetic()
+    P, info = ctx.density_matrix(dev(F))
+    err = np.max(np.abs(host(P) - ref["P"]))
+    assert err < 1e-9, err
+    assert abs(info.n_e_trace - s.n_electrons) < 1e-7
+    ctx.close()
+
+
+def test_scf_step_tiny(tiny):
+    """One SCF cycle from the superposition-of-atoms start against the
+    oracle's (exact-DM) cycle."""
+    s, st = tiny
+    ctx = dft.Context(s, cheb_tail_tol=1e-11, mix_alpha=0.3)
+    ctx.overlap_kinetic()
+    n = ctx.initial_density()
+    n0 = scf.ion_density(s)
+    assert np.max(np.abs(host(n) - n0)) < 1e-14
+    P = ctx.matrix()
+    v = ctx.grid_array()
+    info = ctx.scf_step(n, v_ks_out=v, P_out=P)
+    r = scf.step(st, n0)
+    assert abs(info.e_total - r["E"]["total"]) / s.n_atoms < 1e-7
+    assert abs(info.e_kin - r["E"]["kin"]) < 1e-6
+    assert np.max(np.abs(host(v) - r["v"])) < 1e-10
+    assert np.max(np.abs(host(P) - r["P"])) < 1e-7
+    nxt = scf.linear_mix(0.3)(n0, r["n_out"])
+    assert np.max(np.abs(host(n) - nxt)) < 1e-7
+    assert abs(info.residual - np.max(np.abs(r["n_out"] - n0))) < 1e-7
+    ctx.close()
+
+
+def test_scf_two_steps_kerker(tiny):
+    s, st = tiny
+    ctx = dft.Context(s, cheb_tail_tol=1e-11, mixer=dft.DFT_MIX_KERKER, mix_alpha=0.4, kerker_q0=0.8)
+    ctx.overlap_kinetic()
+    n = ctx.initial_density()
+    mix = scf.Pulay(alpha=0.4, hist=1, precond=scf.kerker(s, 0.8))
+    n_ref = scf.ion_density(s)
+    for _ in range(2):
+        info = ctx.scf_step(n)
+        r = scf.step(st, n_ref)
+        assert abs(info.e_total - r["E"]["total"]) / s.n_atoms < 1e-6
+        n_ref = mix(n_ref, r["n_out"])
+        assert np.max(np.abs(host(n) - n_ref)) < 1e-6
+    ctx.close()
+
+
+def test_invalid_arguments_return_status(tiny):
+    s, _ = tiny
+    ctx = dft.Context(s)
+    with pytest.raises(dft.DftError) as e:
+        ctx.density_matrix(ctx.matrix())      # no Cholesky yet
+    assert e.value.status == 1
+    ctx.close()
+    with pytest.raises(dft.DftError):
+        dft.Context(s, eta=2.0)
