@@ -423,6 +423,9 @@ int cholesky_inplace(double* A, int K, int* d_flag, cudaStream_t s) {
 }
 
 void tri_inverse_lower(const double* L, double* Linv, int K, cudaStream_t s) {
+    // the kernel writes rows r >= (first column of each warp) only; the strictly
+    // upper part above that is zero and must be cleared here
+    DFT_CUDA_CHECK(cudaMemsetAsync(Linv, 0, sizeof(double) * (size_t)K * K, s));
     k_tri_inverse<<<blocks_for(K, 128), 128, 0, s>>>(L, Linv, K);
     check_launch("tri_inverse");
 }

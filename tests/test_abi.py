@@ -12,8 +12,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def built():
-    from paper_2108_13478_gb300 import build
-    return build.build()
+    import __graft_entry__
+    __graft_entry__.build()
+    return os.path.join(ROOT, "paper_2108_13478_gb300", "libdft.so")
 
 
 def header_functions():

@@ -146,20 +146,28 @@ def test_density_matrix_fixed_bounds_tiny(tiny):
     P, info = ctx.density_matrix(dev(F))
     P = host(P)
     assert info.n_cheb == n_c
-    assert abs(info.mu - ref["mu"]) < 1e-8
+    # mu is unique only up to flat stretches of N(mu) (a gap): check that the
+    # GPU's mu reproduces N_e under the oracle's expansion
+    n_gpu_mu = dm.electron_count(info.mu, 1.0 / s.kT, lo, hi, ref["moments"])
+    assert abs(n_gpu_mu - s.n_electrons) < 1e-8
     assert np.max(np.abs(P - ref["P"])) < 1e-9
     assert abs(info.n_e_trace - s.n_electrons) < 1e-8
     ctx.close()
 
 
 def test_density_matrix_auto_order_matches_tail_rule(tiny):
-    """With given bounds the automatic N_C equals the oracle's tail rule."""
+    """With given bounds the automatic N_C follows the oracle's tail rule.
+    The tail near 1e-10 carries ~1e-12 of rounding noise from the vanishing
+    (odd/even) coefficients, so the crossing index is fixed to a few indices:
+    compare within 0.5% and check the oracle's tail at the GPU's N_C."""
     s, st = tiny
     F, lo, hi, n_c = _fixed_bounds_case(s, st)
     ctx = dft.Context(s, e_min=lo, e_max=hi, cheb_tail_tol=1e-10)
     ctx.overlap_kinetic()
     P, info = ctx.density_matrix(dev(F))
-    assert abs(info.n_cheb - n_c) <= 1
+    assert abs(info.n_cheb - n_c) <= max(2, 0.005 * n_c)
+    a = dm.cheb_coeffs(0.5 * (lo + hi), 1.0 / s.kT, lo, hi, 2 * n_c)
+    assert np.sum(np.abs(a[info.n_cheb:])) < 1.1e-10
     ctx.close()
 
 
@@ -176,7 +184,7 @@ def test_density_matrix_lanczos_bounds(tiny):
     assert info.e_max - info.e_min < 1.2 * (ex["eps"][-1] - ex["eps"][0])
     assert info.spectrum_ok == 1
     assert np.max(np.abs(host(P) - ex["P"])) < 1e-7
-    assert abs(info.mu - ex["mu"]) < 1e-4
+    assert abs(2 * dm.fermi(ex["eps"], info.mu, 1.0 / s.kT).sum() - s.n_electrons) < 1e-6
     ctx.close()
 
 
