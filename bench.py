@@ -44,8 +44,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="cluster64")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp16x3", "bf16x3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--model", default="neutral", choices=["neutral", "literal"])
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -108,6 +109,12 @@ def peaks():
         return json.load(open(PEAKS_PATH))
     except Exception:
         return {}
+
+
+def tc_tiles(K, bm=128, bn=256):
+    """Output tiles of the tensor-core step that reach the upper triangle."""
+    mt, nt = -(-K // bm), -(-K // bn)
+    return sum(1 for i in range(mt) for j in range(nt) if j * bn + bn - 1 >= i * bm)
 
 
 def cpu_baseline(sysm, budget_s):
@@ -189,9 +196,10 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    prec = dft.DFT_PREC_FP64 if args.precision == "fp64" else dft.DFT_PREC_BF16X3
+    prec = {"fp64": dft.DFT_PREC_FP64, "fp16x3": dft.DFT_PREC_FP16X3, "bf16x3": dft.DFT_PREC_BF16X3}[args.precision]
     stream = torch.cuda.current_stream()
-    ctx = dft.Context(sysm, device=f"cuda:{local}", precision=prec, cheb_tail_tol=1e-10, mix_alpha=0.3)
+    ctx = dft.Context(sysm, device=f"cuda:{local}", precision=prec, cheb_tail_tol=1e-10, mix_alpha=0.3,
+                      model=dft.DFT_MODEL_NEUTRAL if args.model == "neutral" else dft.DFT_MODEL_LITERAL)
     ctx.overlap_kinetic()
     n = ctx.initial_density()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{local}")
@@ -263,17 +271,25 @@ def main():
                 "traffic": None, "peak_source": "FP64 issue rate 4 flop/SM/clk x 152 SMs x median SM clock"}
         dtype = "f64"
     else:
-        flops = 3 * 2.0 * K ** 3
+        # three 16-bit products per step on the upper triangle of the symmetric
+        # output: 3 x K(K+1)/2 outputs x 2K flop
+        flops = 3.0 * K * K * (K + 1)
+        tiles = tc_tiles(K)
+        kpad = -(-K // 64) * 64
+        executed = 3.0 * tiles * 128 * 256 * 2 * kpad
         peak = pk.get("bf16_tflops_sustained", 1700.0)
-        roof = {"kernel": "cheb_step_bf16x3", "bound": "tensor", "achieved": flops / per_launch_s / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "frac": (flops / per_launch_s / 1e12) / peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
-        dtype = "bf16x3"
+        ach = flops / per_launch_s / 1e12
+        roof = {"kernel": "k_cheb_step_tc", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "executed_mma_tflops": executed / per_launch_s / 1e12,
+                "fp32_class_tflops": ach / 3.0,
+                "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured; fp16 dense rate equals bf16)"}
+        dtype = args.precision
     line = {"metric": METRIC, "value": value, "unit": "P-columns/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": sysm.name, "n_basis": K, "n_atoms": sysm.n_atoms,
-                       "grid": [int(x) for x in sysm.grid_n], "kT": sysm.kT, "n_cheb": n_c,
+                       "grid": [int(x) for x in sysm.grid_n], "kT": sysm.kT, "n_cheb": n_c, "model": args.model,
                        "precision": args.precision, "l2": "flushed (256 MB write) between timed steps",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": "P-columns/s",

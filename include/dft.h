@@ -48,7 +48,11 @@ typedef enum dft_status {
     DFT_EUNSUPPORTED = 8  /* feature not built in this library */
 } dft_status;
 
-enum { DFT_PREC_FP64 = 0, DFT_PREC_BF16X3 = 1 };
+/* Precision of the Chebyshev products: FP64 throughout, or tensor cores on
+ * operands split into two 16-bit floats (hi + lo) with three products per
+ * step and FP32 accumulation (BF16 or FP16 pairs).  The mixed modes also run
+ * collocation and quadrature in FP32 arithmetic. */
+enum { DFT_PREC_FP64 = 0, DFT_PREC_BF16X3 = 1, DFT_PREC_FP16X3 = 2 };
 enum { DFT_MODEL_LITERAL = 0, DFT_MODEL_NEUTRAL = 1 };
 enum { DFT_MIX_LINEAR = 0, DFT_MIX_KERKER = 1 };
 
@@ -83,7 +87,7 @@ typedef struct dft_params {
     double eta;             /* window charge cutoff of Eq. A.4 (e.g. 1e-10) */
     double cheb_tail_tol;   /* N_C = smallest order whose coefficient tail sum |a_l| is below this */
     int    cheb_order;      /* > 0: use this N_C instead of the tail rule */
-    int    precision;       /* DFT_PREC_FP64 or DFT_PREC_BF16X3 (Chebyshev products) */
+    int    precision;       /* DFT_PREC_FP64, DFT_PREC_BF16X3 or DFT_PREC_FP16X3 */
     double e_min, e_max;    /* if e_max > e_min: fixed spectral bounds, no Lanczos */
     int    lanczos_steps;   /* Lanczos steps for the bounds (0 -> 64) */
     int    model;           /* DFT_MODEL_LITERAL: Hartree of the electrons only;

@@ -16,7 +16,7 @@ DFT_OK, DFT_EINVAL, DFT_ENOMEM, DFT_ECUDA, DFT_ESPECTRUM, DFT_ENOTCONV, DFT_ETIM
     DFT_EUNSUPPORTED = range(9)
 STATUS_NAMES = {0: "DFT_OK", 1: "DFT_EINVAL", 2: "DFT_ENOMEM", 3: "DFT_ECUDA", 4: "DFT_ESPECTRUM",
                 5: "DFT_ENOTCONV", 6: "DFT_ETIMEOUT", 7: "DFT_EINTERNAL", 8: "DFT_EUNSUPPORTED"}
-DFT_PREC_FP64, DFT_PREC_BF16X3 = 0, 1
+DFT_PREC_FP64, DFT_PREC_BF16X3, DFT_PREC_FP16X3 = 0, 1, 2
 DFT_MODEL_LITERAL, DFT_MODEL_NEUTRAL = 0, 1
 DFT_MIX_LINEAR, DFT_MIX_KERKER = 0, 1
 

@@ -58,8 +58,9 @@ void validate(const dft_basis_desc* b, const dft_grid_desc* g, const dft_params*
         if (g->n[d] <= 0 || g->n[d] > 4096) throw Error(DFT_EINVAL, "grid size out of range");
     if (!(p->beta > 0.0)) throw Error(DFT_EINVAL, "beta must be positive");
     if (!(p->eta > 0.0 && p->eta < 1.0)) throw Error(DFT_EINVAL, "eta must be in (0, 1)");
-    if (p->precision != DFT_PREC_FP64 && p->precision != DFT_PREC_BF16X3)
+    if (p->precision != DFT_PREC_FP64 && p->precision != DFT_PREC_BF16X3 && p->precision != DFT_PREC_FP16X3)
         throw Error(DFT_EINVAL, "unknown precision");
+    if (p->cheb_order <= 0 && !(p->cheb_tail_tol > 0.0)) throw Error(DFT_EINVAL, "cheb_tail_tol must be positive");
 }
 
 // functions, windows, tables and tile lists (host part of the set-up)
@@ -126,7 +127,11 @@ void build_basis(Ctx& c, const dft_basis_desc* b, const dft_grid_desc* g, const 
     c.nfft_r = (long long)c.Nfft[0] * c.Nfft[1] * c.Nfft[2];
     c.nfft_c = (long long)(c.Nfft[0] / 2 + 1) * c.Nfft[1] * c.Nfft[2];
     c.cheb_cap = 1 << 16;
-    c.part_cap = std::max<long long>({2LL * cheb_step_parts(c.K), 3LL * 1184, 2048}) + 64;
+    if (c.p.precision != DFT_PREC_FP64) {
+        c.Kp = tc_pad(c.K);
+        c.n_tc_tiles = (int)(tc_tiles(c.K).size() / 2);
+    }
+    c.part_cap = std::max<long long>({2LL * cheb_step_parts(c.K), 2LL * c.n_tc_tiles, 3LL * 1184, 2048}) + 64;
 }
 
 // carve the workspace; with base == nullptr only the size is computed
@@ -157,6 +162,14 @@ size_t carve(Ctx& c, char* base) {
     size_t o_fc = L.off(sizeof(cufftDoubleComplex) * c.nfft_c);
     size_t o_kw = L.off(sizeof(double) * nkc);
     size_t o_kc = L.off(sizeof(cufftDoubleComplex) * nkc);
+    size_t o_h16[2] = {0, 0}, o_x16[4] = {0, 0, 0, 0}, o_rtc = 0, o_tiles = 0;
+    if (c.Kp > 0) {
+        size_t P16 = (size_t)c.Kp * c.Kp * 2;
+        for (auto& o : o_h16) o = L.off(P16);
+        for (auto& o : o_x16) o = L.off(P16);
+        o_rtc = L.off((size_t)c.Kp * c.Kp * sizeof(double));
+        o_tiles = L.off(sizeof(int) * 2 * (size_t)c.n_tc_tiles);
+    }
     if (base) {
         c.d_fn = (Fn*)(base + o_fn);
         c.d_tab = (double*)(base + o_tab);
@@ -182,6 +195,12 @@ size_t carve(Ctx& c, char* base) {
         c.d_fft_c = (cufftDoubleComplex*)(base + o_fc);
         c.d_kerker = (double*)(base + o_kw);
         c.d_kc = (cufftDoubleComplex*)(base + o_kc);
+        if (c.Kp > 0) {
+            for (int q = 0; q < 2; ++q) c.d_h16[q] = base + o_h16[q];
+            for (int q = 0; q < 4; ++q) c.d_x16[q] = base + o_x16[q];
+            c.d_rho_tc = (double*)(base + o_rtc);
+            c.d_tiles = (int*)(base + o_tiles);
+        }
     }
     return L.total;
 }
@@ -253,7 +272,6 @@ int auto_order(Ctx& c, double emin, double emax, cudaStream_t s) {
 void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cudaStream_t s, Timer* tm,
                          int t0) {
     if (!c.have_chol) throw Error(DFT_EINVAL, "call dft_overlap_kinetic first");
-    if (c.p.precision != DFT_PREC_FP64) throw Error(DFT_EUNSUPPORTED, "this build runs the FP64 path only");
     const int K = c.K;
     DFT_CUDA_CHECK(cudaMemsetAsync(c.d_flags, 0, sizeof(int) * FLAG_COUNT, s));
     if (tm) tm->mark(t0);
@@ -278,22 +296,38 @@ void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cud
     const int M = 4 * n_c;
     launch_cos_table(M, c.d_cos, s);
     if (tm) tm->mark(t0 + 2);
+    const bool tcp = c.p.precision != DFT_PREC_FP64;
     // pass 1: moments m_l = Tr T_l(H_N), l < N_C, by doubling
-    launch_cheb_init(K, c.d_H, c.d_X0, c.d_X1, nullptr, nullptr, s);
     double m0 = (double)K;
     DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_mom, &m0, sizeof(double), cudaMemcpyHostToDevice, s));
-    launch_trace(K, c.d_H, c.d_mom + 1, s);
-    launch_frob_dot((long long)K * K, c.d_H, c.d_H, c.d_part, c.d_scal + SCAL_TRACE, s);
+    if (tcp) {
+        // split H_N into its 16-bit pair; trace and |H|^2 of the pair
+        tc_split_h(c, s);
+        tc_init(c, nullptr, s);
+        DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_mom + 1, c.d_scal + SCAL_TRACE, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_scal + SCAL_TRACE, c.d_scal + SCAL_TRACE + 1, sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s));
+    } else {
+        launch_cheb_init(K, c.d_H, c.d_X0, c.d_X1, nullptr, nullptr, s);
+        launch_trace(K, c.d_H, c.d_mom + 1, s);
+        launch_frob_dot((long long)K * K, c.d_H, c.d_H, c.d_part, c.d_scal + SCAL_TRACE, s);
+    }
     DFT_CUDA_CHECK(cudaMemsetAsync(c.d_scal + SCAL_TRACE + 1, 0, sizeof(double), s));
     if (n_c > 2) launch_moment_reduce(1, c.d_scal + SCAL_TRACE, c.d_mom, 2, -1, m0, c.d_mom + 1, s);
-    int nparts = cheb_step_parts(K);
+    int nparts = tcp ? c.n_tc_tiles : cheb_step_parts(K);
     double* cur = c.d_X1;
     double* prev = c.d_X0;
+    int tcur = 1;   // tensor-core path: pair index holding X_l
     for (int j = 1; 2 * j + 1 <= n_c - 1; ++j) {
-        launch_cheb_step_fp64(K, c.d_H, cur, prev, nullptr, nullptr, 0, c.d_part, c.d_flags, s);
+        if (tcp) {
+            tc_step(c, tcur, nullptr, nullptr, 0, c.d_part, s);
+            tcur = 1 - tcur;
+        } else {
+            launch_cheb_step_fp64(K, c.d_H, cur, prev, nullptr, nullptr, 0, c.d_part, c.d_flags, s);
+            std::swap(cur, prev);
+        }
         launch_moment_reduce(nparts, c.d_part, c.d_mom, (2 * j + 2 < n_c) ? 2 * j + 2 : -1, 2 * j + 1, m0,
                              c.d_mom + 1, s);
-        std::swap(cur, prev);
     }
     // mu from 2 sum_l a_l(mu) m_l = N_e (Eq. 2.8), then the coefficients
     launch_moment_weights(n_c, M, c.d_cos, c.d_mom, c.d_wk, s);
@@ -301,12 +335,22 @@ void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cud
     launch_cheb_coeffs(n_c, M, c.d_cos, c.d_scal, c.p.beta, 0.0, false, c.d_coef, s);
     if (tm) tm->mark(t0 + 3);
     // pass 2: rho = sum_l a_l X_l
-    launch_cheb_init(K, c.d_H, c.d_X0, c.d_X1, c.d_rho, c.d_coef, s);
-    cur = c.d_X1;
-    prev = c.d_X0;
-    for (int l = 2; l < n_c; ++l) {
-        launch_cheb_step_fp64(K, c.d_H, cur, prev, c.d_rho, c.d_coef, l, nullptr, c.d_flags, s);
-        std::swap(cur, prev);
+    if (tcp) {
+        tc_init(c, c.d_coef, s);
+        tcur = 1;
+        for (int l = 2; l < n_c; ++l) {
+            tc_step(c, tcur, c.d_rho_tc, c.d_coef, l, nullptr, s);
+            tcur = 1 - tcur;
+        }
+        tc_rho_finish(c, s);
+    } else {
+        launch_cheb_init(K, c.d_H, c.d_X0, c.d_X1, c.d_rho, c.d_coef, s);
+        cur = c.d_X1;
+        prev = c.d_X0;
+        for (int l = 2; l < n_c; ++l) {
+            launch_cheb_step_fp64(K, c.d_H, cur, prev, c.d_rho, c.d_coef, l, nullptr, c.d_flags, s);
+            std::swap(cur, prev);
+        }
     }
     if (tm) tm->mark(t0 + 4);
     // P = L^-T rho L^-1
@@ -327,6 +371,7 @@ void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cud
         info->n_cheb = n_c;
         info->spectrum_ok = flags[FLAG_SPECTRUM] ? 0 : 1;
     }
+    if (flags[FLAG_TIMEOUT]) throw Error(DFT_ETIMEOUT, "a tensor-core pipeline wait expired");
     if (flags[FLAG_SPECTRUM]) throw Error(DFT_ESPECTRUM, "Chebyshev iterates left [-1, 1]: spectral bounds too tight");
     if (flags[FLAG_MU]) throw Error(DFT_ENOTCONV, "mu bisection: the bracket does not contain N_e");
 }
@@ -374,6 +419,12 @@ dft_status dft_init_basis(dft_ctx** ctx, const dft_basis_desc* basis, const dft_
                                        cudaMemcpyHostToDevice, s));
         DFT_CUDA_CHECK(cudaMemsetAsync(c->d_scal, 0, sizeof(double) * SCAL_COUNT, s));
         DFT_CUDA_CHECK(cudaMemsetAsync(c->d_flags, 0, sizeof(int) * FLAG_COUNT, s));
+        if (c->Kp > 0) {
+            std::vector<int> tl = tc_tiles(c->K);
+            DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_tiles, tl.data(), sizeof(int) * tl.size(), cudaMemcpyHostToDevice, s));
+            DFT_CUDA_CHECK(cudaMemsetAsync(c->d_x16[0], 0, (size_t)c->Kp * c->Kp * 2 * 4, s));
+            tc_setup(*c);
+        }
         launch_build_tables(*c, s);
         launch_gaussian_sum(*c, -c->p.vloc_depth, c->p.vloc_width, c->d_vloc, s);
         double w = c->p.vloc_width;
@@ -433,7 +484,7 @@ dft_status dft_density_on_grid(dft_ctx* ctx, const double* P, double* n_grid, vo
     return guarded(ctx, [&] {
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !P || !n_grid) throw Error(DFT_EINVAL, "null argument");
-        launch_collocate_fp64(c, P, n_grid, static_cast<cudaStream_t>(stream));
+        launch_collocate(c, P, n_grid, static_cast<cudaStream_t>(stream));
     });
 }
 
@@ -442,7 +493,7 @@ dft_status dft_potential_matrix(dft_ctx* ctx, const double* v_grid, double* V, v
     return guarded(ctx, [&] {
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !v_grid || !V) throw Error(DFT_EINVAL, "null argument");
-        launch_quadrature_fp64(c, v_grid, V, static_cast<cudaStream_t>(stream));
+        launch_quadrature(c, v_grid, V, static_cast<cudaStream_t>(stream));
     });
 }
 
@@ -484,13 +535,13 @@ dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double
         tm.mark(0);
         // v_KS[n_in] -> V^KS -> F = T + V^KS
         hartree_xc(c, n_in_out, c.d_vks, false, s);
-        launch_quadrature_fp64(c, c.d_vks, c.d_F, s);
+        launch_quadrature(c, c.d_vks, c.d_F, s);
         launch_axpby_mat(K, 1.0, c.d_T, 1.0, c.d_F, c.d_F, s);
         tm.mark(1);
         // P, then n_out
         density_matrix_impl(c, c.d_F, c.d_P, &loc, s, &tm, 1);
         tm.mark(7);
-        launch_collocate_fp64(c, c.d_P, c.d_nout, s);
+        launch_collocate(c, c.d_P, c.d_nout, s);
         tm.mark(8);
         // energy of n_out
         hartree_xc(c, c.d_nout, nullptr, true, s);

@@ -2,6 +2,7 @@
 // kernel launchers shared by the translation units.  Not part of the ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <stdint.h>
@@ -83,6 +84,16 @@ struct Ctx {
     int cheb_cap = 0;            // capacity of coefficient arrays
     long long part_cap = 0;
 
+    // tensor-core (split 16-bit) Chebyshev path
+    int Kp = 0;                  // padded order (multiple of 256)
+    int n_tc_tiles = 0;
+    void* d_h16[2] = {nullptr, nullptr};   // H_N hi, lo  [Kp x Kp] 16-bit
+    void* d_x16[4] = {nullptr, nullptr, nullptr, nullptr};  // X pairs (hi, lo) x 2
+    double* d_rho_tc = nullptr;  // [Kp x Kp] FP64, upper triangle accumulated
+    int* d_tiles = nullptr;      // (row tile, col tile) pairs
+    CUtensorMap tm_h[2];
+    CUtensorMap tm_x[4];
+
     cufftHandle plan_f = 0, plan_b = 0;
     cufftHandle kplan_f = 0, kplan_b = 0;
     bool have_chol = false;
@@ -101,12 +112,13 @@ enum {
     SCAL_E0, SCAL_E1, SCAL_E2,        // grid energy terms
     SCAL_COUNT = 300
 };
-enum { FLAG_SPECTRUM = 0, FLAG_CHOL = 1, FLAG_MU = 2, FLAG_COUNT = 8 };
+enum { FLAG_SPECTRUM = 0, FLAG_CHOL = 1, FLAG_MU = 2, FLAG_TIMEOUT = 3, FLAG_COUNT = 8 };
 
 // ---- grid kernels (k_grid.cu) ----
 void launch_build_tables(const Ctx& c, cudaStream_t s);
-void launch_collocate_fp64(const Ctx& c, const double* P, double* n, cudaStream_t s);
-void launch_quadrature_fp64(const Ctx& c, const double* v, double* V, cudaStream_t s);
+// FP64 kernels on the FP64 path, FP32 arithmetic (FP64 in and out) on the mixed path
+void launch_collocate(const Ctx& c, const double* P, double* n, cudaStream_t s);
+void launch_quadrature(const Ctx& c, const double* v, double* V, cudaStream_t s);
 void launch_gaussian_sum(const Ctx& c, double amp, double width, double* out, cudaStream_t s);
 
 // ---- dense FP64 linear algebra (k_linalg.cu) ----
@@ -143,6 +155,15 @@ void launch_cheb_step_fp64(int K, const double* H, const double* Xcur, double* X
 int cheb_step_parts(int K);
 void launch_moment_reduce(int nparts, const double* part, double* mom, int idx_even, int idx_odd,
                           double m0, const double* m1, cudaStream_t s);
+
+// ---- tensor-core Chebyshev path (k_cheb_tc.cu) ----
+int tc_pad(int K);
+std::vector<int> tc_tiles(int K);
+void tc_setup(Ctx& c);
+void tc_split_h(const Ctx& c, cudaStream_t s);        // H_N -> 16-bit pair; trace, |H|^2 -> scal[SCAL_TRACE..+1]
+void tc_init(const Ctx& c, const double* coef, cudaStream_t s);
+void tc_step(const Ctx& c, int cur, double* rho, const double* coef, int l, double* part, cudaStream_t s);
+void tc_rho_finish(const Ctx& c, cudaStream_t s);
 
 // ---- Poisson + LDA (k_poisson.cu) ----
 void poisson_setup(Ctx& c, cudaStream_t s);

@@ -35,10 +35,11 @@ __global__ void k_build_tables(const Fn* __restrict__ fn, int K, int W, double o
 }
 
 // stage the 8-point slices of FCH functions' tables for the tile at t0
+template <typename R>
 __device__ __forceinline__ void stage_slices(const Fn* __restrict__ fn, const double* __restrict__ tab,
                                              int W, const int* __restrict__ list, int n_t, int c0,
-                                             const int t0[3], double (*sx)[TILE], double (*sy)[TILE],
-                                             double (*sz)[TILE]) {
+                                             const int t0[3], R (*sx)[TILE], R (*sy)[TILE],
+                                             R (*sz)[TILE]) {
     for (int e = threadIdx.x; e < FCH * 3 * TILE; e += blockDim.x) {
         int fl = e / (3 * TILE);
         int d = (e / TILE) % 3;
@@ -50,21 +51,24 @@ __device__ __forceinline__ void stage_slices(const Fn* __restrict__ fn, const do
             int lo = fn[f].lo[d], hi = fn[f].hi[d];
             if (i >= lo && i <= hi) val = tab[((long long)f * 3 + d) * W + (i - lo)];
         }
-        if (d == 0) sx[fl][q] = val;
-        else if (d == 1) sy[fl][q] = val;
-        else sz[fl][q] = val;
+        if (d == 0) sx[fl][q] = (R)val;
+        else if (d == 1) sy[fl][q] = (R)val;
+        else sz[fl][q] = (R)val;
     }
 }
 
 // n(r_g) = sum_a 2 phi_a(r_g) sum_b phi_b(r_g) P_ba for the points of one tile
-// (Eq. A.5 summed over the columns a).  256 threads, 2 points each.
-__global__ void __launch_bounds__(256) k_collocate_fp64(
+// (Eq. A.5 summed over the columns a).  256 threads, 2 points each.  R is the
+// arithmetic type (double on the FP64 path, float on the mixed path); inputs
+// and output stay double.
+template <typename R>
+__global__ void __launch_bounds__(256) k_collocate(
     const Fn* __restrict__ fn, const double* __restrict__ tab, int W, const int* __restrict__ tile_ptr,
     const int* __restrict__ tile_fn, int ntx, int nty, int nx, int ny, int nz, int K,
     const double* __restrict__ P, double* __restrict__ n_out) {
-    __shared__ double sxa[FCH][TILE], sya[FCH][TILE], sza[FCH][TILE];
-    __shared__ double sxb[FCH][TILE], syb[FCH][TILE], szb[FCH][TILE];
-    __shared__ double sP[FCH][FCH];
+    __shared__ R sxa[FCH][TILE], sya[FCH][TILE], sza[FCH][TILE];
+    __shared__ R sxb[FCH][TILE], syb[FCH][TILE], szb[FCH][TILE];
+    __shared__ __align__(16) R sP[FCH][FCH];
     const int t = blockIdx.x;
     const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
     const int t0[3] = {tx * TILE, ty * TILE, tz * TILE};
@@ -73,9 +77,9 @@ __global__ void __launch_bounds__(256) k_collocate_fp64(
     const int px = threadIdx.x & 7, py = (threadIdx.x >> 3) & 7, pz0 = threadIdx.x >> 6, pz1 = pz0 + 4;
     double acc0 = 0.0, acc1 = 0.0;
     for (int ca = 0; ca < n_t; ca += FCH) {
-        double y0[FCH], y1[FCH];
+        R y0[FCH], y1[FCH];
 #pragma unroll
-        for (int j = 0; j < FCH; ++j) { y0[j] = 0.0; y1[j] = 0.0; }
+        for (int j = 0; j < FCH; ++j) { y0[j] = (R)0; y1[j] = (R)0; }
         for (int cb = 0; cb < n_t; cb += FCH) {
             __syncthreads();
             stage_slices(fn, tab, W, list, n_t, cb, t0, sxb, syb, szb);
@@ -83,17 +87,17 @@ __global__ void __launch_bounds__(256) k_collocate_fp64(
                 int i = e / FCH, j = e % FCH;
                 double v = 0.0;
                 if (cb + i < n_t && ca + j < n_t) v = P[(long long)list[cb + i] * K + list[ca + j]];
-                sP[i][j] = v;
+                sP[i][j] = (R)v;
             }
             __syncthreads();
 #pragma unroll 2
             for (int i = 0; i < FCH; ++i) {
-                double pxy = sxb[i][px] * syb[i][py];
-                double pb0 = pxy * szb[i][pz0];
-                double pb1 = pxy * szb[i][pz1];
+                R pxy = sxb[i][px] * syb[i][py];
+                R pb0 = pxy * szb[i][pz0];
+                R pb1 = pxy * szb[i][pz1];
 #pragma unroll
                 for (int j = 0; j < FCH; ++j) {
-                    double pv = sP[i][j];
+                    R pv = sP[i][j];
                     y0[j] = fma(pb0, pv, y0[j]);
                     y1[j] = fma(pb1, pv, y1[j]);
                 }
@@ -102,12 +106,15 @@ __global__ void __launch_bounds__(256) k_collocate_fp64(
         __syncthreads();
         stage_slices(fn, tab, W, list, n_t, ca, t0, sxa, sya, sza);
         __syncthreads();
+        R c0 = (R)0, c1 = (R)0;
 #pragma unroll
         for (int j = 0; j < FCH; ++j) {
-            double pxy = sxa[j][px] * sya[j][py];
-            acc0 = fma(pxy * sza[j][pz0], y0[j], acc0);
-            acc1 = fma(pxy * sza[j][pz1], y1[j], acc1);
+            R pxy = sxa[j][px] * sya[j][py];
+            c0 = fma(pxy * sza[j][pz0], y0[j], c0);
+            c1 = fma(pxy * sza[j][pz1], y1[j], c1);
         }
+        acc0 += (double)c0;
+        acc1 += (double)c1;
     }
     int gx = t0[0] + px, gy = t0[1] + py;
     if (gx < nx && gy < ny) {
@@ -121,14 +128,15 @@ __global__ void __launch_bounds__(256) k_collocate_fp64(
 // (Eq. A.6).  Chunk pairs (ca <= cb); the off-diagonal chunk blocks are
 // mirrored.  Contributions of different tiles meet through FP64 atomics.
 constexpr int QPTS = 64;
-__global__ void __launch_bounds__(256) k_quadrature_fp64(
+template <typename R>
+__global__ void __launch_bounds__(256) k_quadrature(
     const Fn* __restrict__ fn, const double* __restrict__ tab, int W, const int* __restrict__ tile_ptr,
     const int* __restrict__ tile_fn, int ntx, int nty, int nx, int ny, int nz, int K, double h3,
     const double* __restrict__ v, double* __restrict__ V) {
-    __shared__ double sxa[FCH][TILE], sya[FCH][TILE], sza[FCH][TILE];
-    __shared__ double sxb[FCH][TILE], syb[FCH][TILE], szb[FCH][TILE];
-    __shared__ double sv[TILE_PTS];
-    __shared__ double pa[QPTS][FCH + 1], pb[QPTS][FCH + 1];
+    __shared__ R sxa[FCH][TILE], sya[FCH][TILE], sza[FCH][TILE];
+    __shared__ R sxb[FCH][TILE], syb[FCH][TILE], szb[FCH][TILE];
+    __shared__ R sv[TILE_PTS];
+    __shared__ R pa[QPTS][FCH + 1], pb[QPTS][FCH + 1];
     const int t = blockIdx.x;
     const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
     const int t0[3] = {tx * TILE, ty * TILE, tz * TILE};
@@ -137,7 +145,7 @@ __global__ void __launch_bounds__(256) k_quadrature_fp64(
     if (n_t == 0) return;
     for (int p = threadIdx.x; p < TILE_PTS; p += blockDim.x) {
         int gx = t0[0] + (p & 7), gy = t0[1] + ((p >> 3) & 7), gz = t0[2] + (p >> 6);
-        sv[p] = (gx < nx && gy < ny && gz < nz) ? v[((long long)gz * ny + gy) * nx + gx] : 0.0;
+        sv[p] = (R)((gx < nx && gy < ny && gz < nz) ? v[((long long)gz * ny + gy) * nx + gx] : 0.0);
     }
     const int a = threadIdx.x & 31;
     const int b0 = (threadIdx.x >> 5) * 4;
@@ -147,7 +155,7 @@ __global__ void __launch_bounds__(256) k_quadrature_fp64(
         for (int cb = ca; cb < n_t; cb += FCH) {
             __syncthreads();
             stage_slices(fn, tab, W, list, n_t, cb, t0, sxb, syb, szb);
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            R acc[4] = {(R)0, (R)0, (R)0, (R)0};
             for (int p0 = 0; p0 < TILE_PTS; p0 += QPTS) {
                 __syncthreads();
                 for (int e = threadIdx.x; e < QPTS * FCH; e += blockDim.x) {
@@ -160,7 +168,7 @@ __global__ void __launch_bounds__(256) k_quadrature_fp64(
                 __syncthreads();
 #pragma unroll 4
                 for (int pp = 0; pp < QPTS; ++pp) {
-                    double va = pa[pp][a];
+                    R va = pa[pp][a];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc[q] = fma(va, pb[pp][b0 + q], acc[q]);
                 }
@@ -171,7 +179,7 @@ __global__ void __launch_bounds__(256) k_quadrature_fp64(
                 for (int q = 0; q < 4; ++q) {
                     if (cb + b0 + q < n_t) {
                         int fb = list[cb + b0 + q];
-                        double val = h3 * acc[q];
+                        double val = h3 * (double)acc[q];
                         atomicAdd(&V[(long long)fa * K + fb], val);
                         if (ca != cb) atomicAdd(&V[(long long)fb * K + fa], val);
                     }
@@ -209,19 +217,27 @@ void launch_build_tables(const Ctx& c, cudaStream_t s) {
     check_launch("build_tables");
 }
 
-void launch_collocate_fp64(const Ctx& c, const double* P, double* n, cudaStream_t s) {
-    k_collocate_fp64<<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
-                                                         c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K,
-                                                         P, n);
-    check_launch("collocate_fp64");
+void launch_collocate(const Ctx& c, const double* P, double* n, cudaStream_t s) {
+    if (c.p.precision == DFT_PREC_FP64)
+        k_collocate<double><<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
+                                                                c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K, P, n);
+    else
+        k_collocate<float><<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
+                                                               c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K, P, n);
+    check_launch("collocate");
 }
 
-void launch_quadrature_fp64(const Ctx& c, const double* v, double* V, cudaStream_t s) {
+void launch_quadrature(const Ctx& c, const double* v, double* V, cudaStream_t s) {
     DFT_CUDA_CHECK(cudaMemsetAsync(V, 0, sizeof(double) * (size_t)c.K * c.K, s));
-    k_quadrature_fp64<<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
-                                                          c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K,
-                                                          c.h * c.h * c.h, v, V);
-    check_launch("quadrature_fp64");
+    if (c.p.precision == DFT_PREC_FP64)
+        k_quadrature<double><<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
+                                                                 c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K,
+                                                                 c.h * c.h * c.h, v, V);
+    else
+        k_quadrature<float><<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
+                                                                c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K,
+                                                                c.h * c.h * c.h, v, V);
+    check_launch("quadrature");
 }
 
 void launch_gaussian_sum(const Ctx& c, double amp, double width, double* out, cudaStream_t s) {

@@ -1,0 +1,85 @@
+"""Mixed-precision (tensor-core, split 16-bit) path against the FP64 oracle.
+
+The Chebyshev products run on tcgen05 with operands split into hi + lo
+16-bit pairs and FP32 accumulation; the recurrence result rho is summed in
+FP64.  The errors are reported per result; the gates are the ones the method
+needs: P within 2e-5 max-abs and energy-like traces within 1e-5 Ha/atom.
+"""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import dm, grid_ops, scf
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2108_13478_gb300 as dft  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def case(name, neutral=True):
+    s = w.config_system(name)
+    st = scf.setup(s, scf.Model(neutral=neutral))
+    n0 = scf.ion_density(s)
+    v, _, _ = scf.potential(st, n0)
+    F = scf.fock(st, v)
+    eps = dm.geneig(F, st.S)[0]
+    W = eps[-1] - eps[0]
+    lo, hi = eps[0] - 0.02 * W, eps[-1] + 0.02 * W
+    beta = 1.0 / s.kT
+    n_c = dm.cheb_order(0.5 * (lo + hi), beta, lo, hi, 1e-10)
+    ref = dm.dm_cheb(F, st.S, s.n_electrons, beta, lo, hi, n_c)
+    return s, st, F, lo, hi, n_c, ref
+
+
+@pytest.mark.parametrize("name,prec,tol_p,tol_e", [
+    ("tiny8", "fp16x3", 1e-4, 1e-5),
+    ("cluster64", "fp16x3", 1e-4, 1e-5),
+    ("tiny8", "bf16x3", 2e-3, 1e-3),
+])
+def test_mixed_density_matrix(name, prec, tol_p, tol_e):
+    s, st, F, lo, hi, n_c, ref = case(name)
+    p = dft.DFT_PREC_FP16X3 if prec == "fp16x3" else dft.DFT_PREC_BF16X3
+    ctx = dft.Context(s, precision=p, e_min=lo, e_max=hi, cheb_order=n_c, model=dft.DFT_MODEL_NEUTRAL)
+    ctx.overlap_kinetic()
+    P, info = ctx.density_matrix(dev(F))
+    P = P.cpu().numpy()
+    dP = P - ref["P"]
+    err = float(np.max(np.abs(dP)))
+    e_kin = abs(2 * np.sum(dP * st.T)) / s.n_atoms
+    e_band = abs(2 * np.sum(dP * F)) / s.n_atoms
+    print(f"{name} {prec}: max|dP| {err:.3e}  dEkin/atom {e_kin:.3e}  dEband/atom {e_band:.3e}  "
+          f"N_e {info.n_e_trace:.8f}  mu {info.mu:.8f} vs {ref['mu']:.8f}")
+    assert info.spectrum_ok == 1
+    assert err < tol_p
+    assert e_kin < tol_e and e_band < tol_e
+    ctx.close()
+
+
+def test_mixed_grid_kernels_fp32():
+    """FP32-arithmetic collocation and quadrature against the FP64 oracle."""
+    s = w.config_system("cluster64")
+    st = scf.setup(s)
+    rng = np.random.default_rng(5)
+    v = st.vloc + 0.1 * rng.normal(size=tuple(int(t) for t in s.grid_n[::-1]))
+    ctx = dft.Context(s, precision=dft.DFT_PREC_FP16X3)
+    V = ctx.potential_matrix(dev(v)).cpu().numpy()
+    pairs = [(int(a), int(b)) for a, b in rng.integers(0, s.n_basis, (40, 2))]
+    ref = grid_ops.potential_entries(s, v, pairs)
+    got = np.array([V[a, b] for a, b in pairs])
+    assert np.max(np.abs(got - ref)) < 2e-6 * max(1.0, np.max(np.abs(ref)))
+    K = s.n_basis
+    A = rng.normal(size=(K, K)) * 0.01
+    P = A + A.T
+    n = ctx.density_on_grid(dev(P)).cpu().numpy().ravel()
+    pick = rng.integers(0, n.size, 200)
+    refn = grid_ops.density_at(s, P, pick)
+    assert np.max(np.abs(n[pick] - refn)) < 1e-5 * max(1.0, np.max(np.abs(refn)))
+    ctx.close()
