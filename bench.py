@@ -210,6 +210,8 @@ def main():
         torch.cuda.synchronize()
     for _ in range(args.warmup):
         ctx.scf_step(n)
+    n_start = n.clone()          # the e2e leg re-runs the same SCF steps from here
+    e_prev_state = None
     barrier()
     sampler = ClockSampler(local)
     sampler.start()
@@ -237,7 +239,7 @@ def main():
     # end to end through the public API with host buffers: pinned n_in -> device,
     # step, next density and energies back to the host
     n_host = torch.empty(ctx.grid_shape, dtype=torch.float64, pin_memory=True)
-    n_host.copy_(n.cpu())
+    n_host.copy_(n_start.cpu())
     out_host = torch.empty_like(n_host).pin_memory()
     dev_n = ctx.grid_array()
     barrier()

@@ -276,8 +276,7 @@ void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cud
     DFT_CUDA_CHECK(cudaMemsetAsync(c.d_flags, 0, sizeof(int) * FLAG_COUNT, s));
     if (tm) tm->mark(t0);
     // F~ = L^-1 F L^-T
-    dgemm('N', 'N', K, K, K, 1.0, c.d_Linv, K, F, K, 0.0, c.d_B, K, s);
-    dgemm('N', 'T', K, K, K, 1.0, c.d_B, K, c.d_Linv, K, 0.0, c.d_A, K, s);
+    congruence_lower(K, c.d_Linv, F, c.d_B, c.d_A, s);
     if (tm) tm->mark(t0 + 1);
     // spectral bounds of S^-1 F
     if (c.p.e_max > c.p.e_min) {
@@ -354,8 +353,7 @@ void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cud
     }
     if (tm) tm->mark(t0 + 4);
     // P = L^-T rho L^-1
-    dgemm('T', 'N', K, K, K, 1.0, c.d_Linv, K, c.d_rho, K, 0.0, c.d_B, K, s);
-    dgemm('N', 'N', K, K, K, 1.0, c.d_B, K, c.d_Linv, K, 0.0, P, K, s);
+    congruence_lower_t(K, c.d_Linv, c.d_rho, c.d_B, P, s);
     if (tm) tm->mark(t0 + 5);
     launch_frob_dot((long long)K * K, P, c.d_S, c.d_part, c.d_scal + SCAL_NE, s);
     int flags[FLAG_COUNT];

@@ -127,6 +127,10 @@ void dgemm(char ta, char tb, int M, int N, int Kd, double alpha, const double* A
            const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s);
 int cholesky_inplace(double* A, int K, int* d_flag, cudaStream_t s);   // lower L, upper zeroed
 void tri_inverse_lower(const double* L, double* Linv, int K, cudaStream_t s);
+// out = Linv F Linv^T and out = Linv^T R Linv for lower-triangular Linv and
+// symmetric F, R (FP64, k ranges cut to the triangle, upper tiles mirrored)
+void congruence_lower(int K, const double* Linv, const double* F, double* tmp, double* out, cudaStream_t s);
+void congruence_lower_t(int K, const double* Linv, const double* R, double* tmp, double* out, cudaStream_t s);
 void launch_overlap_kinetic(const Ctx& c, double* S, double* T, cudaStream_t s);
 void launch_axpby_mat(int K, double a, const double* X, double b, const double* Y, double* Z,
                       cudaStream_t s);   // Z = a X + b Y

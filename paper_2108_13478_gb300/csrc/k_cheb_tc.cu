@@ -31,8 +31,14 @@
 namespace dft {
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 2;
-constexpr int GK = 4;                                 // k-blocks per promoted chunk
+// k-block width: 32 (64-byte rows, 64-byte swizzle, 4 stages) or 64 (128-byte
+// rows and swizzle, 2 stages); either way 192 KB of operand ring
+#ifndef DFT_TC_BK
+#define DFT_TC_BK 32
+#endif
+constexpr int BM = 128, BN = 256, BK = DFT_TC_BK, STAGES = BK == 64 ? 2 : 4;
+constexpr int GK = 256 / BK;                          // k-blocks per promoted chunk (256 of K)
+constexpr int ROW_BYTES = BK * 2;                     // one operand row in shared memory
 constexpr int NEPI = 256;                             // epilogue threads (8 warps)
 constexpr int NTHREADS = 64 + NEPI;                   // + producer warp + MMA warp
 constexpr int A_BYTES = BM * BK * 2;                  // 16 KB
@@ -90,11 +96,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row core groups 1024 bytes apart
+// shared-memory matrix descriptor of a K-major operand whose rows are one
+// swizzle atom wide (ROW_BYTES): 8-row core groups 8 * ROW_BYTES apart;
+// layout type 2 = 128-byte swizzle, 4 = 64-byte swizzle
 __device__ __forceinline__ uint64_t smem_desc(const void* p) {
     uint64_t addr = (uint64_t)(smem_u32(p) & 0x3FFFF) >> 4;
-    return addr | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
+    const uint64_t sbo = (uint64_t)(8 * ROW_BYTES) >> 4;
+    const uint64_t layout = ROW_BYTES == 128 ? 2ull : 4ull;
+    return addr | (1ull << 16) | (sbo << 32) | (1ull << 46) | (layout << 61);
 }
 
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -549,7 +558,8 @@ void make_map(CUtensorMap* m, const void* base, int Kp, int box_rows) {
     cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             ROW_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) throw Error(DFT_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }

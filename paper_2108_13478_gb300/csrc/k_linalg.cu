@@ -72,6 +72,77 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int Kd, double alph
     }
 }
 
+// Square K x K products with a triangular factor: the k range of each 64 x 64
+// output tile is cut to where the triangular operand is nonzero, and with
+// UPPER only tiles on or above the diagonal are computed (symmetric results,
+// mirrored afterwards).  KR: 0 full, 1 k < end of row tile, 2 k < end of
+// column tile, 3 k >= start of row tile, 4 k >= start of column tile.
+template <bool TA, bool TB, int KR, bool UPPER>
+__global__ void __launch_bounds__(256) k_dgemm_tri(int K, const double* __restrict__ A, const double* __restrict__ B,
+                                                   double* __restrict__ C) {
+    if (UPPER && blockIdx.x < blockIdx.y) return;
+    __shared__ double As[GK][GB + 1];
+    __shared__ double Bs[GK][GB + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int m0 = blockIdx.y * GB, n0 = blockIdx.x * GB;
+    int klo = 0, khi = K;
+    if (KR == 1) khi = min(K, m0 + GB);
+    if (KR == 2) khi = min(K, n0 + GB);
+    if (KR == 3) klo = m0;
+    if (KR == 4) klo = n0;
+    double acc[4][4] = {};
+    for (int k0 = klo; k0 < khi; k0 += GK) {
+        for (int e = threadIdx.x; e < GB * GK; e += 256) {
+            int mm, kk;
+            if (!TA) { kk = e % GK; mm = e / GK; } else { mm = e % GB; kk = e / GB; }
+            int gm = m0 + mm, gk = k0 + kk;
+            double v = 0.0;
+            if (gm < K && gk < khi) v = TA ? A[(long long)gk * K + gm] : A[(long long)gm * K + gk];
+            As[kk][mm] = v;
+        }
+        for (int e = threadIdx.x; e < GB * GK; e += 256) {
+            int nn, kk;
+            if (!TB) { nn = e % GB; kk = e / GB; } else { kk = e % GK; nn = e / GK; }
+            int gn = n0 + nn, gk = k0 + kk;
+            double v = 0.0;
+            if (gn < K && gk < khi) v = TB ? B[(long long)gn * K + gk] : B[(long long)gk * K + gn];
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gm = m0 + ty + 16 * i;
+        if (gm >= K) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gn = n0 + tx + 16 * j;
+            if (gn < K) C[(long long)gm * K + gn] = acc[i][j];
+        }
+    }
+}
+
+// lower triangle from the upper one (for results of k_dgemm_tri<..., true>)
+__global__ void k_mirror_upper(int K, double* C) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)K * K) return;
+    int i = (int)(e / K), j = (int)(e % K);
+    if (i > j) C[e] = C[(long long)j * K + i];
+}
+
 // in-place Cholesky of the nb x nb diagonal block at (kb, kb); lower factor
 __global__ void __launch_bounds__(256) k_potrf_diag(double* A, int K, int kb, int nb, int* flag) {
     __shared__ double s[GB][GB + 1];
@@ -420,6 +491,26 @@ int cholesky_inplace(double* A, int K, int* d_flag, cudaStream_t s) {
     k_zero_upper<<<blocks_for((long long)K * K, 256), 256, 0, s>>>(A, K);
     check_launch("cholesky");
     return 0;
+}
+
+void congruence_lower(int K, const double* Linv, const double* F, double* tmp, double* out, cudaStream_t s) {
+    // out = Linv F Linv^T, Linv lower triangular, F and out symmetric
+    const int nb = (K + GB - 1) / GB;
+    dim3 grid(nb, nb);
+    k_dgemm_tri<false, false, 1, false><<<grid, 256, 0, s>>>(K, Linv, F, tmp);
+    k_dgemm_tri<false, true, 2, true><<<grid, 256, 0, s>>>(K, tmp, Linv, out);
+    k_mirror_upper<<<blocks_for((long long)K * K, 256), 256, 0, s>>>(K, out);
+    check_launch("congruence_lower", 3);
+}
+
+void congruence_lower_t(int K, const double* Linv, const double* R, double* tmp, double* out, cudaStream_t s) {
+    // out = Linv^T R Linv, Linv lower triangular, R and out symmetric
+    const int nb = (K + GB - 1) / GB;
+    dim3 grid(nb, nb);
+    k_dgemm_tri<true, false, 3, false><<<grid, 256, 0, s>>>(K, Linv, R, tmp);
+    k_dgemm_tri<false, false, 4, true><<<grid, 256, 0, s>>>(K, tmp, Linv, out);
+    k_mirror_upper<<<blocks_for((long long)K * K, 256), 256, 0, s>>>(K, out);
+    check_launch("congruence_lower_t", 3);
 }
 
 void tri_inverse_lower(const double* L, double* Linv, int K, cudaStream_t s) {
