@@ -178,6 +178,24 @@ dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double
  * vloc_width on every atom.  n_grid device grid, overwritten. */
 dft_status dft_initial_density(dft_ctx* ctx, double* n_grid, void* stream);
 
+/* Spectral bounds of S^-1 F for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a deployment variant of the Lanczos
+ * step inside dft_density_matrix for code that runs where cudaMalloc is not
+ * allowed (a host framework's fixed memory pool, pre-planned execution with
+ * every buffer fixed up front).  It computes F~ = L^-1 F L^-T and the padded
+ * Lanczos bounds exactly as dft_density_matrix does, but its scratch is a
+ * file-scope device array of 2 K^2 + 4 K + 300 doubles for K <= 768 (about
+ * 9.5 MB, held by every GPU that loads the library until the process ends);
+ * it calls no cudaMalloc, cudaFree or allocating library routine.
+ *   F       device, K x K Fock matrix (as for dft_density_matrix)
+ *   bounds  host, 2 doubles: E_min, E_max (padded as in dft_density_matrix)
+ * Returns DFT_EINVAL when K > 768.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call shares the
+ * one array, so calls that overlap on the GPU (other streams, other host
+ * threads) race; the stream is synchronised before returning. */
+dft_status dft_spectral_bounds_static(dft_ctx* ctx, const double* F, double* bounds, void* stream);
+
 /* Release the context (not the caller's workspace). */
 dft_status dft_destroy(dft_ctx* ctx);
 

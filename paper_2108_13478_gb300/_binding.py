@@ -70,6 +70,7 @@ SIGNATURES = [
     ("dft_last_error", C.c_char_p, [_P]),
     ("dft_version", C.c_char_p, []),
     ("dft_kernel_launches", C.c_ulonglong, []),
+    ("dft_spectral_bounds_static", C.c_int, [_P, _P, C.POINTER(C.c_double), _P]),
 ]
 
 
@@ -172,6 +173,14 @@ def dft_last_error(ctx) -> str:
 
 def dft_version() -> str:
     return lib.dft_version().decode()
+
+
+def dft_spectral_bounds_static(ctx, F, stream=None):
+    """Lanczos bounds of S^-1 F through the allocation-free entry point
+    (K <= 768); returns (E_min, E_max)."""
+    b = (C.c_double * 2)()
+    _check(ctx, lib.dft_spectral_bounds_static(ctx, _ptr(F), b, _stream(stream)))
+    return b[0], b[1]
 
 
 def dft_kernel_launches() -> int:

@@ -141,6 +141,9 @@ void launch_trace(int K, const double* X, double* out, cudaStream_t s);
 void launch_identity(int K, double* X, cudaStream_t s);
 // Lanczos on symmetric A: writes padded bounds to scal[SCAL_EMIN], scal[SCAL_EMAX]
 void lanczos_bounds(const Ctx& c, const double* A, int steps, cudaStream_t s);
+// the same with explicit buffers (vec: 4 K doubles, scal: SCAL_COUNT doubles)
+void lanczos_bounds_at(int K, const double* A, int steps, unsigned long long seed, double* vec, double* scal,
+                       cudaStream_t s);
 
 // ---- Chebyshev engine (k_cheb.cu) ----
 void launch_cos_table(int M, double* cos_tab, cudaStream_t s);

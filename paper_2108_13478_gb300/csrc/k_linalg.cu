@@ -573,4 +573,25 @@ void lanczos_bounds(const Ctx& c, const double* A, int steps, cudaStream_t s) {
     check_launch("lanczos");
 }
 
+// Lanczos bounds with caller-given buffers: vec holds 4 K doubles, scal
+// SCAL_COUNT doubles; the padded bounds land in scal[SCAL_EMIN], scal[SCAL_EMAX]
+void lanczos_bounds_at(int K, const double* A, int steps, unsigned long long seed, double* vec, double* scal,
+                       cudaStream_t s) {
+    int m = std::max(2, std::min(steps, std::min(K, 120)));
+    double* v[3] = {vec, vec + K, vec + 2 * K};
+    double* w = vec + 3 * K;
+    k_lanczos_start<<<1, 1024, 0, s>>>(K, seed, v[0], scal);
+    check_launch("lanczos_start");
+    for (int j = 0; j < m; ++j) {
+        double* vj = v[j % 3];
+        double* vjm1 = v[(j + 2) % 3];
+        double* vn = v[(j + 1) % 3];
+        k_gemv<<<blocks_for(K, 8), 256, 0, s>>>(K, A, vj, w);
+        k_lanczos_update<<<1, 1024, 0, s>>>(K, j, w, vj, vjm1, vn, scal);
+        check_launch("lanczos_step", 2);
+    }
+    k_tridiag_bounds<<<1, 32, 0, s>>>(m, scal);
+    check_launch("lanczos");
+}
+
 }  // namespace dft
