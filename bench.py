@@ -43,10 +43,14 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="cluster64")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp16x3", "bf16x3"])
+    ap.add_argument("--workload", default="sphere25")
+    ap.add_argument("--precision", default="fp16x3", choices=["fp64", "fp16x3", "bf16x3"])
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the mixed-vs-FP64 comparison on the 64-atom cluster")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--model", default="neutral", choices=["neutral", "literal"])
+    ap.add_argument("--mixer", default="pulay", choices=["pulay", "kerker", "linear"],
+                    help="density mixing (linear 0.3 diverges for the neutral model on the R = 25 sphere)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -160,6 +164,37 @@ def cpu_baseline(sysm, budget_s):
                                                              "poisson": 2 * t_pois}}
 
 
+def compare_precisions(dft, torch, local, name="cluster64", steps=2):
+    """Mixed (FP16x3) and FP64 GPU paths on the same SCF steps of the 64-atom
+    cluster (the largest case where the FP64 path finishes in seconds): step
+    time of each and the energy difference per atom."""
+    import workloads as w
+    sysm = w.config_system(name)
+    out = {"workload": name, "n_basis": sysm.n_basis, "steps": steps}
+    res = {}
+    for prec, key in ((dft.DFT_PREC_FP64, "fp64"), (dft.DFT_PREC_FP16X3, "fp16x3")):
+        ctx = dft.Context(sysm, device=f"cuda:{local}", precision=prec, cheb_tail_tol=1e-10, mix_alpha=0.3,
+                          mixer=dft.DFT_MIX_PULAY, kerker_q0=0.8, mix_history=8, model=dft.DFT_MODEL_NEUTRAL)
+        ctx.overlap_kinetic()
+        n = ctx.initial_density()
+        ms, es = [], []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = ctx.scf_step(n)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            es.append(info.e_total / sysm.n_atoms)
+        res[key] = (ms, es)
+        ctx.close()
+    out["fp64_ms_per_step"] = statistics.median(res["fp64"][0])
+    out["fp16x3_ms_per_step"] = statistics.median(res["fp16x3"][0])
+    out["speedup"] = out["fp64_ms_per_step"] / out["fp16x3_ms_per_step"]
+    out["max_abs_dE_per_atom"] = max(abs(a - b) for a, b in zip(res["fp64"][1], res["fp16x3"][1]))
+    return out
+
+
 def run_reference(args, sysm, rank, world):
     if rank != 0:
         return
@@ -198,7 +233,9 @@ def main():
         dist.init_process_group("nccl")
     prec = {"fp64": dft.DFT_PREC_FP64, "fp16x3": dft.DFT_PREC_FP16X3, "bf16x3": dft.DFT_PREC_BF16X3}[args.precision]
     stream = torch.cuda.current_stream()
+    mixer = {"linear": dft.DFT_MIX_LINEAR, "kerker": dft.DFT_MIX_KERKER, "pulay": dft.DFT_MIX_PULAY}[args.mixer]
     ctx = dft.Context(sysm, device=f"cuda:{local}", precision=prec, cheb_tail_tol=1e-10, mix_alpha=0.3,
+                      mixer=mixer, kerker_q0=0.8, mix_history=8,
                       model=dft.DFT_MODEL_NEUTRAL if args.model == "neutral" else dft.DFT_MODEL_LITERAL)
     ctx.overlap_kinetic()
     n = ctx.initial_density()
@@ -292,6 +329,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": sysm.name, "n_basis": K, "n_atoms": sysm.n_atoms,
                        "grid": [int(x) for x in sysm.grid_n], "kT": sysm.kT, "n_cheb": n_c, "model": args.model,
+                       "mixer": args.mixer + " alpha 0.3" + (" kerker q0 0.8 hist 8" if args.mixer == "pulay" else ""),
                        "precision": args.precision, "l2": "flushed (256 MB write) between timed steps",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": "P-columns/s",
@@ -299,6 +337,8 @@ def main():
             "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
             "stages_ms": [round(x, 3) for x in infos[-1].ms_stage],
             "energy_per_atom": infos[-1].e_total / sysm.n_atoms}
+    if rank == 0 and not args.no_compare:
+        line["mixed_vs_fp64"] = compare_precisions(dft, torch, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(sysm, args.cpu_budget).items()
                                 if k in ("value", "unit", "cores", "kind", "sample")}

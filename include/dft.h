@@ -54,7 +54,10 @@ typedef enum dft_status {
  * collocation and quadrature in FP32 arithmetic. */
 enum { DFT_PREC_FP64 = 0, DFT_PREC_BF16X3 = 1, DFT_PREC_FP16X3 = 2 };
 enum { DFT_MODEL_LITERAL = 0, DFT_MODEL_NEUTRAL = 1 };
-enum { DFT_MIX_LINEAR = 0, DFT_MIX_KERKER = 1 };
+/* Density mixing of the SCF step: linear, Kerker-preconditioned linear, or
+ * Pulay (DIIS, the paper's accelerator, Section 2) on the density residual,
+ * Kerker-preconditioned when kerker_q0 > 0. */
+enum { DFT_MIX_LINEAR = 0, DFT_MIX_KERKER = 1, DFT_MIX_PULAY = 2 };
 
 typedef struct dft_ctx dft_ctx;
 
@@ -95,9 +98,10 @@ typedef struct dft_params {
     double vloc_depth;      /* v_loc = -depth exp(-r^2 / width^2) per atom */
     double vloc_width;
     double ion_charge;      /* ionic charge per atom in the neutral model */
-    int    mixer;           /* DFT_MIX_LINEAR or DFT_MIX_KERKER (density mixing) */
+    int    mixer;           /* DFT_MIX_LINEAR, DFT_MIX_KERKER or DFT_MIX_PULAY */
     double mix_alpha;       /* mixing fraction of the output density */
-    double kerker_q0;       /* Kerker wave number (bohr^-1) for DFT_MIX_KERKER */
+    double kerker_q0;       /* Kerker wave number (bohr^-1); 0 = no preconditioning for Pulay */
+    int    mix_history;     /* Pulay history length (0 -> 8, at most 16) */
     unsigned long long seed;/* Lanczos start vector */
 } dft_params;
 

@@ -14,7 +14,7 @@ import numpy as np
 from . import _binding as B
 from ._binding import (  # noqa: F401
     DftError, dft_basis_desc, dft_grid_desc, dft_info, dft_params,
-    DFT_PREC_FP64, DFT_PREC_BF16X3, DFT_PREC_FP16X3, DFT_MODEL_LITERAL, DFT_MODEL_NEUTRAL, DFT_MIX_LINEAR, DFT_MIX_KERKER,
+    DFT_PREC_FP64, DFT_PREC_BF16X3, DFT_PREC_FP16X3, DFT_MODEL_LITERAL, DFT_MODEL_NEUTRAL, DFT_MIX_LINEAR, DFT_MIX_KERKER, DFT_MIX_PULAY,
     dft_workspace_bytes, dft_init_basis, dft_overlap_kinetic, dft_density_matrix, dft_density_on_grid,
     dft_potential_matrix, dft_hartree_xc, dft_scf_step, dft_initial_density, dft_destroy, dft_last_error,
     dft_version, dft_kernel_launches, dft_spectral_bounds_static,
@@ -23,7 +23,8 @@ from ._binding import (  # noqa: F401
 
 def make_params(*, kT, n_electrons, eta=1e-10, cheb_tail_tol=1e-10, cheb_order=0, precision=DFT_PREC_FP64,
                 e_min=0.0, e_max=0.0, lanczos_steps=64, model=DFT_MODEL_LITERAL, vloc_depth=4.0, vloc_width=1.5,
-                ion_charge=4.0, mixer=DFT_MIX_LINEAR, mix_alpha=0.3, kerker_q0=0.8, seed=1234) -> dft_params:
+                ion_charge=4.0, mixer=DFT_MIX_LINEAR, mix_alpha=0.3, kerker_q0=0.8, mix_history=8,
+                seed=1234) -> dft_params:
     p = dft_params()
     p.beta = 1.0 / kT
     p.n_electrons = n_electrons
@@ -35,7 +36,7 @@ def make_params(*, kT, n_electrons, eta=1e-10, cheb_tail_tol=1e-10, cheb_order=0
     p.lanczos_steps = lanczos_steps
     p.model = model
     p.vloc_depth, p.vloc_width, p.ion_charge = vloc_depth, vloc_width, ion_charge
-    p.mixer, p.mix_alpha, p.kerker_q0 = mixer, mix_alpha, kerker_q0
+    p.mixer, p.mix_alpha, p.kerker_q0, p.mix_history = mixer, mix_alpha, kerker_q0, mix_history
     p.seed = seed
     return p
 

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "DFT_OK", 1: "DFT_EINVAL", 2: "DFT_ENOMEM", 3: "DFT_ECUDA", 4
                 5: "DFT_ENOTCONV", 6: "DFT_ETIMEOUT", 7: "DFT_EINTERNAL", 8: "DFT_EUNSUPPORTED"}
 DFT_PREC_FP64, DFT_PREC_BF16X3, DFT_PREC_FP16X3 = 0, 1, 2
 DFT_MODEL_LITERAL, DFT_MODEL_NEUTRAL = 0, 1
-DFT_MIX_LINEAR, DFT_MIX_KERKER = 0, 1
+DFT_MIX_LINEAR, DFT_MIX_KERKER, DFT_MIX_PULAY = 0, 1, 2
 
 
 class dft_basis_desc(C.Structure):
@@ -37,7 +37,7 @@ class dft_params(C.Structure):
                 ("e_min", C.c_double), ("e_max", C.c_double), ("lanczos_steps", C.c_int), ("model", C.c_int),
                 ("vloc_depth", C.c_double), ("vloc_width", C.c_double), ("ion_charge", C.c_double),
                 ("mixer", C.c_int), ("mix_alpha", C.c_double), ("kerker_q0", C.c_double),
-                ("seed", C.c_ulonglong)]
+                ("mix_history", C.c_int), ("seed", C.c_ulonglong)]
 
 
 class dft_info(C.Structure):

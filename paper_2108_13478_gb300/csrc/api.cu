@@ -61,6 +61,8 @@ void validate(const dft_basis_desc* b, const dft_grid_desc* g, const dft_params*
     if (p->precision != DFT_PREC_FP64 && p->precision != DFT_PREC_BF16X3 && p->precision != DFT_PREC_FP16X3)
         throw Error(DFT_EINVAL, "unknown precision");
     if (p->cheb_order <= 0 && !(p->cheb_tail_tol > 0.0)) throw Error(DFT_EINVAL, "cheb_tail_tol must be positive");
+    if (p->mixer < DFT_MIX_LINEAR || p->mixer > DFT_MIX_PULAY) throw Error(DFT_EINVAL, "unknown mixer");
+    if (p->mix_history < 0 || p->mix_history > 16) throw Error(DFT_EINVAL, "mix_history must be in [0, 16]");
 }
 
 // functions, windows, tables and tile lists (host part of the set-up)
@@ -131,7 +133,8 @@ void build_basis(Ctx& c, const dft_basis_desc* b, const dft_grid_desc* g, const 
         c.Kp = tc_pad(c.K);
         c.n_tc_tiles = (int)(tc_tiles(c.K).size() / 2);
     }
-    c.part_cap = std::max<long long>({2LL * cheb_step_parts(c.K), 2LL * c.n_tc_tiles, 3LL * 1184, 2048}) + 64;
+    c.part_cap = std::max<long long>({2LL * cheb_step_parts(c.K), 2LL * c.n_tc_tiles, 3LL * 1184, 2048, 592LL * 16}) + 64;
+    c.pl_hist = c.p.mixer == DFT_MIX_PULAY ? (c.p.mix_history > 0 ? c.p.mix_history : 8) : 0;
 }
 
 // carve the workspace; with base == nullptr only the size is computed
@@ -162,6 +165,7 @@ size_t carve(Ctx& c, char* base) {
     size_t o_fc = L.off(sizeof(cufftDoubleComplex) * c.nfft_c);
     size_t o_kw = L.off(sizeof(double) * nkc);
     size_t o_kc = L.off(sizeof(cufftDoubleComplex) * nkc);
+    size_t o_pl = c.pl_hist > 0 ? L.off(sizeof(double) * 2 * (size_t)c.pl_hist * c.ng) : 0;
     size_t o_h16[2] = {0, 0}, o_x16[4] = {0, 0, 0, 0}, o_rtc = 0, o_tiles = 0;
     if (c.Kp > 0) {
         size_t P16 = (size_t)c.Kp * c.Kp * 2;
@@ -195,6 +199,7 @@ size_t carve(Ctx& c, char* base) {
         c.d_fft_c = (cufftDoubleComplex*)(base + o_fc);
         c.d_kerker = (double*)(base + o_kw);
         c.d_kc = (cufftDoubleComplex*)(base + o_kc);
+        if (c.pl_hist > 0) c.d_pulay = (double*)(base + o_pl);
         if (c.Kp > 0) {
             for (int q = 0; q < 2; ++q) c.d_h16[q] = base + o_h16[q];
             for (int q = 0; q < 4; ++q) c.d_x16[q] = base + o_x16[q];
@@ -244,6 +249,80 @@ struct Timer {
 void read_flags(Ctx& c, cudaStream_t s, int* flags) {
     DFT_CUDA_CHECK(cudaMemcpyAsync(flags, c.d_flags, sizeof(int) * FLAG_COUNT, cudaMemcpyDeviceToHost, s));
     DFT_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+// Pulay coefficients: minimise |sum c_i R_i| subject to sum c_i = 1, i.e. the
+// bordered system [B -1; -1^T 0][c; l] = [0; -1], by Gaussian elimination
+// with partial pivoting; false if singular
+bool solve_pulay(int m, const std::vector<double>& B, std::vector<double>* c) {
+    int n = m + 1;
+    std::vector<double> A((size_t)n * (n + 1), 0.0);
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) A[(size_t)i * (n + 1) + j] = B[(size_t)i * m + j];
+        A[(size_t)i * (n + 1) + m] = -1.0;
+        A[(size_t)m * (n + 1) + i] = -1.0;
+    }
+    A[(size_t)m * (n + 1) + n] = -1.0;
+    double scale = 0.0;
+    for (int i = 0; i < m; ++i) scale = std::max(scale, std::fabs(B[(size_t)i * m + i]));
+    if (!(scale > 0.0)) return false;
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::fabs(A[(size_t)r * (n + 1) + col]) > std::fabs(A[(size_t)piv * (n + 1) + col])) piv = r;
+        double pv = A[(size_t)piv * (n + 1) + col];
+        if (!(std::fabs(pv) > 1e-14 * scale)) return false;
+        if (piv != col)
+            for (int k = 0; k <= n; ++k) std::swap(A[(size_t)piv * (n + 1) + k], A[(size_t)col * (n + 1) + k]);
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            double f = A[(size_t)r * (n + 1) + col] / pv;
+            if (f == 0.0) continue;
+            for (int k = col; k <= n; ++k) A[(size_t)r * (n + 1) + k] -= f * A[(size_t)col * (n + 1) + k];
+        }
+    }
+    c->assign(m, 0.0);
+    for (int i = 0; i < m; ++i) {
+        (*c)[i] = A[(size_t)i * (n + 1) + n] / A[(size_t)i * (n + 1) + i];
+        if (!std::isfinite((*c)[i])) return false;
+    }
+    return true;
+}
+
+// Pulay (DIIS) update of the input density from the history ring
+void pulay_mix(Ctx& c, double* n_in, const double* n_out, cudaStream_t s) {
+    const int H = c.pl_hist;
+    const int slot = (int)(c.pl_count % H);
+    pulay_store(c, slot, n_in, n_out, s);
+    c.pl_count++;
+    const int m = (int)std::min<long long>(c.pl_count, H);
+    // new row of B: <R_slot, R_j> for the m filled slots (slots 0..m-1)
+    pulay_dots(c, m, slot, c.d_scal + SCAL_PULAY, s);
+    std::vector<double> row(m);
+    DFT_CUDA_CHECK(cudaMemcpyAsync(row.data(), c.d_scal + SCAL_PULAY, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    DFT_CUDA_CHECK(cudaStreamSynchronize(s));
+    for (int j = 0; j < m; ++j) {
+        c.pl_B[(size_t)slot * H + j] = row[j];
+        c.pl_B[(size_t)j * H + slot] = row[j];
+    }
+    // oldest entries are dropped until the system is solvable
+    std::vector<int> act;
+    for (int k = 0; k < m; ++k) act.push_back((int)((c.pl_count - m + k) % H));
+    std::vector<double> coef;
+    while (true) {
+        int mm = (int)act.size();
+        std::vector<double> B((size_t)mm * mm);
+        for (int i = 0; i < mm; ++i)
+            for (int j = 0; j < mm; ++j) B[(size_t)i * mm + j] = c.pl_B[(size_t)act[i] * H + act[j]];
+        if (solve_pulay(mm, B, &coef) || mm == 1) break;
+        act.erase(act.begin());
+    }
+    if (act.size() == 1) coef.assign(1, 1.0);
+    std::vector<double> full(H, 0.0);
+    for (size_t i = 0; i < act.size(); ++i) full[act[i]] = coef[i];
+    DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_scal + SCAL_PULAY + 16, full.data(), sizeof(double) * H,
+                                   cudaMemcpyHostToDevice, s));
+    pulay_update(c, m, c.d_scal + SCAL_PULAY + 16, n_in, s);
 }
 
 // N_C = smallest order whose coefficient tail (at mu = Ebar, the slowest
@@ -428,7 +507,9 @@ dft_status dft_init_basis(dft_ctx** ctx, const dft_basis_desc* basis, const dft_
         double w = c->p.vloc_width;
         launch_gaussian_sum(*c, c->p.ion_charge * std::pow(M_PI * w * w, -1.5), w, c->d_nion, s);
         poisson_setup(*c, s);
-        if (c->p.mixer == DFT_MIX_KERKER) kerker_setup(*c, s);
+        if (c->p.mixer == DFT_MIX_KERKER || (c->p.mixer == DFT_MIX_PULAY && c->p.kerker_q0 > 0.0))
+            kerker_setup(*c, s);
+        c->pl_B.assign((size_t)c->pl_hist * c->pl_hist, 0.0);
         DFT_CUDA_CHECK(cudaStreamSynchronize(s));
     });
     if (st != DFT_OK) {
@@ -549,6 +630,7 @@ dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double
         if (P_out) DFT_CUDA_CHECK(cudaMemcpyAsync(P_out, c.d_P, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
         // mixing
         if (c.p.mixer == DFT_MIX_KERKER) kerker_mix(c, n_in_out, c.d_nout, c.p.mix_alpha, s);
+        else if (c.p.mixer == DFT_MIX_PULAY) pulay_mix(c, n_in_out, c.d_nout, s);
         else launch_linear_mix(c.ng, n_in_out, c.d_nout, c.p.mix_alpha, s);
         double sc[SCAL_COUNT];
         DFT_CUDA_CHECK(cudaMemcpyAsync(sc, c.d_scal, sizeof(sc), cudaMemcpyDeviceToHost, s));

@@ -94,6 +94,12 @@ struct Ctx {
     CUtensorMap tm_h[2];
     CUtensorMap tm_x[4];
 
+    // Pulay mixing: ring of pl_hist inputs then pl_hist residuals, [2 pl_hist][ng]
+    double* d_pulay = nullptr;
+    int pl_hist = 0;
+    long long pl_count = 0;
+    std::vector<double> pl_B;    // cached <R_i, R_j>, pl_hist x pl_hist
+
     cufftHandle plan_f = 0, plan_b = 0;
     cufftHandle kplan_f = 0, kplan_b = 0;
     bool have_chol = false;
@@ -108,8 +114,14 @@ enum {
     SCAL_ALPHA = 0,      // Lanczos alpha_j at SCAL_ALPHA + j (j < 128)
     SCAL_BETA = 128,     // Lanczos beta_j
     SCAL_MU = 256,
-    SCAL_EMIN, SCAL_EMAX, SCAL_NE, SCAL_TRACE, SCAL_EKIN, SCAL_RES,
-    SCAL_E0, SCAL_E1, SCAL_E2,        // grid energy terms
+    SCAL_EMIN = 257,
+    SCAL_EMAX = 258,
+    SCAL_NE = 259,
+    SCAL_TRACE = 260,    // two slots: trace and squared norm of H_N
+    SCAL_EKIN = 262,
+    SCAL_RES = 263,
+    SCAL_E0 = 264, SCAL_E1 = 265, SCAL_E2 = 266,   // grid energy terms
+    SCAL_PULAY = 268,    // 16 Pulay dots, then 16 coefficients
     SCAL_COUNT = 300
 };
 enum { FLAG_SPECTRUM = 0, FLAG_CHOL = 1, FLAG_MU = 2, FLAG_TIMEOUT = 3, FLAG_COUNT = 8 };
@@ -178,6 +190,10 @@ void hartree_xc(Ctx& c, const double* n, double* vks, bool energies, cudaStream_
 void kerker_setup(Ctx& c, cudaStream_t s);
 void kerker_mix(Ctx& c, double* n_in, const double* n_out, double alpha, cudaStream_t s);
 void launch_linear_mix(long long ng, double* n_in, const double* n_out, double alpha, cudaStream_t s);
+void kerker_apply(Ctx& c, double* r, cudaStream_t s);
+void pulay_store(Ctx& c, int slot, const double* n_in, const double* n_out, cudaStream_t s);
+void pulay_dots(Ctx& c, int m, int slot, double* out, cudaStream_t s);
+void pulay_update(Ctx& c, int m, const double* coef_dev, double* n_in, cudaStream_t s);
 void launch_maxabs_diff(long long ng, const double* a, const double* b, double* part, double* out,
                         cudaStream_t s);
 

@@ -176,6 +176,55 @@ __global__ void k_kerker_weights(int nx, int ny, int nz, double h, double q0, do
     w[e] = g2 / (g2 + q0 * q0) / ((double)nx * ny * nz);
 }
 
+// partial sums of <R_i, R_new> for the m ring slots (Pulay's B matrix row)
+constexpr int PMAX = 16;
+__global__ void __launch_bounds__(256) k_ring_dots(long long ng, int m, const double* __restrict__ ring,
+                                                   const double* __restrict__ rn, double* part) {
+    double acc[PMAX];
+#pragma unroll
+    for (int i = 0; i < PMAX; ++i) acc[i] = 0.0;
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < ng; e += (long long)gridDim.x * 256) {
+        double r = rn[e];
+#pragma unroll
+        for (int i = 0; i < PMAX; ++i)
+            if (i < m) acc[i] = fma(ring[(long long)i * ng + e], r, acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < PMAX; ++i) {
+        if (i >= m) break;
+        double v = block_sum<256>(acc[i]);
+        if (threadIdx.x == 0) part[(long long)blockIdx.x * PMAX + i] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ring_dots_reduce(int np, int m, const double* part, double* out) {
+    for (int i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < np; b += 256) s += part[(long long)b * PMAX + i];
+        s = block_sum<256>(s);
+        if (threadIdx.x == 0) out[i] = s;
+    }
+}
+
+// x = sum_i c_i x_i, r = sum_i c_i R_i over the ring
+__global__ void k_ring_combine(long long ng, int m, const double* __restrict__ rx, const double* __restrict__ rr,
+                               const double* __restrict__ c, double* __restrict__ x, double* __restrict__ r) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ng) return;
+    double sx = 0.0, sr = 0.0;
+    for (int i = 0; i < m; ++i) {
+        sx = fma(c[i], rx[(long long)i * ng + e], sx);
+        sr = fma(c[i], rr[(long long)i * ng + e], sr);
+    }
+    x[e] = sx;
+    r[e] = sr;
+}
+
+__global__ void k_axpy_grid(long long n, double* y, const double* x, const double* r, double a) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) y[e] = x[e] + a * r[e];
+}
+
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 void cufft_check(cufftResult r, const char* what) {
@@ -238,6 +287,44 @@ void kerker_mix(Ctx& c, double* n_in, const double* n_out, double alpha, cudaStr
     cufft_check(cufftExecZ2D(c.kplan_b, c.d_kc, c.d_gtmp), "kerker Z2D");
     k_add_scaled<<<blocks_for(c.ng, 256), 256, 0, s>>>(c.ng, n_in, c.d_gtmp, alpha);
     check_launch("kerker_mix", 3);
+}
+
+// Kerker filter applied in place to a grid field
+void kerker_apply(Ctx& c, double* r, cudaStream_t s) {
+    cufft_check(cufftSetStream(c.kplan_f, s), "stream");
+    cufft_check(cufftSetStream(c.kplan_b, s), "stream");
+    long long nc = (long long)(c.n[0] / 2 + 1) * c.n[1] * c.n[2];
+    cufft_check(cufftExecD2Z(c.kplan_f, r, c.d_kc), "kerker D2Z");
+    k_mul_real<<<blocks_for(nc, 256), 256, 0, s>>>(nc, c.d_kc, c.d_kerker);
+    cufft_check(cufftExecZ2D(c.kplan_b, c.d_kc, r), "kerker Z2D");
+    check_launch("kerker_apply");
+}
+
+void pulay_store(Ctx& c, int slot, const double* n_in, const double* n_out, cudaStream_t s) {
+    double* x = c.d_pulay + (size_t)slot * c.ng;
+    double* r = c.d_pulay + (size_t)(c.pl_hist + slot) * c.ng;
+    DFT_CUDA_CHECK(cudaMemcpyAsync(x, n_in, sizeof(double) * c.ng, cudaMemcpyDeviceToDevice, s));
+    k_residual<<<blocks_for(c.ng, 256), 256, 0, s>>>(c.ng, n_in, n_out, r);
+    check_launch("pulay_store");
+}
+
+void pulay_dots(Ctx& c, int m, int slot, double* out, cudaStream_t s) {
+    int np = (int)std::min<long long>(592, (c.ng + 255) / 256);
+    const double* ring = c.d_pulay + (size_t)c.pl_hist * c.ng;
+    k_ring_dots<<<np, 256, 0, s>>>(c.ng, m, ring, ring + (size_t)slot * c.ng, c.d_part);
+    k_ring_dots_reduce<<<1, 256, 0, s>>>(np, m, c.d_part, out);
+    check_launch("pulay_dots", 2);
+}
+
+// n_in = sum c_i x_i + alpha K[sum c_i R_i]
+void pulay_update(Ctx& c, int m, const double* coef_dev, double* n_in, cudaStream_t s) {
+    const double* rx = c.d_pulay;
+    const double* rr = c.d_pulay + (size_t)c.pl_hist * c.ng;
+    k_ring_combine<<<blocks_for(c.ng, 256), 256, 0, s>>>(c.ng, m, rx, rr, coef_dev, n_in, c.d_gtmp);
+    check_launch("pulay_combine");
+    if (c.p.kerker_q0 > 0.0) kerker_apply(c, c.d_gtmp, s);
+    k_axpy_grid<<<blocks_for(c.ng, 256), 256, 0, s>>>(c.ng, n_in, n_in, c.d_gtmp, c.p.mix_alpha);
+    check_launch("pulay_axpy");
 }
 
 void launch_linear_mix(long long ng, double* n_in, const double* n_out, double alpha, cudaStream_t s) {

@@ -55,7 +55,7 @@ def test_struct_sizes_match_header(built):
 #include "dft.h"
 int main(){printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dft_basis_desc), sizeof(dft_grid_desc),
  sizeof(dft_params), sizeof(dft_info), offsetof(dft_params, seed), offsetof(dft_info, ms_stage),
- offsetof(dft_params, kerker_q0));return 0;}
+ offsetof(dft_params, kerker_q0) + offsetof(dft_params, mix_history) * 1000);return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
@@ -65,7 +65,7 @@ int main(){printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dft_basis_desc), sizeo
         out = [int(x) for x in subprocess.check_output([exe]).split()]
     got = [ctypes.sizeof(B.dft_basis_desc), ctypes.sizeof(B.dft_grid_desc), ctypes.sizeof(B.dft_params),
            ctypes.sizeof(B.dft_info), B.dft_params.seed.offset, B.dft_info.ms_stage.offset,
-           B.dft_params.kerker_q0.offset]
+           B.dft_params.kerker_q0.offset + B.dft_params.mix_history.offset * 1000]
     assert got == out
 
 

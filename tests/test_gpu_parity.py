@@ -250,3 +250,22 @@ def test_invalid_arguments_return_status(tiny):
     ctx.close()
     with pytest.raises(dft.DftError):
         dft.Context(s, eta=2.0)
+
+
+def test_scf_pulay_steps(tiny):
+    """Pulay (DIIS) mixing with Kerker preconditioning: four cycles against
+    the oracle's Pulay mixer on the same inputs."""
+    s, st = tiny
+    ctx = dft.Context(s, cheb_tail_tol=1e-11, mixer=dft.DFT_MIX_PULAY, mix_alpha=0.3, kerker_q0=0.8,
+                      mix_history=8)
+    ctx.overlap_kinetic()
+    n = ctx.initial_density()
+    mix = scf.Pulay(alpha=0.3, hist=8, precond=scf.kerker(s, 0.8))
+    n_ref = scf.ion_density(s)
+    for _ in range(4):
+        info = ctx.scf_step(n)
+        r = scf.step(st, n_ref)
+        assert abs(info.e_total - r["E"]["total"]) / s.n_atoms < 1e-6
+        n_ref = mix(n_ref, r["n_out"])
+        assert np.max(np.abs(host(n) - n_ref)) < 1e-6
+    ctx.close()

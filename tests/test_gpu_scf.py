@@ -1,0 +1,56 @@
+"""Converged SCF energies of the GPU paths against the FP64 oracle.
+
+The oracle's converged energies are stored in tests/golden/scf_<name>.json by
+tests/golden/make_scf_golden.py (oracle only).  Both GPU precisions run the
+same model (charge-neutral), start (superposition of atoms) and mixer
+(Pulay + Kerker) to |dE|/atom < 1e-8 and max|n_out - n_in| < 1e-5; the gate
+is the method's target, 1e-5 Ha/atom.
+"""
+import json
+import os
+
+import pytest
+
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2108_13478_gb300 as dft  # noqa: E402
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    p = os.path.join(GOLD, f"scf_{name}.json")
+    if not os.path.exists(p):
+        pytest.skip(f"no oracle golden energy for {name}")
+    g = json.load(open(p))
+    assert g["converged"]
+    return g
+
+
+@pytest.mark.parametrize("name,prec", [("tiny8", "fp64"), ("tiny8", "fp16x3"),
+                                       ("cluster64", "fp16x3"), ("cluster64", "fp64")])
+def test_converged_energy(name, prec):
+    g = golden(name)
+    s = w.config_system(name)
+    p = dft.DFT_PREC_FP64 if prec == "fp64" else dft.DFT_PREC_FP16X3
+    ctx = dft.Context(s, precision=p, model=dft.DFT_MODEL_NEUTRAL, mixer=dft.DFT_MIX_PULAY, mix_alpha=0.3,
+                      kerker_q0=0.8, mix_history=8, cheb_tail_tol=1e-10)
+    ctx.overlap_kinetic()
+    n = ctx.initial_density()
+    info = None
+    for it in range(100):
+        info = ctx.scf_step(n)
+        if it > 0 and abs(info.de_per_atom) < 1e-8 and info.residual < 1e-5:
+            break
+    e = info.e_total / s.n_atoms
+    print(f"{name} {prec}: {it + 1} cycles, E/atom {e:.10f} vs oracle {g['E_per_atom']:.10f} "
+          f"({g['iterations']} cycles), |dE| {abs(e - g['E_per_atom']):.2e}")
+    assert abs(info.de_per_atom) < 1e-7
+    assert abs(e - g["E_per_atom"]) < 1e-5
+    ctx.close()
