@@ -177,6 +177,20 @@ dft_status dft_hartree_xc(dft_ctx* ctx, const double* n_grid, double* v_ks, doub
 dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double* P_out,
                         dft_info* info, void* stream);
 
+/* One SCF cycle for each of n independent systems (at most 64), e.g.
+ * clusters of uneven basis size.  Every context must use the same mixed
+ * precision (DFT_PREC_FP16X3 or DFT_PREC_BF16X3).  The per-system stages run
+ * one after another on `stream`; the two Chebyshev passes of all systems are
+ * merged: one persistent tensor-core launch per recurrence step walks the
+ * tiles of every system still inside its own N_C, so ragged K share the SMs.
+ * The launch sequences of both passes are captured once in CUDA graphs and
+ * replayed while the step counts stay the same.  ctxs[0] holds the batch
+ * tables (system table, tensor maps, up to 131072 tiles) and the graphs.
+ * n_in_out[q]: device density of system q, updated as by dft_scf_step;
+ * infos (host, may be NULL) receives n results (stage times are shared). */
+dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in_out, dft_info* infos,
+                                void* stream);
+
 /* Superposition-of-atoms start density (Supp. A.3: "sum of atomic
  * densities"): a normalised Gaussian of ion_charge electrons and width
  * vloc_width on every atom.  n_grid device grid, overwritten. */

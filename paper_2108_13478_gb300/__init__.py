@@ -17,7 +17,7 @@ from ._binding import (  # noqa: F401
     DFT_PREC_FP64, DFT_PREC_BF16X3, DFT_PREC_FP16X3, DFT_MODEL_LITERAL, DFT_MODEL_NEUTRAL, DFT_MIX_LINEAR, DFT_MIX_KERKER, DFT_MIX_PULAY,
     dft_workspace_bytes, dft_init_basis, dft_overlap_kinetic, dft_density_matrix, dft_density_on_grid,
     dft_potential_matrix, dft_hartree_xc, dft_scf_step, dft_initial_density, dft_destroy, dft_last_error,
-    dft_version, dft_kernel_launches, dft_spectral_bounds_static,
+    dft_version, dft_kernel_launches, dft_spectral_bounds_static, dft_scf_step_batched,
 )
 
 

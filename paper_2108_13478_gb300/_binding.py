@@ -66,6 +66,7 @@ SIGNATURES = [
     ("dft_hartree_xc", C.c_int, [_P, _P, _P, C.POINTER(C.c_double), _P]),
     ("dft_scf_step", C.c_int, [_P, _P, _P, _P, C.POINTER(dft_info), _P]),
     ("dft_initial_density", C.c_int, [_P, _P, _P]),
+    ("dft_scf_step_batched", C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P), C.POINTER(dft_info), _P]),
     ("dft_destroy", C.c_int, [_P]),
     ("dft_last_error", C.c_char_p, [_P]),
     ("dft_version", C.c_char_p, []),
@@ -157,6 +158,18 @@ def dft_scf_step(ctx, n_in_out, v_ks_out=None, P_out=None, stream=None) -> dft_i
     info = dft_info()
     _check(ctx, lib.dft_scf_step(ctx, _ptr(n_in_out), _ptr(v_ks_out), _ptr(P_out), C.byref(info), _stream(stream)))
     return info
+
+
+def dft_scf_step_batched(ctxs, n_in_out, stream=None):
+    """One SCF step for several contexts; returns their dft_info results."""
+    n = len(ctxs)
+    carr = (_P * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    narr = (_P * n)(*[t.data_ptr() for t in n_in_out])
+    infos = (dft_info * n)()
+    st = lib.dft_scf_step_batched(carr, n, narr, infos, _stream(stream))
+    if st != DFT_OK:
+        raise DftError(st, lib.dft_last_error(carr[0]).decode())
+    return list(infos)
 
 
 def dft_initial_density(ctx, n_grid, stream=None):

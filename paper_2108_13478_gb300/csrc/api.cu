@@ -132,8 +132,9 @@ void build_basis(Ctx& c, const dft_basis_desc* b, const dft_grid_desc* g, const 
     if (c.p.precision != DFT_PREC_FP64) {
         c.Kp = tc_pad(c.K);
         c.n_tc_tiles = (int)(tc_tiles(c.K).size() / 2);
+        c.tile_cap = std::max(c.n_tc_tiles, 1 << 17);
     }
-    c.part_cap = std::max<long long>({2LL * cheb_step_parts(c.K), 2LL * c.n_tc_tiles, 3LL * 1184, 2048, 592LL * 16}) + 64;
+    c.part_cap = std::max<long long>({2LL * cheb_step_parts(c.K), 2LL * c.tile_cap, 3LL * 1184, 2048, 592LL * 16}) + 64;
     c.pl_hist = c.p.mixer == DFT_MIX_PULAY ? (c.p.mix_history > 0 ? c.p.mix_history : 8) : 0;
 }
 
@@ -166,13 +167,15 @@ size_t carve(Ctx& c, char* base) {
     size_t o_kw = L.off(sizeof(double) * nkc);
     size_t o_kc = L.off(sizeof(cufftDoubleComplex) * nkc);
     size_t o_pl = c.pl_hist > 0 ? L.off(sizeof(double) * 2 * (size_t)c.pl_hist * c.ng) : 0;
-    size_t o_h16[2] = {0, 0}, o_x16[4] = {0, 0, 0, 0}, o_rtc = 0, o_tiles = 0;
+    size_t o_h16[2] = {0, 0}, o_x16[4] = {0, 0, 0, 0}, o_rtc = 0, o_tiles = 0, o_systab = 0, o_maps = 0;
     if (c.Kp > 0) {
         size_t P16 = (size_t)c.Kp * c.Kp * 2;
         for (auto& o : o_h16) o = L.off(P16);
         for (auto& o : o_x16) o = L.off(P16);
         o_rtc = L.off((size_t)c.Kp * c.Kp * sizeof(double));
-        o_tiles = L.off(sizeof(int) * 2 * (size_t)c.n_tc_tiles);
+        o_systab = L.off(sizeof(TcSys) * TC_MAX_SYS);
+        o_maps = L.off(sizeof(CUtensorMap) * TC_MAPS_PER_SYS * TC_MAX_SYS);
+        o_tiles = L.off(sizeof(TcTile) * (size_t)c.tile_cap);
     }
     if (base) {
         c.d_fn = (Fn*)(base + o_fn);
@@ -204,7 +207,9 @@ size_t carve(Ctx& c, char* base) {
             for (int q = 0; q < 2; ++q) c.d_h16[q] = base + o_h16[q];
             for (int q = 0; q < 4; ++q) c.d_x16[q] = base + o_x16[q];
             c.d_rho_tc = (double*)(base + o_rtc);
-            c.d_tiles = (int*)(base + o_tiles);
+            c.d_systab = (TcSys*)(base + o_systab);
+            c.d_maps = (CUtensorMap*)(base + o_maps);
+            c.d_tiles = (TcTile*)(base + o_tiles);
         }
     }
     return L.total;
@@ -347,17 +352,19 @@ int auto_order(Ctx& c, double emin, double emax, cudaStream_t s) {
     return std::max(nc, 2);
 }
 
-// P = f(S^-1 F) S^-1 through the symmetric Chebyshev recurrence (Supp. B)
-void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cudaStream_t s, Timer* tm,
-                         int t0) {
+// ---- the density matrix in phases (Supp. B); batched SCF steps interleave them ----
+
+// number of moments-pass steps j = 1..J with 2j + 1 <= N_C - 1
+inline int pass1_steps(int n_c) { return n_c >= 2 ? (n_c - 2) / 2 : 0; }
+
+// F~ = L^-1 F L^-T, spectral bounds, N_C, H_N, and m_0, m_1, m_2
+void dm_prepare(Ctx& c, const double* F, cudaStream_t s, Timer* tm, int t0) {
     if (!c.have_chol) throw Error(DFT_EINVAL, "call dft_overlap_kinetic first");
     const int K = c.K;
     DFT_CUDA_CHECK(cudaMemsetAsync(c.d_flags, 0, sizeof(int) * FLAG_COUNT, s));
     if (tm) tm->mark(t0);
-    // F~ = L^-1 F L^-T
     congruence_lower(K, c.d_Linv, F, c.d_B, c.d_A, s);
     if (tm) tm->mark(t0 + 1);
-    // spectral bounds of S^-1 F
     if (c.p.e_max > c.p.e_min) {
         double b[2] = {c.p.e_min, c.p.e_max};
         DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_scal + SCAL_EMIN, b, sizeof(b), cudaMemcpyHostToDevice, s));
@@ -368,17 +375,17 @@ void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cud
     DFT_CUDA_CHECK(cudaMemcpyAsync(eb, c.d_scal + SCAL_EMIN, sizeof(eb), cudaMemcpyDeviceToHost, s));
     DFT_CUDA_CHECK(cudaStreamSynchronize(s));
     if (!(eb[1] > eb[0])) throw Error(DFT_ESPECTRUM, "degenerate spectral bounds");
+    c.e_bounds[0] = eb[0];
+    c.e_bounds[1] = eb[1];
     launch_normalise_h(K, c.d_A, c.d_scal, c.d_H, s);
     int n_c = c.p.cheb_order > 0 ? c.p.cheb_order : auto_order(c, eb[0], eb[1], s);
     if (n_c < 2 || n_c > c.cheb_cap) throw Error(DFT_EINVAL, "Chebyshev order out of range");
-    const int M = 4 * n_c;
-    launch_cos_table(M, c.d_cos, s);
+    c.n_c_cur = n_c;
+    launch_cos_table(4 * n_c, c.d_cos, s);
     if (tm) tm->mark(t0 + 2);
-    const bool tcp = c.p.precision != DFT_PREC_FP64;
-    // pass 1: moments m_l = Tr T_l(H_N), l < N_C, by doubling
     double m0 = (double)K;
     DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_mom, &m0, sizeof(double), cudaMemcpyHostToDevice, s));
-    if (tcp) {
+    if (c.p.precision != DFT_PREC_FP64) {
         // split H_N into its 16-bit pair; trace and |H|^2 of the pair
         tc_split_h(c, s);
         tc_init(c, nullptr, s);
@@ -392,65 +399,209 @@ void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cud
     }
     DFT_CUDA_CHECK(cudaMemsetAsync(c.d_scal + SCAL_TRACE + 1, 0, sizeof(double), s));
     if (n_c > 2) launch_moment_reduce(1, c.d_scal + SCAL_TRACE, c.d_mom, 2, -1, m0, c.d_mom + 1, s);
-    int nparts = tcp ? c.n_tc_tiles : cheb_step_parts(K);
+}
+
+// moments-pass steps j0..J of a tensor-core batch; when the launch shape of
+// this (precision, size) has not been tuned yet, the first steps run each
+// candidate shape on three real steps, timed by events, and the fastest is
+// kept for the rest (no step is repeated).  Returns the first step not run.
+int tc_pass1_tuned(TcBatch& b, int total_k, int J, cudaStream_t s) {
+    int j = 1;
+    TcCfg cand[4];
+    const int nc = tc_candidates(cand);
+    const int per = 3;
+    if (tc_needs_tuning(b, total_k) && J >= nc * per + 4) {
+        float ms[4];
+        cudaEvent_t e0, e1;
+        DFT_CUDA_CHECK(cudaEventCreate(&e0));
+        DFT_CUDA_CHECK(cudaEventCreate(&e1));
+        for (int i = 0; i < nc; ++i) {
+            b.cfg = cand[i];
+            DFT_CUDA_CHECK(cudaEventRecord(e0, s));
+            for (int r = 0; r < per; ++r, ++j) {
+                tc_step_batch(b, j, j & 1, 2, s);
+                tc_moment_reduce_batch(b, j, s);
+            }
+            DFT_CUDA_CHECK(cudaEventRecord(e1, s));
+            DFT_CUDA_CHECK(cudaEventSynchronize(e1));
+            DFT_CUDA_CHECK(cudaEventElapsedTime(&ms[i], e0, e1));
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        int best = 0;
+        for (int i = 1; i < nc; ++i)
+            if (ms[i] < ms[best]) best = i;
+        tc_record(b, total_k, cand[best], ms, nc);
+    }
+    b.cfg = tc_tuned(b, total_k);
+    return j;
+}
+
+// moments pass of one system: m_l = Tr T_l(H_N), l < N_C, by doubling
+void dm_pass1(Ctx& c, cudaStream_t s) {
+    const int K = c.K, n_c = c.n_c_cur, J = pass1_steps(n_c);
+    if (c.p.precision != DFT_PREC_FP64) {
+        Ctx* cp = &c;
+        int lim = J + 1, last = J;
+        TcBatch b = tc_batch(c, &cp, 1, &lim, &last, s);
+        tc_set_limits(b, &cp, &lim, &last, s);
+        for (int j = tc_pass1_tuned(b, K, J, s); j <= J; ++j) {
+            tc_step_batch(b, j, j & 1, 2, s);
+            tc_moment_reduce_batch(b, j, s);
+        }
+        c.tc_cfg = b.cfg;
+        return;
+    }
+    const double m0 = (double)K;
+    int nparts = cheb_step_parts(K);
     double* cur = c.d_X1;
     double* prev = c.d_X0;
-    int tcur = 1;   // tensor-core path: pair index holding X_l
-    for (int j = 1; 2 * j + 1 <= n_c - 1; ++j) {
-        if (tcp) {
-            tc_step(c, tcur, nullptr, nullptr, 0, c.d_part, s);
-            tcur = 1 - tcur;
-        } else {
-            launch_cheb_step_fp64(K, c.d_H, cur, prev, nullptr, nullptr, 0, c.d_part, c.d_flags, s);
-            std::swap(cur, prev);
-        }
+    for (int j = 1; j <= J; ++j) {
+        launch_cheb_step_fp64(K, c.d_H, cur, prev, nullptr, nullptr, 0, c.d_part, c.d_flags, s);
+        std::swap(cur, prev);
         launch_moment_reduce(nparts, c.d_part, c.d_mom, (2 * j + 2 < n_c) ? 2 * j + 2 : -1, 2 * j + 1, m0,
                              c.d_mom + 1, s);
     }
-    // mu from 2 sum_l a_l(mu) m_l = N_e (Eq. 2.8), then the coefficients
+}
+
+// mu from 2 sum_l a_l(mu) m_l = N_e (Eq. 2.8), then the coefficients
+void dm_mu(Ctx& c, cudaStream_t s) {
+    const int n_c = c.n_c_cur, M = 4 * n_c;
     launch_moment_weights(n_c, M, c.d_cos, c.d_mom, c.d_wk, s);
     launch_mu_bisect(M, c.d_cos, c.d_wk, c.p.beta, c.p.n_electrons, c.d_scal, c.d_flags, s);
     launch_cheb_coeffs(n_c, M, c.d_cos, c.d_scal, c.p.beta, 0.0, false, c.d_coef, s);
-    if (tm) tm->mark(t0 + 3);
-    // pass 2: rho = sum_l a_l X_l
-    if (tcp) {
+}
+
+// weighted pass of one system: rho = sum_l a_l X_l
+void dm_pass2(Ctx& c, cudaStream_t s) {
+    const int K = c.K, n_c = c.n_c_cur;
+    if (c.p.precision != DFT_PREC_FP64) {
         tc_init(c, c.d_coef, s);
-        tcur = 1;
-        for (int l = 2; l < n_c; ++l) {
-            tc_step(c, tcur, c.d_rho_tc, c.d_coef, l, nullptr, s);
-            tcur = 1 - tcur;
-        }
+        Ctx* cp = &c;
+        int lim = n_c, last = 0;
+        TcBatch b = tc_batch(c, &cp, 1, &lim, &last, s);
+        b.cfg = c.tc_cfg;
+        tc_set_limits(b, &cp, &lim, &last, s);
+        for (int l = 2; l < n_c; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, s);
         tc_rho_finish(c, s);
-    } else {
-        launch_cheb_init(K, c.d_H, c.d_X0, c.d_X1, c.d_rho, c.d_coef, s);
-        cur = c.d_X1;
-        prev = c.d_X0;
-        for (int l = 2; l < n_c; ++l) {
-            launch_cheb_step_fp64(K, c.d_H, cur, prev, c.d_rho, c.d_coef, l, nullptr, c.d_flags, s);
-            std::swap(cur, prev);
-        }
+        return;
     }
-    if (tm) tm->mark(t0 + 4);
-    // P = L^-T rho L^-1
+    launch_cheb_init(K, c.d_H, c.d_X0, c.d_X1, c.d_rho, c.d_coef, s);
+    double* cur = c.d_X1;
+    double* prev = c.d_X0;
+    for (int l = 2; l < n_c; ++l) {
+        launch_cheb_step_fp64(K, c.d_H, cur, prev, c.d_rho, c.d_coef, l, nullptr, c.d_flags, s);
+        std::swap(cur, prev);
+    }
+}
+
+// P = L^-T rho L^-1, electron count, status flags
+void dm_finish(Ctx& c, double* P, dft_info* info, cudaStream_t s) {
+    const int K = c.K;
     congruence_lower_t(K, c.d_Linv, c.d_rho, c.d_B, P, s);
-    if (tm) tm->mark(t0 + 5);
     launch_frob_dot((long long)K * K, P, c.d_S, c.d_part, c.d_scal + SCAL_NE, s);
     int flags[FLAG_COUNT];
     read_flags(c, s, flags);
     double sc[2];
-    DFT_CUDA_CHECK(cudaMemcpy(sc, c.d_scal + SCAL_MU, sizeof(double), cudaMemcpyDeviceToHost));
-    DFT_CUDA_CHECK(cudaMemcpy(sc + 1, c.d_scal + SCAL_NE, sizeof(double), cudaMemcpyDeviceToHost));
+    DFT_CUDA_CHECK(cudaMemcpyAsync(sc, c.d_scal + SCAL_MU, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DFT_CUDA_CHECK(cudaMemcpyAsync(sc + 1, c.d_scal + SCAL_NE, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DFT_CUDA_CHECK(cudaStreamSynchronize(s));
     if (info) {
         info->mu = sc[0];
-        info->e_min = eb[0];
-        info->e_max = eb[1];
+        info->e_min = c.e_bounds[0];
+        info->e_max = c.e_bounds[1];
         info->n_e_trace = 2.0 * sc[1];
-        info->n_cheb = n_c;
+        info->n_cheb = c.n_c_cur;
         info->spectrum_ok = flags[FLAG_SPECTRUM] ? 0 : 1;
     }
     if (flags[FLAG_TIMEOUT]) throw Error(DFT_ETIMEOUT, "a tensor-core pipeline wait expired");
     if (flags[FLAG_SPECTRUM]) throw Error(DFT_ESPECTRUM, "Chebyshev iterates left [-1, 1]: spectral bounds too tight");
     if (flags[FLAG_MU]) throw Error(DFT_ENOTCONV, "mu bisection: the bracket does not contain N_e");
+}
+
+// P = f(S^-1 F) S^-1 through the symmetric Chebyshev recurrence (Supp. B)
+void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cudaStream_t s, Timer* tm,
+                         int t0) {
+    dm_prepare(c, F, s, tm, t0);
+    dm_pass1(c, s);
+    dm_mu(c, s);
+    if (tm) tm->mark(t0 + 3);
+    dm_pass2(c, s);
+    if (tm) tm->mark(t0 + 4);
+    dm_finish(c, P, info, s);
+    if (tm) tm->mark(t0 + 5);
+}
+
+// v_KS[n_in] -> V^KS -> F = T + V^KS (into c.d_F)
+void scf_head(Ctx& c, const double* n_in, cudaStream_t s) {
+    hartree_xc(c, n_in, c.d_vks, false, s);
+    launch_quadrature(c, c.d_vks, c.d_F, s);
+    launch_axpby_mat(c.K, 1.0, c.d_T, 1.0, c.d_F, c.d_F, s);
+}
+
+// n_out from c.d_P, energy of n_out, residual, mixing; fills loc
+void scf_tail(Ctx& c, double* n_in_out, double* v_ks_out, double* P_out, dft_info* loc, cudaStream_t s, Timer* tm) {
+    const int K = c.K;
+    if (tm) tm->mark(7);
+    launch_collocate(c, c.d_P, c.d_nout, s);
+    if (tm) tm->mark(8);
+    hartree_xc(c, c.d_nout, nullptr, true, s);
+    launch_frob_dot((long long)K * K, c.d_P, c.d_T, c.d_part, c.d_scal + SCAL_EKIN, s);
+    launch_maxabs_diff(c.ng, c.d_nout, n_in_out, c.d_part, c.d_scal + SCAL_RES, s);
+    if (v_ks_out) DFT_CUDA_CHECK(cudaMemcpyAsync(v_ks_out, c.d_vks, sizeof(double) * c.ng, cudaMemcpyDeviceToDevice, s));
+    if (P_out) DFT_CUDA_CHECK(cudaMemcpyAsync(P_out, c.d_P, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
+    double sc[SCAL_COUNT];
+    DFT_CUDA_CHECK(cudaMemcpyAsync(sc, c.d_scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
+    DFT_CUDA_CHECK(cudaStreamSynchronize(s));
+    loc->e_kin = 2.0 * sc[SCAL_EKIN];
+    loc->e_loc = sc[SCAL_E0];
+    loc->e_hartree = sc[SCAL_E1];
+    loc->e_xc = sc[SCAL_E2];
+    loc->e_total = loc->e_kin + loc->e_loc + loc->e_hartree + loc->e_xc;
+    loc->residual = sc[SCAL_RES];
+    // mixing (Pulay needs the residual on the host for its small solve)
+    if (c.p.mixer == DFT_MIX_KERKER) kerker_mix(c, n_in_out, c.d_nout, c.p.mix_alpha, s);
+    else if (c.p.mixer == DFT_MIX_PULAY) pulay_mix(c, n_in_out, c.d_nout, s);
+    else launch_linear_mix(c.ng, n_in_out, c.d_nout, c.p.mix_alpha, s);
+    loc->de_per_atom = c.have_prev ? (loc->e_total - c.e_prev) / c.n_atoms : 0.0;
+    c.e_prev = loc->e_total;
+    c.have_prev = true;
+    loc->iter = ++c.iter;
+    if (tm) loc->ms_stage[6] = tm->ms(7, 8);
+}
+
+// run a launch sequence through a CUDA graph cached in `lead` under (slot,
+// count): the recurrence loops are thousands of launches that repeat
+// unchanged from one SCF step to the next while N_C stays the same
+template <class F>
+void run_graph(Ctx& lead, int slot, int count, long long key, cudaStream_t s, F&& body) {
+    if (count <= 0) return;
+    if (!lead.graph_exec[slot] || lead.graph_count[slot] != count || lead.graph_key[slot] != key) {
+        if (lead.graph_exec[slot]) {
+            cudaGraphExecDestroy(lead.graph_exec[slot]);
+            lead.graph_exec[slot] = nullptr;
+        }
+        cudaStream_t cs = nullptr;
+        DFT_CUDA_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        DFT_CUDA_CHECK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        try {
+            body(cs);
+        } catch (...) {
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            throw;
+        }
+        DFT_CUDA_CHECK(cudaStreamEndCapture(cs, &g));
+        cudaError_t e = cudaGraphInstantiate(&lead.graph_exec[slot], g, 0);
+        cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) throw Error(DFT_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        lead.graph_count[slot] = count;
+        lead.graph_key[slot] = key;
+    }
+    DFT_CUDA_CHECK(cudaGraphLaunch(lead.graph_exec[slot], s));
 }
 
 }  // namespace
@@ -497,8 +648,6 @@ dft_status dft_init_basis(dft_ctx** ctx, const dft_basis_desc* basis, const dft_
         DFT_CUDA_CHECK(cudaMemsetAsync(c->d_scal, 0, sizeof(double) * SCAL_COUNT, s));
         DFT_CUDA_CHECK(cudaMemsetAsync(c->d_flags, 0, sizeof(int) * FLAG_COUNT, s));
         if (c->Kp > 0) {
-            std::vector<int> tl = tc_tiles(c->K);
-            DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_tiles, tl.data(), sizeof(int) * tl.size(), cudaMemcpyHostToDevice, s));
             DFT_CUDA_CHECK(cudaMemsetAsync(c->d_x16[0], 0, (size_t)c->Kp * c->Kp * 2 * 4, s));
             tc_setup(*c);
         }
@@ -608,55 +757,101 @@ dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !n_in_out) throw Error(DFT_EINVAL, "null argument");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
-        const int K = c.K;
         Timer tm(s);
         dft_info loc{};
         tm.mark(0);
-        // v_KS[n_in] -> V^KS -> F = T + V^KS
-        hartree_xc(c, n_in_out, c.d_vks, false, s);
-        launch_quadrature(c, c.d_vks, c.d_F, s);
-        launch_axpby_mat(K, 1.0, c.d_T, 1.0, c.d_F, c.d_F, s);
+        scf_head(c, n_in_out, s);
         tm.mark(1);
-        // P, then n_out
         density_matrix_impl(c, c.d_F, c.d_P, &loc, s, &tm, 1);
-        tm.mark(7);
-        launch_collocate(c, c.d_P, c.d_nout, s);
-        tm.mark(8);
-        // energy of n_out
-        hartree_xc(c, c.d_nout, nullptr, true, s);
-        launch_frob_dot((long long)K * K, c.d_P, c.d_T, c.d_part, c.d_scal + SCAL_EKIN, s);
-        launch_maxabs_diff(c.ng, c.d_nout, n_in_out, c.d_part, c.d_scal + SCAL_RES, s);
-        if (v_ks_out) DFT_CUDA_CHECK(cudaMemcpyAsync(v_ks_out, c.d_vks, sizeof(double) * c.ng, cudaMemcpyDeviceToDevice, s));
-        if (P_out) DFT_CUDA_CHECK(cudaMemcpyAsync(P_out, c.d_P, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
-        // mixing
-        if (c.p.mixer == DFT_MIX_KERKER) kerker_mix(c, n_in_out, c.d_nout, c.p.mix_alpha, s);
-        else if (c.p.mixer == DFT_MIX_PULAY) pulay_mix(c, n_in_out, c.d_nout, s);
-        else launch_linear_mix(c.ng, n_in_out, c.d_nout, c.p.mix_alpha, s);
-        double sc[SCAL_COUNT];
-        DFT_CUDA_CHECK(cudaMemcpyAsync(sc, c.d_scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
-        DFT_CUDA_CHECK(cudaStreamSynchronize(s));
-        loc.e_kin = 2.0 * sc[SCAL_EKIN];
-        loc.e_loc = sc[SCAL_E0];
-        loc.e_hartree = sc[SCAL_E1];
-        loc.e_xc = sc[SCAL_E2];
-        loc.e_total = loc.e_kin + loc.e_loc + loc.e_hartree + loc.e_xc;
-        loc.residual = sc[SCAL_RES];
-        loc.de_per_atom = c.have_prev ? (loc.e_total - c.e_prev) / c.n_atoms : 0.0;
-        c.e_prev = loc.e_total;
-        c.have_prev = true;
-        loc.iter = ++c.iter;
-        // stage times: quadrature, transform, Lanczos, moments, Chebyshev, back-transform, collocation
+        scf_tail(c, n_in_out, v_ks_out, P_out, &loc, s, &tm);
         loc.ms_stage[0] = tm.ms(0, 1);
         for (int i = 1; i < 6; ++i) loc.ms_stage[i] = tm.ms(i, i + 1);
-        loc.ms_stage[6] = tm.ms(7, 8);
-        loc.ms_stage[7] = 0.f;
         if (info) *info = loc;
+    });
+}
+
+dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in_out, dft_info* infos,
+                                void* stream) {
+    if (!ctxs || n < 1 || !ctxs[0]) return DFT_EINVAL;
+    return guarded(ctxs[0], [&] {
+        if (n > TC_MAX_SYS) throw Error(DFT_EINVAL, "at most 64 systems per batch");
+        if (!n_in_out) throw Error(DFT_EINVAL, "null argument");
+        std::vector<Ctx*> cs(n);
+        for (int q = 0; q < n; ++q) {
+            if (!ctxs[q] || !n_in_out[q]) throw Error(DFT_EINVAL, "null context or density in the batch");
+            cs[q] = reinterpret_cast<Ctx*>(ctxs[q]);
+            if (cs[q]->K == 0 || cs[q]->Kp == 0) throw Error(DFT_EINVAL, "batched steps need mixed-precision contexts");
+            if (cs[q]->p.precision != cs[0]->p.precision) throw Error(DFT_EINVAL, "batch mixes precisions");
+            for (int r = 0; r < q; ++r)
+                if (cs[r] == cs[q]) throw Error(DFT_EINVAL, "a context appears twice in the batch");
+        }
+        Ctx& lead = *cs[0];
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        Timer tm(s);
+        std::vector<dft_info> loc(n);
+        tm.mark(0);
+        // per system: potential, Fock matrix, bounds, N_C, split H_N, m_0..m_2
+        for (int q = 0; q < n; ++q) {
+            scf_head(*cs[q], n_in_out[q], s);
+            dm_prepare(*cs[q], cs[q]->d_F, s, nullptr, 0);
+        }
+        tm.mark(1);
+        // one persistent launch per recurrence step for all systems: moments pass
+        std::vector<int> lim(n), last(n);
+        int Jmax = 0, Lmax = 0;
+        for (int q = 0; q < n; ++q) {
+            int J = pass1_steps(cs[q]->n_c_cur);
+            lim[q] = J + 1;
+            last[q] = J;
+            Jmax = std::max(Jmax, J);
+            Lmax = std::max(Lmax, cs[q]->n_c_cur);
+        }
+        TcBatch b = tc_batch(lead, cs.data(), n, lim.data(), last.data(), s);
+        tc_set_limits(b, cs.data(), lim.data(), last.data(), s);
+        int total_k = 0;
+        for (int q = 0; q < n; ++q) total_k += cs[q]->K;
+        const int j0 = tc_pass1_tuned(b, total_k, Jmax, s);
+        const long long gkey = ((long long)b.ntiles * 128 + b.nsys) * 256 + b.cfg.bk + b.cfg.persist;
+        run_graph(lead, 0, Jmax - j0 + 1, gkey * 65536 + j0, s, [&](cudaStream_t gs) {
+            for (int j = j0; j <= Jmax; ++j) {
+                tc_step_batch(b, j, j & 1, 2, gs);
+                tc_moment_reduce_batch(b, j, gs);
+            }
+        });
+        tm.mark(2);
+        for (int q = 0; q < n; ++q) {
+            dm_mu(*cs[q], s);
+            tc_init(*cs[q], cs[q]->d_coef, s);
+            lim[q] = cs[q]->n_c_cur;
+            last[q] = 0;
+        }
+        tc_set_limits(b, cs.data(), lim.data(), last.data(), s);
+        tm.mark(3);
+        run_graph(lead, 1, Lmax, gkey, s, [&](cudaStream_t gs) {
+            for (int l = 2; l < Lmax; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, gs);
+        });
+        tm.mark(4);
+        for (int q = 0; q < n; ++q) {
+            tc_rho_finish(*cs[q], s);
+            dm_finish(*cs[q], cs[q]->d_P, &loc[q], s);
+            scf_tail(*cs[q], n_in_out[q], nullptr, nullptr, &loc[q], s, nullptr);
+        }
+        tm.mark(5);
+        for (int q = 0; q < n; ++q) {
+            loc[q].ms_stage[0] = tm.ms(0, 1);   // shared stages: potentials, Fock, bounds (all systems)
+            loc[q].ms_stage[3] = tm.ms(1, 2);   // joint moments pass
+            loc[q].ms_stage[4] = tm.ms(3, 4);   // joint Chebyshev pass
+            loc[q].ms_stage[5] = tm.ms(4, 5);   // back-transforms, collocation, energies, mixing
+            if (infos) infos[q] = loc[q];
+        }
     });
 }
 
 dft_status dft_destroy(dft_ctx* ctx) {
     if (!ctx) return DFT_OK;
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    for (auto& g : c->graph_exec)
+        if (g) cudaGraphExecDestroy(g);
     if (c->plan_f) cufftDestroy(c->plan_f);
     if (c->plan_b) cufftDestroy(c->plan_b);
     if (c->kplan_f) cufftDestroy(c->kplan_f);

@@ -29,6 +29,26 @@ struct Fn {
     int pad;
 };
 
+// one system of a (possibly batched) tensor-core Chebyshev launch
+struct TcSys {
+    int K, Kp, nk, lim;      // steps l >= lim skip this system
+    int n_c, part_off, mom_last, ntl;   // ntl: its tiles; part_off: first partial slot
+    void* x16[4];            // X pairs (hi, lo) x 2, Kp x Kp 16-bit
+    double* rho;             // Kp x Kp FP64 upper triangle
+    const double* coef;
+    double* mom;
+};
+struct TcTile {
+    int sys, i, j, idx;      // system, row tile, column tile, index within the system
+};
+constexpr int TC_MAX_SYS = 64;
+constexpr int TC_MAPS_PER_SYS = 12;
+
+// launch configuration of the tensor-core step (chosen by the autotuner)
+struct TcCfg {
+    int bk = 32;        // k-block width: 32 (4-stage ring) or 64 (2-stage ring)
+    int persist = 0;    // 0: one CTA per tile; p > 0: p CTAs per SM, strided tile loop
+};
 struct Ctx {
     // problem
     int K = 0, n_atoms = 0;
@@ -90,9 +110,19 @@ struct Ctx {
     void* d_h16[2] = {nullptr, nullptr};   // H_N hi, lo  [Kp x Kp] 16-bit
     void* d_x16[4] = {nullptr, nullptr, nullptr, nullptr};  // X pairs (hi, lo) x 2
     double* d_rho_tc = nullptr;  // [Kp x Kp] FP64, upper triangle accumulated
-    int* d_tiles = nullptr;      // (row tile, col tile) pairs
-    CUtensorMap tm_h[2];
-    CUtensorMap tm_x[4];
+    CUtensorMap tm_h[2][2];      // host copies of this system's tensor maps,
+    CUtensorMap tm_x[2][4];      // per k-block variant (32 or 64 wide)
+    // batch area (device): system table, tensor maps (6 per system), tile list
+    TcSys* d_systab = nullptr;
+    CUtensorMap* d_maps = nullptr;
+    TcTile* d_tiles = nullptr;
+    int tile_cap = 0;
+    int n_c_cur = 0;             // Chebyshev order of the density matrix in progress
+    TcCfg tc_cfg;                // launch shape chosen for this system
+    double e_bounds[2] = {0, 0}; // its spectral bounds
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};   // batched recurrence loops
+    int graph_count[2] = {0, 0};
+    long long graph_key[2] = {0, 0};
 
     // Pulay mixing: ring of pl_hist inputs then pl_hist residuals, [2 pl_hist][ng]
     double* d_pulay = nullptr;
@@ -181,7 +211,25 @@ std::vector<int> tc_tiles(int K);
 void tc_setup(Ctx& c);
 void tc_split_h(const Ctx& c, cudaStream_t s);        // H_N -> 16-bit pair; trace, |H|^2 -> scal[SCAL_TRACE..+1]
 void tc_init(const Ctx& c, const double* coef, cudaStream_t s);
-void tc_step(const Ctx& c, int cur, double* rho, const double* coef, int l, double* part, cudaStream_t s);
+// a launch over several systems whose tables sit in `leader`'s batch area
+struct TcBatch {
+    const Ctx* leader = nullptr;
+    int nsys = 0, ntiles = 0;
+    bool bf = false;
+    TcCfg cfg;
+};
+// in-flight tuning: the first steps of a pass run each candidate on real
+// steps, the fastest is kept per (precision, K bucket, systems) and cached
+// (optionally in the JSON file named by DFT_AUTOTUNE_CACHE)
+TcCfg tc_tuned(const TcBatch& b, int total_k);
+bool tc_needs_tuning(const TcBatch& b, int total_k);
+void tc_record(const TcBatch& b, int total_k, TcCfg best, const float* ms, int ncand);
+int tc_candidates(TcCfg* out);
+// fill leader's batch area with the given systems (pass lim/mom_last per system)
+TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const int* mom_last, cudaStream_t s);
+void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s);
+void tc_moment_reduce_batch(const TcBatch& b, int j, cudaStream_t s);
+void tc_set_limits(const TcBatch& b, Ctx* const* sys, const int* lim, const int* mom_last, cudaStream_t s);
 void tc_rho_finish(const Ctx& c, cudaStream_t s);
 
 // ---- Poisson + LDA (k_poisson.cu) ----

@@ -127,19 +127,22 @@ __global__ void k_cheb_init(int K, const double* __restrict__ H, double* X0, dou
     if (rho) rho[e] = a[0] * id + a[1] * h;
 }
 
-constexpr int CB = 64, CK = 16;
+constexpr int CK = 16;
 
-// One Chebyshev step on a 64x64 tile: C = H Xcur; Xn = 2C - Xprev (stored over
-// Xprev); rho += a_l Xn; optional moment partials <Xn,Xn>, <Xn,Xcur>.
+// One Chebyshev step on a CB x CB tile: C = H Xcur; Xn = 2C - Xprev (stored over
+// Xprev); rho += a_l Xn; optional moment partials <Xn,Xn>, <Xn,Xcur>.  The
+// FP64 pipe is the limit, so small K uses 32 x 32 tiles to give every SM work.
+template <int CB>
 __global__ void __launch_bounds__(256) k_cheb_step_fp64(int K, const double* __restrict__ H,
                                                         const double* __restrict__ Xc, double* __restrict__ Xp,
                                                         double* __restrict__ rho, const double* __restrict__ a,
                                                         int l, double* __restrict__ part, int* flags) {
+    constexpr int TM = CB / 16;
     __shared__ double As[CK][CB + 1];
     __shared__ double Bs[CK][CB + 1];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int m0 = blockIdx.y * CB, n0 = blockIdx.x * CB;
-    double acc[4][4] = {};
+    double acc[TM][TM] = {};
     for (int k0 = 0; k0 < K; k0 += CK) {
         for (int e = threadIdx.x; e < CB * CK; e += 256) {
             int kk = e % CK, mm = e / CK;
@@ -152,15 +155,15 @@ __global__ void __launch_bounds__(256) k_cheb_step_fp64(int K, const double* __r
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < CK; ++kk) {
-            double av[4], bv[4];
+            double av[TM], bv[TM];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < TM; ++i) av[i] = As[kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < TM; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+                for (int j = 0; j < TM; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
         }
         __syncthreads();
     }
@@ -168,11 +171,11 @@ __global__ void __launch_bounds__(256) k_cheb_step_fp64(int K, const double* __r
     double s_nn = 0.0, s_nc = 0.0;
     bool bad = false;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TM; ++i) {
         int gm = m0 + ty + 16 * i;
         if (gm >= K) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TM; ++j) {
             int gn = n0 + tx + 16 * j;
             if (gn >= K) continue;
             long long e = (long long)gm * K + gn;
@@ -196,6 +199,11 @@ __global__ void __launch_bounds__(256) k_cheb_step_fp64(int K, const double* __r
             part[2 * b + 1] = s_nc;
         }
     }
+}
+
+inline int fp64_tile(int K) {
+    int nb = (K + 63) / 64;
+    return nb * nb < 2 * 152 ? 32 : 64;
 }
 
 // m_{even} = 2 <Xn,Xn> - m0, m_{odd} = 2 <Xn,Xc> - m1 (T_{2l} = 2T_l^2 - 1,
@@ -252,15 +260,18 @@ void launch_cheb_init(int K, const double* H, double* X0, double* X1, double* rh
 }
 
 int cheb_step_parts(int K) {
-    int nb = (K + CB - 1) / CB;
+    int cb = fp64_tile(K);
+    int nb = (K + cb - 1) / cb;
     return nb * nb;
 }
 
 void launch_cheb_step_fp64(int K, const double* H, const double* Xcur, double* Xprev, double* rho,
                            const double* coef, int l, double* part, int* flags, cudaStream_t s) {
-    int nb = (K + CB - 1) / CB;
+    int cb = fp64_tile(K);
+    int nb = (K + cb - 1) / cb;
     dim3 grid(nb, nb);
-    k_cheb_step_fp64<<<grid, 256, 0, s>>>(K, H, Xcur, Xprev, rho, coef, l, part, flags);
+    if (cb == 32) k_cheb_step_fp64<32><<<grid, 256, 0, s>>>(K, H, Xcur, Xprev, rho, coef, l, part, flags);
+    else k_cheb_step_fp64<64><<<grid, 256, 0, s>>>(K, H, Xcur, Xprev, rho, coef, l, part, flags);
     check_launch("cheb_step_fp64");
 }
 

@@ -27,24 +27,34 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 
 namespace dft {
 namespace tc {
 
-// k-block width: 32 (64-byte rows, 64-byte swizzle, 4 stages) or 64 (128-byte
-// rows and swizzle, 2 stages); either way 192 KB of operand ring
-#ifndef DFT_TC_BK
-#define DFT_TC_BK 32
-#endif
-constexpr int BM = 128, BN = 256, BK = DFT_TC_BK, STAGES = BK == 64 ? 2 : 4;
-constexpr int GK = 256 / BK;                          // k-blocks per promoted chunk (256 of K)
-constexpr int ROW_BYTES = BK * 2;                     // one operand row in shared memory
+constexpr int BM = 128, BN = 256;
 constexpr int NEPI = 256;                             // epilogue threads (8 warps)
 constexpr int NTHREADS = 64 + NEPI;                   // + producer warp + MMA warp
-constexpr int A_BYTES = BM * BK * 2;                  // 16 KB
-constexpr int B_BYTES = BN * BK * 2;                  // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
+// k-block variants: 32 wide (64-byte rows and swizzle, 4 stages) or 64 wide
+// (128-byte rows and swizzle, 2 stages); either way a 192 KB operand ring and
+// chunks of 256 of K between promotions
+template <int BK_>
+struct Cfg {
+    static constexpr int BK = BK_;
+    static constexpr int STAGES = BK_ == 64 ? 2 : 4;
+    static constexpr int GK = 256 / BK_;
+    static constexpr int ROW_BYTES = BK_ * 2;
+    static constexpr int A_BYTES = BM * BK_ * 2;
+    static constexpr int B_BYTES = BN * BK_ * 2;
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
+};
 constexpr int TMEM_COLS = 2 * BN;                     // two chunk accumulators
 constexpr unsigned long long WAIT_NS = 1000000000ull;   // 1 s per wait
 
@@ -99,6 +109,7 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 // shared-memory matrix descriptor of a K-major operand whose rows are one
 // swizzle atom wide (ROW_BYTES): 8-row core groups 8 * ROW_BYTES apart;
 // layout type 2 = 128-byte swizzle, 4 = 64-byte swizzle
+template <int ROW_BYTES>
 __device__ __forceinline__ uint64_t smem_desc(const void* p) {
     uint64_t addr = (uint64_t)(smem_u32(p) & 0x3FFFF) >> 4;
     const uint64_t sbo = (uint64_t)(8 * ROW_BYTES) >> 4;
@@ -154,20 +165,6 @@ struct H16<true> {
     static __device__ __forceinline__ T from_d(double x) { return __double2bfloat16(x); }
 };
 
-struct StepArgs {
-    int K, Kp, nk;
-    const int2* tiles;
-    const void* xc_hi;   // X_l (moments)
-    const void* xc_lo;
-    void* xp_hi;         // X_{l-1} in, X_{l+1} out
-    void* xp_lo;
-    double* rho;         // upper triangle, ld Kp (nullptr: moments pass)
-    const double* coef;
-    int l;
-    double* part;        // moment partials (nullptr: no moments)
-    int* flags;
-};
-
 template <int BS>
 __device__ double block_sum(double v) {
     __shared__ double red[BS / 32];
@@ -187,18 +184,25 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// per-element update of one output (r, c), c >= r: returns X_{l+1}
-template <bool BF>
-__device__ __forceinline__ float step_elem(float acc, float xp) {
-    return 2.0f * acc - xp;
-}
+// barrier among the NEPI epilogue threads only (the producer and MMA warps
+// keep running their own loops)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(NEPI) : "memory"); }
 
-template <bool BF>
-__global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const __grid_constant__ CUtensorMap tmAh,
-                                                              const __grid_constant__ CUtensorMap tmAl,
-                                                              const __grid_constant__ CUtensorMap tmBh,
-                                                              const __grid_constant__ CUtensorMap tmBl, StepArgs g) {
+// Persistent multi-system step.  Each CTA walks the tile list with stride
+// gridDim.x; a tile of system s is active when l < sys[s].lim.  Pipeline
+// phases (stage ring, chunk accumulators) run on across tiles, so the MMA
+// warp starts the next tile's first two chunks while the epilogue warps
+// finish the previous tile.
+template <bool BF, int BKV>
+__global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __restrict__ sys,
+                                                              const CUtensorMap* __restrict__ maps,
+                                                              const TcTile* __restrict__ tiles, int ntiles, int l,
+                                                              int cur, int mode, double* __restrict__ part,
+                                                              int* __restrict__ flags) {
     using T = typename H16<BF>::T;
+    using C = Cfg<BKV>;
+    constexpr int BK = C::BK, STAGES = C::STAGES, GK = C::GK, STAGE_BYTES = C::STAGE_BYTES;
+    constexpr int A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -208,11 +212,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const __grid_const
     uint64_t* drain = accempty + 2;
     uint32_t* tmem_slot = (uint32_t*)(drain + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    double* red = (double*)(smem + STAGES * STAGE_BYTES + 128);   // 2 x 8 doubles
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int2 tile = g.tiles[blockIdx.x];
-    const int m0 = tile.x * BM, n0 = tile.y * BN;
-    const int nchunk = (g.nk + GK - 1) / GK;
+    const bool do_rho = (mode & 1) != 0, do_mom = (mode & 2) != 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -247,24 +250,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const __grid_const
     if (warp == 0) {
         if (lane == 0) {
             // producer: four operand tiles per k-block into the stage ring
-            int issued = 0;
-            for (int kb = 0; kb < g.nk; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
-                if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
-                    *abort_flag = 1;
-                    break;
+            long long g = 0;   // k-blocks issued by this CTA
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                const TcTile tl = tiles[t];
+                const TcSys& S = sys[tl.sys];
+                if (l >= S.lim) continue;
+                const CUtensorMap* mp = maps + 12 * tl.sys + (BK == 64 ? 6 : 0);
+                const int m0 = tl.i * BM, n0 = tl.j * BN;
+                const int nk = (S.K + BK - 1) / BK;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = (int)(g % STAGES);
+                    const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+                    if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(sAh(s), mp + 0, kb * BK, m0, &full[s]);
+                    tma_load_2d(sAl(s), mp + 1, kb * BK, m0, &full[s]);
+                    tma_load_2d(sBh(s), mp + 2 + 2 * cur, kb * BK, n0, &full[s]);
+                    tma_load_2d(sBl(s), mp + 3 + 2 * cur, kb * BK, n0, &full[s]);
                 }
-                mbar_expect_tx(&full[s], STAGE_BYTES);
-                tma_load_2d(sAh(s), &tmAh, kb * BK, m0, &full[s]);
-                tma_load_2d(sAl(s), &tmAl, kb * BK, m0, &full[s]);
-                tma_load_2d(sBh(s), &tmBh, kb * BK, n0, &full[s]);
-                tma_load_2d(sBl(s), &tmBl, kb * BK, n0, &full[s]);
-                issued = kb + 1;
             }
             if (*abort_flag) {
-                for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-                    mbar_wait(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
+                // the last load issued into each stage must land before exit
+                for (long long q = (g > STAGES ? g - STAGES : 0); q < g; ++q)
+                    mbar_wait(&full[q % STAGES], (uint32_t)((q / STAGES) & 1));
             }
         }
         __syncwarp();
@@ -273,39 +284,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const __grid_const
             // MMA issuer: chunks of GK k-blocks alternate between two accumulators
             const uint32_t idesc = (1u << 4) | ((BF ? 1u : 0u) << 7) | ((BF ? 1u : 0u) << 10) |
                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-            int kb = 0;
-            for (int q = 0; q < nchunk; ++q) {
-                const int a = q & 1;
-                if (*abort_flag || !mbar_wait(&accempty[a], (uint32_t)(((q >> 1) & 1) ^ 1))) {
-                    *abort_flag = 1;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(a * BN);
-                const int kend = min(g.nk, (q + 1) * GK);
-                bool first = true;
-                for (; kb < kend; ++kb) {
-                    const int s = kb % STAGES;
-                    const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
-                    if (*abort_flag || !mbar_wait(&full[s], ph)) {
+            long long g = 0, qg = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                const TcTile tl = tiles[t];
+                const TcSys& S = sys[tl.sys];
+                if (l >= S.lim) continue;
+                const int nk = (S.K + BK - 1) / BK;
+                const int nchunk = (nk + GK - 1) / GK;
+                int kb = 0;
+                for (int q = 0; q < nchunk; ++q, ++qg) {
+                    const int a = (int)(qg & 1);
+                    if (*abort_flag || !mbar_wait(&accempty[a], (uint32_t)(((qg >> 1) & 1) ^ 1))) {
                         *abort_flag = 1;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t ah = smem_desc(sAh(s)), al = smem_desc(sAl(s));
-                    const uint64_t bh = smem_desc(sBh(s)), bl = smem_desc(sBl(s));
+                    const uint32_t d = tmem + (uint32_t)(a * BN);
+                    const int kend = min(nk, (q + 1) * GK);
+                    bool first = true;
+                    for (; kb < kend; ++kb, ++g) {
+                        const int s = (int)(g % STAGES);
+                        const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+                        if (*abort_flag || !mbar_wait(&full[s], ph)) {
+                            *abort_flag = 1;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t ah = smem_desc<C::ROW_BYTES>(sAh(s)), al = smem_desc<C::ROW_BYTES>(sAl(s));
+                        const uint64_t bh = smem_desc<C::ROW_BYTES>(sBh(s)), bl = smem_desc<C::ROW_BYTES>(sBl(s));
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint64_t off = (uint64_t)(kk * 2);   // 32 bytes per 16-element k step
-                        umma_f16(d, ah + off, bh + off, idesc, first ? 0u : 1u);
-                        umma_f16(d, ah + off, bl + off, idesc, 1u);
-                        umma_f16(d, al + off, bh + off, idesc, 1u);
-                        first = false;
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint64_t off = (uint64_t)(kk * 2);   // 32 bytes per 16-element k step
+                            umma_f16(d, ah + off, bh + off, idesc, first ? 0u : 1u);
+                            umma_f16(d, ah + off, bl + off, idesc, 1u);
+                            umma_f16(d, al + off, bh + off, idesc, 1u);
+                            first = false;
+                        }
+                        umma_commit(&empty[s]);
                     }
-                    umma_commit(&empty[s]);
+                    umma_commit(&accfull[a]);
+                    if (*abort_flag) break;
                 }
-                umma_commit(&accfull[a]);
-                if (*abort_flag) break;
             }
             if (*abort_flag) {
                 // every MMA this thread issued must finish before tensor memory is freed
@@ -318,158 +337,190 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const __grid_const
         // ---- epilogue warps: quadrant = warp % 4 (tensor-memory lane group), half = column half ----
         const int quad = warp & 3;
         const int half = (warp - 2) >> 2;
-        float R[BN / 2];
-#pragma unroll
-        for (int i = 0; i < BN / 2; ++i) R[i] = 0.0f;
+        long long qg = 0;
         bool ok = true;
-        for (int q = 0; q < nchunk; ++q) {
-            const int a = q & 1;
-            const bool got = mbar_wait(&accfull[a], (uint32_t)((q >> 1) & 1));
-            ok = __all_sync(0xffffffffu, got && !*abort_flag);
-            if (!ok) break;
-            tc_fence_after();
-            // promote the chunk's partial sums: round-to-nearest FP32 adds in registers
-#pragma unroll
-            for (int cc = 0; cc < BN / 64; ++cc) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * BN + half * (BN / 2) + cc * 32), v);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) R[cc * 32 + j] += __uint_as_float(v[j]);
-            }
-            tc_fence_before();
-            mbar_arrive(&accempty[a]);
-        }
-        const int r = m0 + 32 * quad + lane;
-        const double al = g.rho ? g.coef[g.l] : 0.0;
-        double s_nn = 0.0, s_nc = 0.0;
         bool bad = false;
-        T* xph = (T*)g.xp_hi;
-        T* xpl = (T*)g.xp_lo;
-        const T* xch = (const T*)g.xc_hi;
-        const T* xcl = (const T*)g.xc_lo;
-        if (ok && r < g.K) {
-            const size_t rowoff = (size_t)r * g.Kp;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TcTile tl = tiles[t];
+            const TcSys& S = sys[tl.sys];
+            if (l >= S.lim) continue;
+            const int nchunk = ((S.K + BK - 1) / BK + GK - 1) / GK;
+            const int m0 = tl.i * BM, n0 = tl.j * BN;
+            float R[BN / 2];
 #pragma unroll
-            for (int cc = 0; cc < BN / 64; ++cc) {
-                const int cb = n0 + half * (BN / 2) + cc * 32;
-                if (cb + 31 < r || cb >= g.K) continue;
-                const bool vec = (cb >= r) && (cb + 31 < g.K);
-                if (vec) {
-                    // whole 32-column run is upper and inside: 16-byte accesses along the
-                    // row, eight columns at a time
+            for (int i = 0; i < BN / 2; ++i) R[i] = 0.0f;
+            for (int q = 0; q < nchunk; ++q, ++qg) {
+                const int a = (int)(qg & 1);
+                const bool got = mbar_wait(&accfull[a], (uint32_t)((qg >> 1) & 1));
+                ok = __all_sync(0xffffffffu, got && !*abort_flag);
+                if (!ok) break;
+                tc_fence_after();
+                // promote the chunk's partial sums: round-to-nearest FP32 adds in registers
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const size_t e0 = rowoff + cb + 8 * i;
-                        const uint4 ph4 = *(const uint4*)(xph + e0);
-                        const uint4 pl4 = *(const uint4*)(xpl + e0);
-                        const T* phv = (const T*)&ph4;
-                        const T* plv = (const T*)&pl4;
-                        uint4 oh4, ol4;
-                        T* ohv = (T*)&oh4;
-                        T* olv = (T*)&ol4;
-                        float xn[8];
+                for (int cc = 0; cc < BN / 64; ++cc) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * BN + half * (BN / 2) + cc * 32),
+                              v);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const float xp = H16<BF>::to_f(phv[j]) + H16<BF>::to_f(plv[j]);
-                            xn[j] = 2.0f * R[cc * 32 + 8 * i + j] - xp;
-                            const T h = H16<BF>::from_f(xn[j]);
-                            ohv[j] = h;
-                            olv[j] = H16<BF>::from_f(xn[j] - H16<BF>::to_f(h));
-                            bad |= !(fabsf(xn[j]) <= 4.0f);
-                        }
-                        *(uint4*)(xph + e0) = oh4;
-                        *(uint4*)(xpl + e0) = ol4;
+                    for (int j = 0; j < 32; ++j) R[cc * 32 + j] += __uint_as_float(v[j]);
+                }
+                tc_fence_before();
+                mbar_arrive(&accempty[a]);
+            }
+            if (!ok) break;
+            const int r = m0 + 32 * quad + lane;
+            const double al = do_rho ? S.coef[l] : 0.0;
+            double s_nn = 0.0, s_nc = 0.0;
+            T* xph = (T*)S.x16[2 * (1 - cur)];
+            T* xpl = (T*)S.x16[2 * (1 - cur) + 1];
+            const T* xch = (const T*)S.x16[2 * cur];
+            const T* xcl = (const T*)S.x16[2 * cur + 1];
+            double* rho = S.rho;
+            const int K = S.K;
+            const size_t Kp = (size_t)S.Kp;
+            if (r < K) {
+                const size_t rowoff = (size_t)r * Kp;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int c = cb + 8 * i + j;
-                            if (c != r) {
-                                const size_t et = (size_t)c * g.Kp + r;
-                                xph[et] = ohv[j];
-                                xpl[et] = olv[j];
-                            }
-                        }
-                        if (g.rho) {
-                            double2* rp = (double2*)(g.rho + e0);
+                for (int cc = 0; cc < BN / 64; ++cc) {
+                    const int cb = n0 + half * (BN / 2) + cc * 32;
+                    if (cb + 31 < r || cb >= K) continue;
+                    const bool vec = (cb >= r) && (cb + 31 < K);
+                    if (vec) {
+                        // the whole 32-column run is upper and inside: 16-byte accesses
+                        // along the row, eight columns at a time
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                double2 q2 = rp[k];
-                                q2.x = fma(al, (double)xn[2 * k], q2.x);
-                                q2.y = fma(al, (double)xn[2 * k + 1], q2.y);
-                                rp[k] = q2;
-                            }
-                        }
-                        if (g.part) {
-                            const uint4 ch4 = *(const uint4*)(xch + e0);
-                            const uint4 cl4 = *(const uint4*)(xcl + e0);
-                            const T* chv = (const T*)&ch4;
-                            const T* clv = (const T*)&cl4;
+                        for (int i = 0; i < 4; ++i) {
+                            const size_t e0 = rowoff + cb + 8 * i;
+                            const uint4 ph4 = *(const uint4*)(xph + e0);
+                            const uint4 pl4 = *(const uint4*)(xpl + e0);
+                            const T* phv = (const T*)&ph4;
+                            const T* plv = (const T*)&pl4;
+                            uint4 oh4, ol4;
+                            T* ohv = (T*)&oh4;
+                            T* olv = (T*)&ol4;
+                            float xn[8];
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
-                                const double w = (cb + 8 * i + j == r) ? 1.0 : 2.0;
-                                const double xc = (double)H16<BF>::to_f(chv[j]) + (double)H16<BF>::to_f(clv[j]);
-                                s_nn = fma(w * xn[j], (double)xn[j], s_nn);
-                                s_nc = fma(w * xn[j], xc, s_nc);
+                                const float xp = H16<BF>::to_f(phv[j]) + H16<BF>::to_f(plv[j]);
+                                xn[j] = 2.0f * R[cc * 32 + 8 * i + j] - xp;
+                                const T h = H16<BF>::from_f(xn[j]);
+                                ohv[j] = h;
+                                olv[j] = H16<BF>::from_f(xn[j] - H16<BF>::to_f(h));
+                                bad |= !(fabsf(xn[j]) <= 4.0f);
+                            }
+                            *(uint4*)(xph + e0) = oh4;
+                            *(uint4*)(xpl + e0) = ol4;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const int c = cb + 8 * i + j;
+                                if (c != r) {
+                                    const size_t et = (size_t)c * Kp + r;
+                                    xph[et] = ohv[j];
+                                    xpl[et] = olv[j];
+                                }
+                            }
+                            if (do_rho) {
+                                double2* rp = (double2*)(rho + e0);
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    double2 q2 = rp[k];
+                                    q2.x = fma(al, (double)xn[2 * k], q2.x);
+                                    q2.y = fma(al, (double)xn[2 * k + 1], q2.y);
+                                    rp[k] = q2;
+                                }
+                            }
+                            if (do_mom) {
+                                const uint4 ch4 = *(const uint4*)(xch + e0);
+                                const uint4 cl4 = *(const uint4*)(xcl + e0);
+                                const T* chv = (const T*)&ch4;
+                                const T* clv = (const T*)&cl4;
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    const double w = (cb + 8 * i + j == r) ? 1.0 : 2.0;
+                                    const double xc = (double)H16<BF>::to_f(chv[j]) + (double)H16<BF>::to_f(clv[j]);
+                                    s_nn = fma(w * xn[j], (double)xn[j], s_nn);
+                                    s_nc = fma(w * xn[j], xc, s_nc);
+                                }
                             }
                         }
-                    }
-                } else {
+                    } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int c = cb + j;
-                        if (c < r || c >= g.K) continue;
-                        const size_t e = rowoff + c;
-                        const float xp = H16<BF>::to_f(xph[e]) + H16<BF>::to_f(xpl[e]);
-                        const float xn = 2.0f * R[cc * 32 + j] - xp;
-                        const T h = H16<BF>::from_f(xn);
-                        const T lo = H16<BF>::from_f(xn - H16<BF>::to_f(h));
-                        xph[e] = h;
-                        xpl[e] = lo;
-                        if (c != r) {
-                            const size_t et = (size_t)c * g.Kp + r;
-                            xph[et] = h;
-                            xpl[et] = lo;
+                        for (int j = 0; j < 32; ++j) {
+                            const int c = cb + j;
+                            if (c < r || c >= K) continue;
+                            const size_t e = rowoff + c;
+                            const float xp = H16<BF>::to_f(xph[e]) + H16<BF>::to_f(xpl[e]);
+                            const float xn = 2.0f * R[cc * 32 + j] - xp;
+                            const T h = H16<BF>::from_f(xn);
+                            const T lo = H16<BF>::from_f(xn - H16<BF>::to_f(h));
+                            xph[e] = h;
+                            xpl[e] = lo;
+                            if (c != r) {
+                                const size_t et = (size_t)c * Kp + r;
+                                xph[et] = h;
+                                xpl[et] = lo;
+                            }
+                            if (do_rho) rho[e] = fma(al, (double)xn, rho[e]);
+                            if (do_mom) {
+                                const double w = (c == r) ? 1.0 : 2.0;
+                                const double xc = (double)H16<BF>::to_f(xch[e]) + (double)H16<BF>::to_f(xcl[e]);
+                                s_nn = fma(w * xn, (double)xn, s_nn);
+                                s_nc = fma(w * xn, xc, s_nc);
+                            }
+                            bad |= !(fabsf(xn) <= 4.0f);
                         }
-                        if (g.rho) g.rho[e] = fma(al, (double)xn, g.rho[e]);
-                        if (g.part) {
-                            const double w = (c == r) ? 1.0 : 2.0;
-                            const double xc = (double)H16<BF>::to_f(xch[e]) + (double)H16<BF>::to_f(xcl[e]);
-                            s_nn = fma(w * xn, (double)xn, s_nn);
-                            s_nc = fma(w * xn, xc, s_nc);
-                        }
-                        bad |= !(fabsf(xn) <= 4.0f);
                     }
                 }
             }
-        }
-        if (bad) atomicExch(&g.flags[FLAG_SPECTRUM], 1);
-        if (!ok && lane == 0) atomicExch(&g.flags[FLAG_TIMEOUT], 1);
-        if (g.part) {
-            for (int o = 16; o > 0; o >>= 1) {
-                s_nn += __shfl_down_sync(0xffffffffu, s_nn, o);
-                s_nc += __shfl_down_sync(0xffffffffu, s_nc, o);
+            if (do_mom) {
+                for (int o = 16; o > 0; o >>= 1) {
+                    s_nn += __shfl_down_sync(0xffffffffu, s_nn, o);
+                    s_nc += __shfl_down_sync(0xffffffffu, s_nc, o);
+                }
+                if (lane == 0) {
+                    red[2 * (warp - 2)] = s_nn;
+                    red[2 * (warp - 2) + 1] = s_nc;
+                }
+                epi_sync();
+                if (threadIdx.x == 64) {
+                    double a0 = 0.0, a1 = 0.0;
+                    for (int w = 0; w < NEPI / 32; ++w) {
+                        a0 += red[2 * w];
+                        a1 += red[2 * w + 1];
+                    }
+                    part[2 * (S.part_off + tl.idx)] = a0;
+                    part[2 * (S.part_off + tl.idx) + 1] = a1;
+                }
+                epi_sync();
             }
-            double* red = (double*)(smem + STAGES * STAGE_BYTES + 128);   // after the barriers
-            if (lane == 0) {
-                red[2 * (warp - 2)] = s_nn;
-                red[2 * (warp - 2) + 1] = s_nc;
-            }
         }
+        if (bad) atomicExch(&flags[FLAG_SPECTRUM], 1);
+        if (!ok && lane == 0) atomicExch(&flags[FLAG_TIMEOUT], 1);
     }
     tc_fence_before();
     __syncthreads();
-    if (g.part && threadIdx.x == 0) {
-        const double* red = (const double*)(smem + STAGES * STAGE_BYTES + 128);
-        double a0 = 0.0, a1 = 0.0;
-        for (int i = 0; i < NEPI / 32; ++i) {
-            a0 += red[2 * i];
-            a1 += red[2 * i + 1];
-        }
-        g.part[2 * blockIdx.x] = a0;
-        g.part[2 * blockIdx.x + 1] = a1;
-    }
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// per-system moment reduction: block b sums the partials of system b's tiles
+__global__ void __launch_bounds__(256) k_moment_reduce_multi(const TcSys* __restrict__ sys,
+                                                             const double* __restrict__ part, int j) {
+    const TcSys& S = sys[blockIdx.x];
+    if (j > S.mom_last) return;
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = threadIdx.x; i < S.ntl; i += 256) {
+        s0 += part[2 * (S.part_off + i)];
+        s1 += part[2 * (S.part_off + i) + 1];
+    }
+    s0 = block_sum<256>(s0);
+    s1 = block_sum<256>(s1);
+    if (threadIdx.x == 0) {
+        const int ie = 2 * j + 2, io = 2 * j + 1;
+        if (ie < S.n_c) S.mom[ie] = 2.0 * s0 - (double)S.K;
+        if (io < S.n_c) S.mom[io] = 2.0 * s1 - S.mom[1];
     }
 }
 
@@ -552,14 +603,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-void make_map(CUtensorMap* m, const void* base, int Kp, int box_rows) {
+void make_map(CUtensorMap* m, const void* base, int Kp, int box_rows, int bk) {
     cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)Kp};
     cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             ROW_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                             bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) throw Error(DFT_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
@@ -584,17 +635,135 @@ void tc_setup(Ctx& c) {
     // one 16-bit type for the bit patterns; BF16 maps are encoded as FLOAT16 of
     // the same width (TMA moves bytes; the MMA's instruction descriptor decides
     // how they are read)
-    tc::make_map(&c.tm_h[0], c.d_h16[0], c.Kp, tc::BM);
-    tc::make_map(&c.tm_h[1], c.d_h16[1], c.Kp, tc::BM);
-    for (int q = 0; q < 4; ++q) tc::make_map(&c.tm_x[q], c.d_x16[q], c.Kp, tc::BN);
-    static bool attr_done[2] = {false, false};
-    if (!attr_done[0]) {
-        DFT_CUDA_CHECK(cudaFuncSetAttribute(tc::k_cheb_step_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            tc::SMEM_BYTES));
-        DFT_CUDA_CHECK(cudaFuncSetAttribute(tc::k_cheb_step_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            tc::SMEM_BYTES));
-        attr_done[0] = true;
+    for (int v = 0; v < 2; ++v) {
+        const int bk = v ? 64 : 32;
+        tc::make_map(&c.tm_h[v][0], c.d_h16[0], c.Kp, tc::BM, bk);
+        tc::make_map(&c.tm_h[v][1], c.d_h16[1], c.Kp, tc::BM, bk);
+        for (int q = 0; q < 4; ++q) tc::make_map(&c.tm_x[v][q], c.d_x16[q], c.Kp, tc::BN, bk);
     }
+    static bool attr_done = false;
+    if (!attr_done) {
+        DFT_CUDA_CHECK(cudaFuncSetAttribute(tc::k_cheb_step_tc<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            tc::Cfg<32>::SMEM_BYTES));
+        DFT_CUDA_CHECK(cudaFuncSetAttribute(tc::k_cheb_step_tc<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            tc::Cfg<32>::SMEM_BYTES));
+        DFT_CUDA_CHECK(cudaFuncSetAttribute(tc::k_cheb_step_tc<false, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            tc::Cfg<64>::SMEM_BYTES));
+        DFT_CUDA_CHECK(cudaFuncSetAttribute(tc::k_cheb_step_tc<true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            tc::Cfg<64>::SMEM_BYTES));
+        attr_done = true;
+    }
+}
+
+namespace {
+TcSys sys_entry(const Ctx& c, int lim, int mom_last, int part_off, int ntl) {
+    TcSys e{};
+    e.K = c.K;
+    e.Kp = c.Kp;
+    e.nk = 0;
+    e.lim = lim;
+    e.n_c = 0;
+    e.part_off = part_off;
+    e.mom_last = mom_last;
+    e.ntl = ntl;
+    for (int q = 0; q < 4; ++q) e.x16[q] = c.d_x16[q];
+    e.rho = c.d_rho_tc;
+    e.coef = c.d_coef;
+    e.mom = c.d_mom;
+    return e;
+}
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+}  // namespace
+
+TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const int* mom_last, cudaStream_t s) {
+    if (nsys < 1 || nsys > TC_MAX_SYS) throw Error(DFT_EINVAL, "batch size out of range");
+    std::vector<TcSys> tab(nsys);
+    std::vector<CUtensorMap> maps(12 * (size_t)nsys);
+    std::vector<TcTile> tiles;
+    int part_off = 0;
+    // interleave the systems' tiles so that consecutive CTAs mix large and small systems
+    std::vector<std::vector<int>> per(nsys);
+    for (int q = 0; q < nsys; ++q) per[q] = tc_tiles(sys[q]->K);
+    for (int q = 0; q < nsys; ++q) {
+        const Ctx& c = *sys[q];
+        if (c.Kp == 0) throw Error(DFT_EINVAL, "batched step needs a mixed-precision context");
+        if (c.p.precision != leader.p.precision) throw Error(DFT_EINVAL, "batch mixes precisions");
+        int ntl = (int)per[q].size() / 2;
+        tab[q] = sys_entry(c, lim[q], mom_last[q], part_off, ntl);
+        part_off += ntl;
+        for (int v = 0; v < 2; ++v) {
+            maps[12 * q + 6 * v + 0] = c.tm_h[v][0];
+            maps[12 * q + 6 * v + 1] = c.tm_h[v][1];
+            for (int k = 0; k < 4; ++k) maps[12 * q + 6 * v + 2 + k] = c.tm_x[v][k];
+        }
+    }
+    size_t longest = 0;
+    for (auto& v : per) longest = std::max(longest, v.size() / 2);
+    for (size_t t = 0; t < longest; ++t)
+        for (int q = 0; q < nsys; ++q)
+            if (t < per[q].size() / 2) tiles.push_back(TcTile{q, per[q][2 * t], per[q][2 * t + 1], (int)t});
+    if ((int)tiles.size() > leader.tile_cap) throw Error(DFT_ENOMEM, "batch tile list exceeds the leader's capacity");
+    if ((long long)2 * part_off > leader.part_cap) throw Error(DFT_ENOMEM, "batch partial sums exceed the leader's capacity");
+    DFT_CUDA_CHECK(cudaMemcpyAsync(leader.d_systab, tab.data(), sizeof(TcSys) * nsys, cudaMemcpyHostToDevice, s));
+    DFT_CUDA_CHECK(cudaMemcpyAsync(leader.d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                                   cudaMemcpyHostToDevice, s));
+    DFT_CUDA_CHECK(cudaMemcpyAsync(leader.d_tiles, tiles.data(), sizeof(TcTile) * tiles.size(),
+                                   cudaMemcpyHostToDevice, s));
+    DFT_CUDA_CHECK(cudaStreamSynchronize(s));   // host staging buffers go out of scope
+    TcBatch b;
+    b.leader = &leader;
+    b.nsys = nsys;
+    b.ntiles = (int)tiles.size();
+    b.bf = leader.p.precision == DFT_PREC_BF16X3;
+    return b;
+}
+
+void tc_set_limits(const TcBatch& b, Ctx* const* sys, const int* lim, const int* mom_last, cudaStream_t s) {
+    for (int q = 0; q < b.nsys; ++q) {
+        int v[2] = {lim[q], mom_last[q]};
+        DFT_CUDA_CHECK(cudaMemcpyAsync((char*)(b.leader->d_systab + q) + offsetof(TcSys, lim), &v[0], sizeof(int),
+                                       cudaMemcpyHostToDevice, s));
+        DFT_CUDA_CHECK(cudaMemcpyAsync((char*)(b.leader->d_systab + q) + offsetof(TcSys, mom_last), &v[1], sizeof(int),
+                                       cudaMemcpyHostToDevice, s));
+        int nc = sys[q]->n_c_cur;
+        DFT_CUDA_CHECK(cudaMemcpyAsync((char*)(b.leader->d_systab + q) + offsetof(TcSys, n_c), &nc, sizeof(int),
+                                       cudaMemcpyHostToDevice, s));
+    }
+    DFT_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s) {
+    const Ctx& L = *b.leader;
+    // launch shape (tuned): one CTA per tile, with the hardware handing tiles
+    // to SMs as they free up, or a persistent grid of `persist` CTAs per SM
+    // walking the tile list with a fixed stride
+    int grid = b.cfg.persist > 0 ? std::min(b.ntiles, b.cfg.persist * num_sms()) : b.ntiles;
+    auto go = [&](auto kern, int smem) {
+        kern<<<grid, tc::NTHREADS, smem, s>>>(L.d_systab, L.d_maps, L.d_tiles, b.ntiles, l, cur, mode, L.d_part,
+                                             L.d_flags);
+    };
+    if (b.cfg.bk == 64) {
+        if (b.bf) go(tc::k_cheb_step_tc<true, 64>, tc::Cfg<64>::SMEM_BYTES);
+        else go(tc::k_cheb_step_tc<false, 64>, tc::Cfg<64>::SMEM_BYTES);
+    } else {
+        if (b.bf) go(tc::k_cheb_step_tc<true, 32>, tc::Cfg<32>::SMEM_BYTES);
+        else go(tc::k_cheb_step_tc<false, 32>, tc::Cfg<32>::SMEM_BYTES);
+    }
+    check_launch("cheb_step_tc");
+}
+
+void tc_moment_reduce_batch(const TcBatch& b, int j, cudaStream_t s) {
+    tc::k_moment_reduce_multi<<<b.nsys, 256, 0, s>>>(b.leader->d_systab, b.leader->d_part, j);
+    check_launch("moment_reduce_multi");
 }
 
 void tc_split_h(const Ctx& c, cudaStream_t s) {
@@ -624,35 +793,80 @@ void tc_init(const Ctx& c, const double* coef, cudaStream_t s) {
     check_launch("tc_init", coef ? 2 : 1);
 }
 
-// one step: X_{l+1} = 2 H X_cur - X_prev written over the prev pair
-void tc_step(const Ctx& c, int cur, double* rho, const double* coef, int l, double* part, cudaStream_t s) {
-    tc::StepArgs g{};
-    g.K = c.K;
-    g.Kp = c.Kp;
-    g.nk = (c.K + tc::BK - 1) / tc::BK;
-    g.tiles = (const int2*)c.d_tiles;
-    int prev = 1 - cur;
-    g.xc_hi = c.d_x16[2 * cur];
-    g.xc_lo = c.d_x16[2 * cur + 1];
-    g.xp_hi = c.d_x16[2 * prev];
-    g.xp_lo = c.d_x16[2 * prev + 1];
-    g.rho = rho;
-    g.coef = coef;
-    g.l = l;
-    g.part = part;
-    g.flags = c.d_flags;
-    if (c.p.precision == DFT_PREC_BF16X3)
-        tc::k_cheb_step_tc<true><<<c.n_tc_tiles, tc::NTHREADS, tc::SMEM_BYTES, s>>>(c.tm_h[0], c.tm_h[1], c.tm_x[2 * cur],
-                                                                          c.tm_x[2 * cur + 1], g);
-    else
-        tc::k_cheb_step_tc<false><<<c.n_tc_tiles, tc::NTHREADS, tc::SMEM_BYTES, s>>>(c.tm_h[0], c.tm_h[1], c.tm_x[2 * cur],
-                                                                           c.tm_x[2 * cur + 1], g);
-    check_launch("cheb_step_tc");
-}
-
 void tc_rho_finish(const Ctx& c, cudaStream_t s) {
     tc::k_rho_mirror<<<tc::blocks_for((long long)c.K * c.K, 256), 256, 0, s>>>(c.K, c.Kp, c.d_rho_tc, c.d_rho);
     check_launch("rho_mirror");
+}
+
+// ---- autotuner of the tensor-core launch configuration ----
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, TcCfg> g_tuned;
+bool g_tune_loaded = false;
+
+std::string tune_key(const TcBatch& b, int total_k) {
+    // quarter-octave buckets of the summed basis size
+    int bucket = (int)std::lround(4.0 * std::log2((double)std::max(total_k, 1)));
+    std::ostringstream o;
+    o << (b.bf ? "bf16x3" : "fp16x3") << "_kb" << bucket << "_n" << b.nsys;
+    return o.str();
+}
+
+// cache file: one entry per line, `"key": [bk, persist],` inside braces
+void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = std::getenv("DFT_AUTOTUNE_CACHE");
+    if (!path) return;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        size_t q0 = line.find('"'), q1 = line.find('"', q0 + 1), lb = line.find('[', q1 + 1);
+        if (q0 == std::string::npos || q1 == std::string::npos || lb == std::string::npos) continue;
+        TcCfg c;
+        if (std::sscanf(line.c_str() + lb, "[%d, %d]", &c.bk, &c.persist) == 2 && (c.bk == 32 || c.bk == 64) &&
+            c.persist >= 0 && c.persist <= 1)
+            g_tuned[line.substr(q0 + 1, q1 - q0 - 1)] = c;
+    }
+}
+
+void tune_save() {
+    const char* path = std::getenv("DFT_AUTOTUNE_CACHE");
+    if (!path) return;
+    std::ofstream f(path);
+    f << "{\n";
+    size_t i = 0;
+    for (auto& kv : g_tuned)
+        f << "  \"" << kv.first << "\": [" << kv.second.bk << ", " << kv.second.persist << "]"
+          << (++i < g_tuned.size() ? "," : "") << "\n";
+    f << "}\n";
+}
+}  // namespace
+
+int tc_candidates(TcCfg* out) {
+    const TcCfg c[4] = {{32, 0}, {64, 0}, {32, 1}, {64, 1}};
+    for (int i = 0; i < 4; ++i) out[i] = c[i];
+    return 4;
+}
+
+bool tc_needs_tuning(const TcBatch& b, int total_k) {
+    if (std::getenv("DFT_AUTOTUNE_OFF")) return false;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load();
+    return g_tuned.find(tune_key(b, total_k)) == g_tuned.end();
+}
+
+TcCfg tc_tuned(const TcBatch& b, int total_k) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load();
+    auto it = g_tuned.find(tune_key(b, total_k));
+    return it == g_tuned.end() ? TcCfg{} : it->second;
+}
+
+void tc_record(const TcBatch& b, int total_k, TcCfg best, const float*, int) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[tune_key(b, total_k)] = best;
+    tune_save();
 }
 
 }  // namespace dft
