@@ -164,6 +164,76 @@ def cpu_baseline(sysm, budget_s):
                                                              "poisson": 2 * t_pois}}
 
 
+def run_batched(args, rank, world):
+    """Ragged batch: every SCF step advances all systems with one
+    dft_scf_step_batched call (one tensor-core launch per recurrence step for
+    the whole batch, graph-captured loops).  Value = sum of K over systems x
+    steps / time."""
+    import torch
+    import torch.distributed as dist
+    import paper_2108_13478_gb300 as dft
+    import workloads as w
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    systems = w.config_batch(args.workload)
+    prec = {"fp16x3": dft.DFT_PREC_FP16X3, "bf16x3": dft.DFT_PREC_BF16X3}[args.precision]
+    # the largest system leads (its workspace holds the batch tables)
+    order = sorted(range(len(systems)), key=lambda i: -systems[i].n_basis)
+    ctxs = []
+    for i in order:
+        c = dft.Context(systems[i], device=f"cuda:{local}", precision=prec, cheb_tail_tol=1e-10, mix_alpha=0.3,
+                        mixer=dft.DFT_MIX_PULAY, kerker_q0=0.8, mix_history=8, model=dft.DFT_MODEL_NEUTRAL)
+        c.overlap_kinetic()
+        ctxs.append(c)
+    dens = [c.initial_density() for c in ctxs]
+    handles = [c.ctx for c in ctxs]
+    for _ in range(args.warmup):
+        dft.dft_scf_step_batched(handles, dens)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = dft.dft_kernel_launches()
+    ms = []
+    infos = None
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos = dft.dft_scf_step_batched(handles, dens)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    launches = (dft.dft_kernel_launches() - l0) / args.steps
+    clocks = sampler.stop()
+    total_ms = sum(ms)
+    t = torch.tensor([total_ms], device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ksum = sum(c.K for c in ctxs)
+    value = world * ksum * args.steps / (total_ms / 1000.0)
+    n_c = [i.n_cheb for i in infos]
+    line = {"metric": METRIC, "value": value, "unit": "P-columns/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": args.workload, "systems": len(ctxs), "sum_n_basis": ksum,
+                       "n_basis_range": [min(c.K for c in ctxs), max(c.K for c in ctxs)],
+                       "n_cheb_range": [min(n_c), max(n_c)], "model": "neutral",
+                       "mixer": "pulay alpha 0.3 kerker q0 0.8 hist 8", "batched": "dft_scf_step_batched",
+                       "l2": "working set above L2 (sum of operands)", "parallelism": f"replicas x{world}"},
+            "gpu_launches": int(launches), "clocks": clocks,
+            "stages_ms": [round(x, 3) for x in infos[0].ms_stage]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def compare_precisions(dft, torch, local, name="cluster64", steps=2):
     """Mixed (FP16x3) and FP64 GPU paths on the same SCF steps of the 64-atom
     cluster (the largest case where the FP64 path finishes in seconds): step
@@ -195,6 +265,37 @@ def compare_precisions(dft, torch, local, name="cluster64", steps=2):
     return out
 
 
+def run_reference_batch(args, rank):
+    """Oracle on a bounded sample of a ragged batch: the bounded one-step
+    sample (cpu_baseline) of 8 systems spread over the size range, scaled to
+    the whole batch by the number of systems."""
+    if rank != 0:
+        return
+    import workloads as w
+    systems = sorted(w.config_batch(args.workload), key=lambda s: s.n_basis)
+    pick = [systems[i] for i in np.linspace(0, len(systems) - 1, min(8, len(systems))).round().astype(int)]
+    vals = []
+    for step in range(args.warmup + args.steps):
+        t = 0.0
+        for sy in pick:
+            cb = cpu_baseline(sy, args.cpu_budget)
+            t += sy.n_basis / cb["value"]
+        if step >= args.warmup:
+            vals.append(sum(s.n_basis for s in systems) / (t * len(systems) / len(pick)))
+    val = statistics.median(vals)
+    ksum = sum(s.n_basis for s in systems)
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": "P-columns/s",
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1000.0 * ksum / val, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": args.workload, "systems": len(systems), "sum_n_basis": ksum},
+                      "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": val, "unit": "P-columns/s",
+                                       "sample": f"bounded one-step samples of {len(pick)} of {len(systems)} systems, "
+                                                 "scaled by the system count"},
+                      "e2e": {"value": val, "unit": "P-columns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
 def run_reference(args, sysm, rank, world):
     if rank != 0:
         return
@@ -221,6 +322,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     import workloads as w
+    if args.workload.startswith("batch"):
+        if args.impl == "reference":
+            run_reference_batch(args, rank)
+            return
+        run_batched(args, rank, world)
+        return
     sysm = w.config_system(args.workload)
     if args.impl == "reference":
         run_reference(args, sysm, rank, world)

@@ -8,5 +8,5 @@ CUDA library.
 """
 from .si_clusters import (  # noqa: F401
     SI_A0, DIAMOND_BASIS, SHELL_SPEC, System,
-    diamond_supercell, diamond_sphere, make_system, config_system,
+    diamond_supercell, diamond_sphere, make_system, config_system, batch_systems, config_batch,
 )

@@ -117,6 +117,29 @@ def jitter(xyz: np.ndarray, sigma: float, seed: int) -> np.ndarray:
     return xyz + rng.normal(0.0, sigma, xyz.shape)
 
 
+def batch_systems(n: int, rmin: float, rmax: float, seed: int = 0, sigma: float = 0.1, kT: float = 0.01):
+    """n spheres with radii uniform in [rmin, rmax] (one seeded draw), each
+    jittered with its own seed; a ragged batch of independent clusters."""
+    rng = np.random.default_rng(seed)
+    radii = rng.uniform(rmin, rmax, n)
+    out = []
+    for i, r in enumerate(radii):
+        xyz = jitter(diamond_sphere(float(r)), sigma, seed * 1000 + i + 1)
+        out.append(make_system(xyz, kT=kT, name=f"sphere{r:.2f}"))
+    return out
+
+
+def config_batch(name: str):
+    """Named batches: batch64 = 64 spheres with R in [10, 30] (the full ragged
+    workload), batch<n>s = n spheres with R in [6, 14] (the same recipe at a
+    size one SCF step of which takes about a second)."""
+    if name == "batch64":
+        return batch_systems(64, 10.0, 30.0, seed=0)
+    if name.startswith("batch") and name.endswith("s"):
+        return batch_systems(int(name[5:-1]), 6.0, 14.0, seed=0)
+    raise ValueError(f"unknown batch {name!r}")
+
+
 def config_system(name: str, seed: int = 0, **kw) -> System:
     """Named workloads.
 
