@@ -191,6 +191,44 @@ dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double
 dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in_out, dft_info* infos,
                                 void* stream);
 
+/* Density of a given potential: V = h^3 sum phi v phi (Eq. 2.5), F = T + V,
+ * P (Eq. 2.9), n = 2 sum P phi phi (Eq. 2.7).  Starts an SCF cycle from a
+ * potential (e.g. the learned warm start) instead of a density.  v_grid,
+ * n_out device grids; info (host, may be NULL) receives the density-matrix
+ * results. */
+dft_status dft_density_from_potential(dft_ctx* ctx, const double* v_grid, double* n_out, dft_info* info,
+                                      void* stream);
+
+/* Learned warm start (not in the paper, which starts from atomic densities,
+ * Supp. A.3): an atom-centred network corrects the starting potential.
+ *   G_Ak = sum_{B != A, r < 8} exp(-(r - m_k)^2 / 2 s^2) (cos(pi r / 8) + 1) / 2,
+ *          m_k = 8 k / 31, s = 8 / 31 (k < 32)
+ *   x = G / 4; three SiLU layers of width 128; c_A = W4 h3 + b4 (16 values)
+ *   v0 = v_start + sum_A sum_k c_Ak exp(-|r - R_A|^2 / w_k^2), |r - R_A| < 12,
+ *        w_k = 0.5 * 6^(k / 15)
+ * Parameters: W1 (128 x 32), b1, W2 (128 x 128), b2, W3, b3, W4 (16 x 128),
+ * b4, row-major, in that order (dft_warmstart_param_count() floats).  The
+ * state (device, dft_warmstart_state_bytes() bytes, caller-owned) holds the
+ * FP32 master parameters, their gradient, the Adam moments and the FP16
+ * copy the kernels use (FP32 arithmetic). */
+size_t dft_warmstart_state_bytes(void);
+int dft_warmstart_param_count(void);
+/* params: host FP32 (NULL = zeros); gradient and Adam moments are cleared. */
+dft_status dft_warmstart_init(void* state, const float* params, void* stream);
+/* v0 (device grid) = v_start (device grid, may be NULL = 0) + the network's correction. */
+dft_status dft_warmstart_potential(dft_ctx* ctx, const void* state, const double* v_start, double* v0,
+                                   void* stream);
+/* Loss L = h^3 sum (v0 - v_target)^2 of this system (host *loss), and dL/dtheta
+ * added into the state's gradient (backward through the grid assembly and
+ * the network). */
+dft_status dft_warmstart_accumulate(dft_ctx* ctx, void* state, const double* v_start, const double* v_target,
+                                    double* loss, void* stream);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8; step counts from 1) on the
+ * accumulated gradient, which is then cleared. */
+dft_status dft_warmstart_adam(void* state, float lr, int step, void* stream);
+/* Copy the FP32 parameters and/or the gradient to the host (either may be NULL). */
+dft_status dft_warmstart_read(const void* state, float* params, float* grads, void* stream);
+
 /* Superposition-of-atoms start density (Supp. A.3: "sum of atomic
  * densities"): a normalised Gaussian of ion_charge electrons and width
  * vloc_width on every atom.  n_grid device grid, overwritten. */

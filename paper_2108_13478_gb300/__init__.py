@@ -18,6 +18,8 @@ from ._binding import (  # noqa: F401
     dft_workspace_bytes, dft_init_basis, dft_overlap_kinetic, dft_density_matrix, dft_density_on_grid,
     dft_potential_matrix, dft_hartree_xc, dft_scf_step, dft_initial_density, dft_destroy, dft_last_error,
     dft_version, dft_kernel_launches, dft_spectral_bounds_static, dft_scf_step_batched,
+    dft_density_from_potential, dft_warmstart_state_bytes, dft_warmstart_param_count, dft_warmstart_init,
+    dft_warmstart_potential, dft_warmstart_accumulate, dft_warmstart_adam, dft_warmstart_read,
 )
 
 

@@ -67,6 +67,14 @@ SIGNATURES = [
     ("dft_scf_step", C.c_int, [_P, _P, _P, _P, C.POINTER(dft_info), _P]),
     ("dft_initial_density", C.c_int, [_P, _P, _P]),
     ("dft_scf_step_batched", C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P), C.POINTER(dft_info), _P]),
+    ("dft_density_from_potential", C.c_int, [_P, _P, _P, C.POINTER(dft_info), _P]),
+    ("dft_warmstart_state_bytes", C.c_size_t, []),
+    ("dft_warmstart_param_count", C.c_int, []),
+    ("dft_warmstart_init", C.c_int, [_P, C.POINTER(C.c_float), _P]),
+    ("dft_warmstart_potential", C.c_int, [_P, _P, _P, _P, _P]),
+    ("dft_warmstart_accumulate", C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_double), _P]),
+    ("dft_warmstart_adam", C.c_int, [_P, C.c_float, C.c_int, _P]),
+    ("dft_warmstart_read", C.c_int, [_P, C.POINTER(C.c_float), C.POINTER(C.c_float), _P]),
     ("dft_destroy", C.c_int, [_P]),
     ("dft_last_error", C.c_char_p, [_P]),
     ("dft_version", C.c_char_p, []),
@@ -170,6 +178,51 @@ def dft_scf_step_batched(ctxs, n_in_out, stream=None):
     if st != DFT_OK:
         raise DftError(st, lib.dft_last_error(carr[0]).decode())
     return list(infos)
+
+
+def dft_density_from_potential(ctx, v_grid, n_out, stream=None) -> dft_info:
+    info = dft_info()
+    _check(ctx, lib.dft_density_from_potential(ctx, _ptr(v_grid), _ptr(n_out), C.byref(info), _stream(stream)))
+    return info
+
+
+def dft_warmstart_state_bytes() -> int:
+    return int(lib.dft_warmstart_state_bytes())
+
+
+def dft_warmstart_param_count() -> int:
+    return int(lib.dft_warmstart_param_count())
+
+
+def _fptr(a):
+    import numpy as np
+    if a is None:
+        return None
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def dft_warmstart_init(state, params=None, stream=None):
+    _check(None, lib.dft_warmstart_init(_ptr(state), _fptr(params), _stream(stream)))
+
+
+def dft_warmstart_potential(ctx, state, v_start, v0, stream=None):
+    _check(ctx, lib.dft_warmstart_potential(ctx, _ptr(state), _ptr(v_start), _ptr(v0), _stream(stream)))
+
+
+def dft_warmstart_accumulate(ctx, state, v_start, v_target, stream=None) -> float:
+    loss = C.c_double()
+    _check(ctx, lib.dft_warmstart_accumulate(ctx, _ptr(state), _ptr(v_start), _ptr(v_target), C.byref(loss),
+                                             _stream(stream)))
+    return loss.value
+
+
+def dft_warmstart_adam(state, lr, step, stream=None):
+    _check(None, lib.dft_warmstart_adam(_ptr(state), C.c_float(lr), int(step), _stream(stream)))
+
+
+def dft_warmstart_read(state, params=None, grads=None, stream=None):
+    _check(None, lib.dft_warmstart_read(_ptr(state), _fptr(params), _fptr(grads), _stream(stream)))
 
 
 def dft_initial_density(ctx, n_grid, stream=None):

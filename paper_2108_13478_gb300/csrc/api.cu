@@ -167,6 +167,10 @@ size_t carve(Ctx& c, char* base) {
     size_t o_kw = L.off(sizeof(double) * nkc);
     size_t o_kc = L.off(sizeof(cufftDoubleComplex) * nkc);
     size_t o_pl = c.pl_hist > 0 ? L.off(sizeof(double) * 2 * (size_t)c.pl_hist * c.ng) : 0;
+    size_t o_wdesc = L.off(sizeof(double) * 32 * (size_t)c.n_atoms);
+    size_t o_wcoef = L.off(sizeof(double) * 16 * (size_t)c.n_atoms);
+    size_t o_wz = L.off(sizeof(float) * 3 * 128 * (size_t)c.n_atoms);
+    size_t o_wdc = L.off(sizeof(double) * 16 * (size_t)c.n_atoms);
     size_t o_h16[2] = {0, 0}, o_x16[4] = {0, 0, 0, 0}, o_rtc = 0, o_tiles = 0, o_systab = 0, o_maps = 0;
     if (c.Kp > 0) {
         size_t P16 = (size_t)c.Kp * c.Kp * 2;
@@ -203,6 +207,10 @@ size_t carve(Ctx& c, char* base) {
         c.d_kerker = (double*)(base + o_kw);
         c.d_kc = (cufftDoubleComplex*)(base + o_kc);
         if (c.pl_hist > 0) c.d_pulay = (double*)(base + o_pl);
+        c.d_wdesc = (double*)(base + o_wdesc);
+        c.d_wcoef = (double*)(base + o_wcoef);
+        c.d_wz = (float*)(base + o_wz);
+        c.d_wdc = (double*)(base + o_wdc);
         if (c.Kp > 0) {
             for (int q = 0; q < 2; ++q) c.d_h16[q] = base + o_h16[q];
             for (int q = 0; q < 4; ++q) c.d_x16[q] = base + o_x16[q];
@@ -858,6 +866,78 @@ dft_status dft_destroy(dft_ctx* ctx) {
     if (c->kplan_b) cufftDestroy(c->kplan_b);
     delete c;
     return DFT_OK;
+}
+
+dft_status dft_density_from_potential(dft_ctx* ctx, const double* v_grid, double* n_out, dft_info* info,
+                                      void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0 || !v_grid || !n_out) throw Error(DFT_EINVAL, "null argument");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        launch_quadrature(c, v_grid, c.d_F, s);
+        launch_axpby_mat(c.K, 1.0, c.d_T, 1.0, c.d_F, c.d_F, s);
+        dft_info loc{};
+        density_matrix_impl(c, c.d_F, c.d_P, &loc, s, nullptr, 0);
+        launch_collocate(c, c.d_P, n_out, s);
+        if (info) *info = loc;
+    });
+}
+
+size_t dft_warmstart_state_bytes(void) { return warm_state_bytes(); }
+
+int dft_warmstart_param_count(void) { return warm_nparam(); }
+
+dft_status dft_warmstart_init(void* state, const float* params, void* stream) {
+    if (!state) return DFT_EINVAL;
+    try {
+        warm_init(state, params, static_cast<cudaStream_t>(stream));
+        return DFT_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+dft_status dft_warmstart_potential(dft_ctx* ctx, const void* state, const double* v_start, double* v0,
+                                   void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0 || !state || !v0) throw Error(DFT_EINVAL, "null argument");
+        warm_forward(c, state, v_start, v0, false, static_cast<cudaStream_t>(stream));
+    });
+}
+
+dft_status dft_warmstart_accumulate(dft_ctx* ctx, void* state, const double* v_start, const double* v_target,
+                                    double* loss, void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0 || !state || !v_target) throw Error(DFT_EINVAL, "null argument");
+        double L = warm_accumulate(c, state, v_start, v_target, static_cast<cudaStream_t>(stream));
+        if (loss) *loss = L;
+    });
+}
+
+dft_status dft_warmstart_adam(void* state, float lr, int step, void* stream) {
+    if (!state || step < 1) return DFT_EINVAL;
+    try {
+        warm_adam(state, lr, step, static_cast<cudaStream_t>(stream));
+        return DFT_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+dft_status dft_warmstart_read(const void* state, float* params, float* grads, void* stream) {
+    if (!state) return DFT_EINVAL;
+    try {
+        if (params) warm_params(state, params, static_cast<cudaStream_t>(stream));
+        if (grads) warm_grad(state, grads, static_cast<cudaStream_t>(stream));
+        return DFT_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
 }
 
 const char* dft_last_error(const dft_ctx* ctx) {

@@ -124,6 +124,11 @@ struct Ctx {
     int graph_count[2] = {0, 0};
     long long graph_key[2] = {0, 0};
 
+    // learned warm start: descriptors, coefficients, hidden pre-activations, dL/dc
+    double* d_wdesc = nullptr;   // [n_atoms][32]
+    double* d_wcoef = nullptr;   // [n_atoms][16]
+    float* d_wz = nullptr;       // [n_atoms][3][128]
+    double* d_wdc = nullptr;     // [n_atoms][16]
     // Pulay mixing: ring of pl_hist inputs then pl_hist residuals, [2 pl_hist][ng]
     double* d_pulay = nullptr;
     int pl_hist = 0;
@@ -246,6 +251,16 @@ void launch_maxabs_diff(long long ng, const double* a, const double* b, double* 
                         cudaStream_t s);
 
 int fft_size(int n);
+
+// ---- learned warm start (k_warm.cu) ----
+int warm_nparam();
+size_t warm_state_bytes();
+void warm_init(void* state, const float* params_host, cudaStream_t s);
+void warm_params(const void* state, float* out, cudaStream_t s);
+void warm_grad(const void* state, float* out, cudaStream_t s);
+void warm_forward(Ctx& c, const void* state, const double* v_start, double* v0, bool keep, cudaStream_t s);
+double warm_accumulate(Ctx& c, void* state, const double* v_start, const double* v_target, cudaStream_t s);
+void warm_adam(void* state, float lr, int step, cudaStream_t s);
 
 }  // namespace dft
 

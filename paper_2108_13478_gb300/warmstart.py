@@ -1,0 +1,125 @@
+"""Training and use of the learned SCF warm start (orchestration only).
+
+The network, its gradients and Adam run in libdft's kernels
+(dft_warmstart_*); this module drives them: it generates training targets
+with the library's own SCF (converged Kohn-Sham potentials of seeded
+clusters), trains, and starts SCF cycles from the predicted potential.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import _binding as B
+from . import Context, make_params  # noqa: F401
+
+
+def init_params(seed=0, scale_out=0.0):
+    """He-style random hidden layers, zero output layer (the untrained
+    network reproduces the superposition-of-atoms start)."""
+    rng = np.random.default_rng(seed)
+    sizes = [(128, 32), (128, 128), (128, 128), (16, 128)]
+    parts = []
+    for li, (o, i) in enumerate(sizes):
+        std = math.sqrt(2.0 / i) if li < 3 else scale_out / math.sqrt(i)
+        parts.append(rng.normal(0.0, 1.0, o * i) * std)
+        parts.append(np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)
+
+
+class WarmStart:
+    """Device state of the network (FP32 master, gradient, Adam moments, FP16 copy)."""
+
+    def __init__(self, params=None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.state = torch.empty(B.dft_warmstart_state_bytes(), dtype=torch.uint8, device=device)
+        p = init_params() if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        B.dft_warmstart_init(self.state, p)
+        self.step = 0
+
+    def params(self):
+        out = np.empty(B.dft_warmstart_param_count(), dtype=np.float32)
+        B.dft_warmstart_read(self.state, params=out)
+        return out
+
+    def grads(self):
+        out = np.empty(B.dft_warmstart_param_count(), dtype=np.float32)
+        B.dft_warmstart_read(self.state, grads=out)
+        return out
+
+    def potential(self, ctx, v_start):
+        v0 = ctx.grid_array()
+        B.dft_warmstart_potential(ctx.ctx, self.state, v_start, v0)
+        return v0
+
+    def accumulate(self, ctx, v_start, v_target):
+        return B.dft_warmstart_accumulate(ctx.ctx, self.state, v_start, v_target)
+
+    def adam(self, lr):
+        self.step += 1
+        B.dft_warmstart_adam(self.state, lr, self.step)
+
+
+def scf_context(system, **kw):
+    kw.setdefault("precision", B.DFT_PREC_FP16X3)
+    kw.setdefault("model", B.DFT_MODEL_NEUTRAL)
+    kw.setdefault("mixer", B.DFT_MIX_PULAY)
+    kw.setdefault("mix_alpha", 0.3)
+    kw.setdefault("kerker_q0", 0.8)
+    kw.setdefault("mix_history", 8)
+    kw.setdefault("cheb_tail_tol", 1e-10)
+    ctx = Context(system, **kw)
+    ctx.overlap_kinetic()
+    return ctx
+
+
+def start_potential(ctx):
+    """v_KS of the superposition-of-atoms density."""
+    n0 = ctx.initial_density()
+    v, _ = ctx.hartree_xc(n0)
+    return v
+
+
+def run_scf(ctx, v_first, max_iter=80, tol_e=1e-8, tol_n=1e-5, e_ref=None, e_tol=1e-5):
+    """SCF cycle that starts from a potential: n_1 = n[v_first], then Pulay
+    cycles.  Returns (cycles, final info, converged v_KS, cycles to reach
+    |E - e_ref| / atom < e_tol if e_ref is given)."""
+    n = ctx.grid_array()
+    B.dft_density_from_potential(ctx.ctx, v_first, n)
+    v = ctx.grid_array()
+    hit = None
+    info = None
+    for it in range(max_iter):
+        info = ctx.scf_step(n, v_ks_out=v)
+        if e_ref is not None and hit is None and abs(info.e_total / ctx.n_atoms - e_ref) < e_tol:
+            hit = it + 1
+        if it > 0 and abs(info.de_per_atom) < tol_e and info.residual < tol_n:
+            return it + 1, info, v, hit
+    return max_iter, info, v, hit
+
+
+def training_set(systems, **kw):
+    """(context, v_start, converged v_KS) for each system, from the library's SCF."""
+    data = []
+    for s in systems:
+        ctx = scf_context(s, **kw)
+        v_start = start_potential(ctx)
+        _, _, v_star, _ = run_scf(ctx, v_start)
+        data.append((ctx, v_start, v_star))
+    return data
+
+
+def train(ws, data, epochs=60, lr=3e-3, log=None):
+    """Full-batch Adam on sum over systems of h^3 sum (v0 - v*)^2."""
+    hist = []
+    for ep in range(epochs):
+        loss = 0.0
+        for ctx, v_start, v_star in data:
+            loss += ws.accumulate(ctx, v_start, v_star)
+        ws.adam(lr)
+        hist.append(loss)
+        if log:
+            log(ep, loss)
+    return hist

@@ -1,0 +1,79 @@
+"""Learned warm start: kernels against the FP64 oracle (forward, gradient
+through the grid assembly and the network), and what training buys: SCF
+cycles from the trained network's potential vs the superposition-of-atoms
+start on a cluster not in the training set."""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import warmstart as ows
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2108_13478_gb300 as dft  # noqa: E402
+from paper_2108_13478_gb300 import warmstart as gws  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_forward_matches_oracle():
+    s = w.config_system("tiny8")
+    theta = gws.init_params(seed=4, scale_out=0.5)
+    ws = gws.WarmStart(theta)
+    ctx = dft.Context(s)
+    v0 = ws.potential(ctx, None).cpu().numpy()
+    t64 = ows.round_fp16(theta.astype(np.float64))
+    c, _ = ows.forward(t64, ows.descriptors(s.xyz))
+    ref = ows.assemble(s, c)
+    assert np.max(np.abs(v0 - ref)) < 1e-4 * np.max(np.abs(ref))
+    ctx.close()
+
+
+def test_gradient_matches_oracle():
+    s = w.config_system("tiny5")
+    rng = np.random.default_rng(7)
+    theta = gws.init_params(seed=5, scale_out=0.5)
+    ws = gws.WarmStart(theta)
+    ctx = dft.Context(s)
+    shp = tuple(int(t) for t in s.grid_n[::-1])
+    v_start = 0.05 * rng.normal(size=shp)
+    v_target = 0.05 * rng.normal(size=shp)
+    loss = ws.accumulate(ctx, dev(v_start), dev(v_target))
+    g = ws.grads().astype(np.float64)
+    L, gref = ows.loss_and_grad(ows.round_fp16(theta.astype(np.float64)), s, v_start, v_target)
+    assert abs(loss - L) < 1e-5 * abs(L)
+    assert np.linalg.norm(g - gref) < 1e-3 * np.linalg.norm(gref)
+    ctx.close()
+
+
+def test_trained_start_needs_fewer_cycles():
+    train_sys = [w.config_system(f"sphereR{r}", seed=10 + i) for i, r in enumerate((8.0, 9.0, 10.0, 11.0))]
+    data = gws.training_set(train_sys)
+    ws = gws.WarmStart(gws.init_params(seed=1))
+    hist = gws.train(ws, data, epochs=80, lr=3e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    test = w.config_system("sphereR12", seed=99)
+    ctx = gws.scf_context(test)
+    v_sad = gws.start_potential(ctx)
+    # reference energy from a tight run
+    _, info, _, _ = gws.run_scf(ctx, v_sad, tol_e=1e-9, tol_n=1e-6)
+    e_ref = info.e_total / test.n_atoms
+    ctx_a = gws.scf_context(test)
+    n_sad, _, _, hit_sad = gws.run_scf(ctx_a, gws.start_potential(ctx_a), e_ref=e_ref)
+    ctx_b = gws.scf_context(test)
+    v0 = ws.potential(ctx_b, gws.start_potential(ctx_b))
+    n_warm, _, _, hit_warm = gws.run_scf(ctx_b, v0, e_ref=e_ref)
+    print(f"loss {hist[0]:.4e} -> {hist[-1]:.4e}; cycles to 1e-5 Ha/atom: atoms {hit_sad}, warm {hit_warm}; "
+          f"to convergence: atoms {n_sad}, warm {n_warm}")
+    assert hit_warm is not None and hit_sad is not None
+    assert hit_warm <= hit_sad
+    for c, _, _ in data:
+        c.close()
+    for c in (ctx, ctx_a, ctx_b):
+        c.close()
