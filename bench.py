@@ -406,8 +406,8 @@ def main():
     # roofline of the dominant kernel: the Chebyshev step (one launch per term of pass 2)
     pk = peaks()
     n_c = infos[-1].n_cheb
-    cheb_ms = statistics.median(i.ms_stage[4] for i in infos)
-    per_launch_s = cheb_ms / 1000.0 / max(1, n_c - 2)
+    # each step's weighted-pass time over its own number of recurrence launches
+    per_launch_s = statistics.median(i.ms_stage[4] / 1000.0 / max(1, i.n_cheb - 2) for i in infos)
     sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     if prec == dft.DFT_PREC_FP64:
         flops = 2.0 * K ** 3

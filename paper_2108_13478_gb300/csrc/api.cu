@@ -409,40 +409,42 @@ void dm_prepare(Ctx& c, const double* F, cudaStream_t s, Timer* tm, int t0) {
     if (n_c > 2) launch_moment_reduce(1, c.d_scal + SCAL_TRACE, c.d_mom, 2, -1, m0, c.d_mom + 1, s);
 }
 
-// moments-pass steps j0..J of a tensor-core batch; when the launch shape of
-// this (precision, size) has not been tuned yet, the first steps run each
-// candidate shape on three real steps, timed by events, and the fastest is
-// kept for the rest (no step is repeated).  Returns the first step not run.
-int tc_pass1_tuned(TcBatch& b, int total_k, int J, cudaStream_t s) {
-    int j = 1;
+// In-flight tuning of the tensor-core launch shape on the weighted pass
+// (the dominant one): while the shape of this (precision, size, batch) is
+// untuned, the first steps l = 2, 3, ... run each candidate shape on two
+// rounds of two real steps, timed by events, and the fastest (minimum over
+// rounds) is kept for the rest of the pass and for later calls; no step is
+// repeated.  Returns the first step not yet run.
+int tc_pass2_tuned(TcBatch& b, int total_k, int Lmax, cudaStream_t s) {
+    int l = 2;
     TcCfg cand[4];
     const int nc = tc_candidates(cand);
-    const int per = 3;
-    if (tc_needs_tuning(b, total_k) && J >= nc * per + 4) {
-        float ms[4];
+    const int per = 2, rounds = 2;
+    if (tc_needs_tuning(b, total_k) && Lmax - 2 >= nc * per * rounds + 8) {
+        float best_ms[4] = {1e30f, 1e30f, 1e30f, 1e30f};
         cudaEvent_t e0, e1;
         DFT_CUDA_CHECK(cudaEventCreate(&e0));
         DFT_CUDA_CHECK(cudaEventCreate(&e1));
-        for (int i = 0; i < nc; ++i) {
-            b.cfg = cand[i];
-            DFT_CUDA_CHECK(cudaEventRecord(e0, s));
-            for (int r = 0; r < per; ++r, ++j) {
-                tc_step_batch(b, j, j & 1, 2, s);
-                tc_moment_reduce_batch(b, j, s);
+        for (int r = 0; r < rounds; ++r)
+            for (int i = 0; i < nc; ++i) {
+                b.cfg = cand[i];
+                DFT_CUDA_CHECK(cudaEventRecord(e0, s));
+                for (int k = 0; k < per; ++k, ++l) tc_step_batch(b, l, (l + 1) & 1, 1, s);
+                DFT_CUDA_CHECK(cudaEventRecord(e1, s));
+                DFT_CUDA_CHECK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                DFT_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+                best_ms[i] = std::min(best_ms[i], ms);
             }
-            DFT_CUDA_CHECK(cudaEventRecord(e1, s));
-            DFT_CUDA_CHECK(cudaEventSynchronize(e1));
-            DFT_CUDA_CHECK(cudaEventElapsedTime(&ms[i], e0, e1));
-        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         int best = 0;
         for (int i = 1; i < nc; ++i)
-            if (ms[i] < ms[best]) best = i;
-        tc_record(b, total_k, cand[best], ms, nc);
+            if (best_ms[i] < best_ms[best]) best = i;
+        tc_record(b, total_k, cand[best], best_ms, nc);
     }
     b.cfg = tc_tuned(b, total_k);
-    return j;
+    return l;
 }
 
 // moments pass of one system: m_l = Tr T_l(H_N), l < N_C, by doubling
@@ -453,11 +455,11 @@ void dm_pass1(Ctx& c, cudaStream_t s) {
         int lim = J + 1, last = J;
         TcBatch b = tc_batch(c, &cp, 1, &lim, &last, s);
         tc_set_limits(b, &cp, &lim, &last, s);
-        for (int j = tc_pass1_tuned(b, K, J, s); j <= J; ++j) {
+        b.cfg = tc_tuned(b, K);
+        for (int j = 1; j <= J; ++j) {
             tc_step_batch(b, j, j & 1, 2, s);
             tc_moment_reduce_batch(b, j, s);
         }
-        c.tc_cfg = b.cfg;
         return;
     }
     const double m0 = (double)K;
@@ -488,9 +490,8 @@ void dm_pass2(Ctx& c, cudaStream_t s) {
         Ctx* cp = &c;
         int lim = n_c, last = 0;
         TcBatch b = tc_batch(c, &cp, 1, &lim, &last, s);
-        b.cfg = c.tc_cfg;
         tc_set_limits(b, &cp, &lim, &last, s);
-        for (int l = 2; l < n_c; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, s);
+        for (int l = tc_pass2_tuned(b, K, n_c, s); l < n_c; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, s);
         tc_rho_finish(c, s);
         return;
     }
@@ -818,10 +819,10 @@ dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in
         tc_set_limits(b, cs.data(), lim.data(), last.data(), s);
         int total_k = 0;
         for (int q = 0; q < n; ++q) total_k += cs[q]->K;
-        const int j0 = tc_pass1_tuned(b, total_k, Jmax, s);
-        const long long gkey = ((long long)b.ntiles * 128 + b.nsys) * 256 + b.cfg.bk + b.cfg.persist;
-        run_graph(lead, 0, Jmax - j0 + 1, gkey * 65536 + j0, s, [&](cudaStream_t gs) {
-            for (int j = j0; j <= Jmax; ++j) {
+        b.cfg = tc_tuned(b, total_k);
+        const long long gkey1 = ((long long)b.ntiles * 128 + b.nsys) * 256 + b.cfg.bk + b.cfg.persist;
+        run_graph(lead, 0, Jmax, gkey1, s, [&](cudaStream_t gs) {
+            for (int j = 1; j <= Jmax; ++j) {
                 tc_step_batch(b, j, j & 1, 2, gs);
                 tc_moment_reduce_batch(b, j, gs);
             }
@@ -835,8 +836,10 @@ dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in
         }
         tc_set_limits(b, cs.data(), lim.data(), last.data(), s);
         tm.mark(3);
-        run_graph(lead, 1, Lmax, gkey, s, [&](cudaStream_t gs) {
-            for (int l = 2; l < Lmax; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, gs);
+        const int l0 = tc_pass2_tuned(b, total_k, Lmax, s);
+        const long long gkey2 = (((long long)b.ntiles * 128 + b.nsys) * 256 + b.cfg.bk + b.cfg.persist) * 65536 + l0;
+        run_graph(lead, 1, Lmax - l0, gkey2, s, [&](cudaStream_t gs) {
+            for (int l = l0; l < Lmax; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, gs);
         });
         tm.mark(4);
         for (int q = 0; q < n; ++q) {

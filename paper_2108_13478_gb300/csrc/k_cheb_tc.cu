@@ -8,7 +8,9 @@
 // Both H_N and X_l are symmetric polynomials of H_N, so only output tiles that
 // reach the upper triangle are computed; each tile writes its upper elements and
 // mirrors them into the lower triangle.  rho = sum_l a_l X_l is accumulated in
-// FP64 on the upper triangle.
+// FP64 on the upper triangle.  The moment partials use compensated FP32 pairs
+// (about 48 bits): GB300's FP64 pipe issues 2 FMA per SM per clock, and two
+// FP64 products per element cost the moments pass ~20% of its time.
 //
 // Per CTA: one 128 x 256 output tile, 10 warps.  Warp 0 lane 0 drives TMA
 // loads of the four operand tiles per 64-wide k-block into a 2-stage ring;
@@ -178,6 +180,24 @@ __device__ double block_sum(double v) {
     }
     __syncthreads();
     return r;
+}
+
+// error-free transforms in FP32: (s, e) with s + e = a + b exactly (TwoSum),
+// and a compensated accumulator (hi, lo) that carries about 48 bits without
+// touching GB300's slow FP64 pipe
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+// (hi, lo) += x * y with the product's rounding error kept (FMA TwoProduct)
+__device__ __forceinline__ void acc_prod(float& hi, float& lo, float x, float y) {
+    float p = x * y;
+    float pe = fmaf(x, y, -p);
+    float s, e;
+    two_sum(hi, p, s, e);
+    hi = s;
+    lo += e + pe;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -370,7 +390,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
             if (!ok) break;
             const int r = m0 + 32 * quad + lane;
             const double al = do_rho ? S.coef[l] : 0.0;
-            double s_nn = 0.0, s_nc = 0.0;
+            float snn_h = 0.0f, snn_l = 0.0f, snc_h = 0.0f, snc_l = 0.0f;
             T* xph = (T*)S.x16[2 * (1 - cur)];
             T* xpl = (T*)S.x16[2 * (1 - cur) + 1];
             const T* xch = (const T*)S.x16[2 * cur];
@@ -436,10 +456,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
                                 const T* clv = (const T*)&cl4;
 #pragma unroll
                                 for (int j = 0; j < 8; ++j) {
-                                    const double w = (cb + 8 * i + j == r) ? 1.0 : 2.0;
-                                    const double xc = (double)H16<BF>::to_f(chv[j]) + (double)H16<BF>::to_f(clv[j]);
-                                    s_nn = fma(w * xn[j], (double)xn[j], s_nn);
-                                    s_nc = fma(w * xn[j], xc, s_nc);
+                                    const float wx = (cb + 8 * i + j == r) ? xn[j] : 2.0f * xn[j];
+                                    const float xc = H16<BF>::to_f(chv[j]) + H16<BF>::to_f(clv[j]);
+                                    acc_prod(snn_h, snn_l, wx, xn[j]);
+                                    acc_prod(snc_h, snc_l, wx, xc);
                                 }
                             }
                         }
@@ -462,10 +482,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
                             }
                             if (do_rho) rho[e] = fma(al, (double)xn, rho[e]);
                             if (do_mom) {
-                                const double w = (c == r) ? 1.0 : 2.0;
-                                const double xc = (double)H16<BF>::to_f(xch[e]) + (double)H16<BF>::to_f(xcl[e]);
-                                s_nn = fma(w * xn, (double)xn, s_nn);
-                                s_nc = fma(w * xn, xc, s_nc);
+                                const float wx = (c == r) ? xn : 2.0f * xn;
+                                const float xc = H16<BF>::to_f(xch[e]) + H16<BF>::to_f(xcl[e]);
+                                acc_prod(snn_h, snn_l, wx, xn);
+                                acc_prod(snc_h, snc_l, wx, xc);
                             }
                             bad |= !(fabsf(xn) <= 4.0f);
                         }
@@ -473,6 +493,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
                 }
             }
             if (do_mom) {
+                double s_nn = (double)snn_h + (double)snn_l, s_nc = (double)snc_h + (double)snc_l;
                 for (int o = 16; o > 0; o >>= 1) {
                     s_nn += __shfl_down_sync(0xffffffffu, s_nn, o);
                     s_nc += __shfl_down_sync(0xffffffffu, s_nc, o);
@@ -802,6 +823,7 @@ void tc_rho_finish(const Ctx& c, cudaStream_t s) {
 namespace {
 std::mutex g_tune_mu;
 std::map<std::string, TcCfg> g_tuned;
+std::map<std::string, std::vector<float>> g_tune_ms;   // candidate times of the tuning run (diagnostics)
 bool g_tune_loaded = false;
 
 std::string tune_key(const TcBatch& b, int total_k) {
@@ -837,8 +859,13 @@ void tune_save() {
     f << "{\n";
     size_t i = 0;
     for (auto& kv : g_tuned)
-        f << "  \"" << kv.first << "\": [" << kv.second.bk << ", " << kv.second.persist << "]"
-          << (++i < g_tuned.size() ? "," : "") << "\n";
+    {
+        f << "  \"" << kv.first << "\": [" << kv.second.bk << ", " << kv.second.persist;
+        auto it = g_tune_ms.find(kv.first);
+        if (it != g_tune_ms.end())
+            for (float m : it->second) f << ", " << m;
+        f << "]" << (++i < g_tuned.size() ? "," : "") << "\n";
+    }
     f << "}\n";
 }
 }  // namespace
@@ -863,9 +890,10 @@ TcCfg tc_tuned(const TcBatch& b, int total_k) {
     return it == g_tuned.end() ? TcCfg{} : it->second;
 }
 
-void tc_record(const TcBatch& b, int total_k, TcCfg best, const float*, int) {
+void tc_record(const TcBatch& b, int total_k, TcCfg best, const float* ms, int n) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tuned[tune_key(b, total_k)] = best;
+    g_tune_ms[tune_key(b, total_k)] = std::vector<float>(ms, ms + n);
     tune_save();
 }
 
