@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="sphere25")
     ap.add_argument("--precision", default="fp16x3", choices=["fp64", "fp16x3", "bf16x3"])
+    ap.add_argument("--dm-only", action="store_true",
+                    help="time one dft_density_matrix call on the start potential instead of SCF steps")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the mixed-vs-FP64 comparison on the 64-atom cluster")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -234,6 +236,50 @@ def run_batched(args, rank, world):
         dist.destroy_process_group()
 
 
+def run_dm_only(args, dft, torch, sysm, prec, local, rank):
+    """P-columns/s of dft_density_matrix alone (K / its wall time), on the
+    Fock matrix of the superposition-of-atoms start; for workloads where a
+    full SCF step is minutes long (the 1963-atom sphere)."""
+    t0 = time.perf_counter()
+    ctx = dft.Context(sysm, device=f"cuda:{local}", precision=prec, cheb_tail_tol=1e-10,
+                      model=dft.DFT_MODEL_NEUTRAL)
+    ctx.overlap_kinetic()
+    n0 = ctx.initial_density()
+    v, _ = ctx.hartree_xc(n0)
+    V = ctx.potential_matrix(v)
+    S, T = ctx.overlap_kinetic()
+    F = V + T
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    ms, infos = [], []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, info = ctx.density_matrix(F)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        infos.append(info)
+    K = ctx.K
+    t = statistics.median(ms)
+    info = infos[-1]
+    flops = 3.0 * K * K * (K + 1)
+    per_launch = info.ms_stage[4] / 1000.0 / max(1, info.n_cheb - 2)
+    pk = peaks()
+    line = {"metric": METRIC, "value": K / (t / 1000.0), "unit": "P-columns/s (dft_density_matrix)", "n_gpus": 1,
+            "steps": args.steps, "warmup": 0, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": sysm.name, "n_basis": K, "n_atoms": sysm.n_atoms, "kT": sysm.kT,
+                       "n_cheb": info.n_cheb, "mode": "density matrix only", "setup_s": setup_s},
+            "stages_ms": [round(x, 3) for x in info.ms_stage],
+            "roofline": {"kernel": "k_cheb_step_tc", "bound": "tensor", "achieved": flops / per_launch / 1e12,
+                         "peak": pk.get("bf16_tflops_sustained", 1700.0), "unit": "TFLOP/s",
+                         "frac": flops / per_launch / 1e12 / pk.get("bf16_tflops_sustained", 1700.0)}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def compare_precisions(dft, torch, local, name="cluster64", steps=2):
     """Mixed (FP16x3) and FP64 GPU paths on the same SCF steps of the 64-atom
     cluster (the largest case where the FP64 path finishes in seconds): step
@@ -340,6 +386,9 @@ def main():
         dist.init_process_group("nccl")
     prec = {"fp64": dft.DFT_PREC_FP64, "fp16x3": dft.DFT_PREC_FP16X3, "bf16x3": dft.DFT_PREC_BF16X3}[args.precision]
     stream = torch.cuda.current_stream()
+    if args.dm_only:
+        run_dm_only(args, dft, torch, sysm, prec, local, rank)
+        return
     mixer = {"linear": dft.DFT_MIX_LINEAR, "kerker": dft.DFT_MIX_KERKER, "pulay": dft.DFT_MIX_PULAY}[args.mixer]
     ctx = dft.Context(sysm, device=f"cuda:{local}", precision=prec, cheb_tail_tol=1e-10, mix_alpha=0.3,
                       mixer=mixer, kerker_q0=0.8, mix_history=8,

@@ -7,11 +7,13 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <new>
+#include <thread>
 
 using namespace dft;
 
-unsigned long long dft::g_launches = 0;
+std::atomic<unsigned long long> dft::g_launches{0};
 
 namespace {
 
@@ -579,6 +581,44 @@ void scf_tail(Ctx& c, double* n_in_out, double* v_ks_out, double* P_out, dft_inf
     if (tm) loc->ms_stage[6] = tm->ms(7, 8);
 }
 
+// Run body(ctx, index, stream) for every system of a batch on host threads,
+// each system on its own stream; the systems' streams first wait for the work
+// already queued on `s`, and `s` waits for all of them at the end.
+template <class F>
+void fork_systems(std::vector<Ctx*>& cs, cudaStream_t s, F&& body) {
+    const int n = (int)cs.size();
+    cudaEvent_t start;
+    DFT_CUDA_CHECK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    DFT_CUDA_CHECK(cudaEventRecord(start, s));
+    for (Ctx* c : cs) {
+        if (!c->aux_stream) DFT_CUDA_CHECK(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+        if (!c->aux_done) DFT_CUDA_CHECK(cudaEventCreateWithFlags(&c->aux_done, cudaEventDisableTiming));
+        DFT_CUDA_CHECK(cudaStreamWaitEvent(c->aux_stream, start, 0));
+    }
+    int dev = 0;
+    DFT_CUDA_CHECK(cudaGetDevice(&dev));
+    const int nt = std::min(n, 16);
+    std::vector<std::exception_ptr> errs(nt);
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&, t] {
+            try {
+                DFT_CUDA_CHECK(cudaSetDevice(dev));
+                for (int q = t; q < n; q += nt) {
+                    body(*cs[q], q, cs[q]->aux_stream);
+                    DFT_CUDA_CHECK(cudaEventRecord(cs[q]->aux_done, cs[q]->aux_stream));
+                }
+            } catch (...) {
+                errs[t] = std::current_exception();
+            }
+        });
+    for (auto& x : th) x.join();
+    cudaEventDestroy(start);
+    for (auto& e : errs)
+        if (e) std::rethrow_exception(e);
+    for (Ctx* c : cs) DFT_CUDA_CHECK(cudaStreamWaitEvent(s, c->aux_done, 0));
+}
+
 // run a launch sequence through a CUDA graph cached in `lead` under (slot,
 // count): the recurrence loops are thousands of launches that repeat
 // unchanged from one SCF step to the next while N_C stays the same
@@ -619,7 +659,7 @@ extern "C" {
 
 const char* dft_version(void) { return kVersion; }
 
-unsigned long long dft_kernel_launches(void) { return g_launches; }
+unsigned long long dft_kernel_launches(void) { return g_launches.load(); }
 
 size_t dft_workspace_bytes(const dft_basis_desc* basis, const dft_grid_desc* grid, const dft_params* params) {
     try {
@@ -693,7 +733,7 @@ dft_status dft_overlap_kinetic(dft_ctx* ctx, double* S, double* T, void* stream)
         DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_A, c.d_S, K2, cudaMemcpyDeviceToDevice, s));
         DFT_CUDA_CHECK(cudaMemsetAsync(c.d_flags, 0, sizeof(int) * FLAG_COUNT, s));
         cholesky_inplace(c.d_A, c.K, c.d_flags + FLAG_CHOL, s);
-        tri_inverse_lower(c.d_A, c.d_Linv, c.K, s);
+        tri_inverse_lower(c.d_A, c.d_Linv, c.K, c.d_B, s);
         int flags[FLAG_COUNT];
         read_flags(c, s, flags);
         if (flags[FLAG_CHOL]) throw Error(DFT_ENOTCONV, "overlap matrix is not positive definite");
@@ -799,11 +839,13 @@ dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in
         Timer tm(s);
         std::vector<dft_info> loc(n);
         tm.mark(0);
-        // per system: potential, Fock matrix, bounds, N_C, split H_N, m_0..m_2
-        for (int q = 0; q < n; ++q) {
-            scf_head(*cs[q], n_in_out[q], s);
-            dm_prepare(*cs[q], cs[q]->d_F, s, nullptr, 0);
-        }
+        // per system, concurrently on the systems' own streams: potential, Fock
+        // matrix, bounds, N_C, split H_N, m_0..m_2 (each waits on the host for
+        // its bounds and order, so systems overlap each other's waits)
+        fork_systems(cs, s, [&](Ctx& c, int q, cudaStream_t as) {
+            scf_head(c, n_in_out[q], as);
+            dm_prepare(c, c.d_F, as, nullptr, 0);
+        });
         tm.mark(1);
         // one persistent launch per recurrence step for all systems: moments pass
         std::vector<int> lim(n), last(n);
@@ -842,11 +884,11 @@ dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in
             for (int l = l0; l < Lmax; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, gs);
         });
         tm.mark(4);
-        for (int q = 0; q < n; ++q) {
-            tc_rho_finish(*cs[q], s);
-            dm_finish(*cs[q], cs[q]->d_P, &loc[q], s);
-            scf_tail(*cs[q], n_in_out[q], nullptr, nullptr, &loc[q], s, nullptr);
-        }
+        fork_systems(cs, s, [&](Ctx& c, int q, cudaStream_t as) {
+            tc_rho_finish(c, as);
+            dm_finish(c, c.d_P, &loc[q], as);
+            scf_tail(c, n_in_out[q], nullptr, nullptr, &loc[q], as, nullptr);
+        });
         tm.mark(5);
         for (int q = 0; q < n; ++q) {
             loc[q].ms_stage[0] = tm.ms(0, 1);   // shared stages: potentials, Fock, bounds (all systems)
@@ -863,6 +905,8 @@ dft_status dft_destroy(dft_ctx* ctx) {
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     for (auto& g : c->graph_exec)
         if (g) cudaGraphExecDestroy(g);
+    if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+    if (c->aux_done) cudaEventDestroy(c->aux_done);
     if (c->plan_f) cufftDestroy(c->plan_f);
     if (c->plan_b) cufftDestroy(c->plan_b);
     if (c->kplan_f) cufftDestroy(c->kplan_f);

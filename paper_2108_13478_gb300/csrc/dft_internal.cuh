@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <stdint.h>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -123,6 +124,8 @@ struct Ctx {
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};   // batched recurrence loops
     int graph_count[2] = {0, 0};
     long long graph_key[2] = {0, 0};
+    cudaStream_t aux_stream = nullptr;   // per-system stream of batched steps
+    cudaEvent_t aux_done = nullptr;
 
     // learned warm start: descriptors, coefficients, hidden pre-activations, dL/dc
     double* d_wdesc = nullptr;   // [n_atoms][32]
@@ -173,7 +176,7 @@ void launch_gaussian_sum(const Ctx& c, double amp, double width, double* out, cu
 void dgemm(char ta, char tb, int M, int N, int Kd, double alpha, const double* A, int lda,
            const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s);
 int cholesky_inplace(double* A, int K, int* d_flag, cudaStream_t s);   // lower L, upper zeroed
-void tri_inverse_lower(const double* L, double* Linv, int K, cudaStream_t s);
+void tri_inverse_lower(const double* L, double* Linv, int K, double* tmp, cudaStream_t s);  // tmp: K^2 doubles
 // out = Linv F Linv^T and out = Linv^T R Linv for lower-triangular Linv and
 // symmetric F, R (FP64, k ranges cut to the triangle, upper tiles mirrored)
 void congruence_lower(int K, const double* Linv, const double* F, double* tmp, double* out, cudaStream_t s);
@@ -278,7 +281,7 @@ struct Error {
     Error(dft_status c, std::string m) : code(c), msg(std::move(m)) {}
 };
 // process-wide count of kernels this library has launched (diagnostics)
-extern unsigned long long g_launches;
+extern std::atomic<unsigned long long> g_launches;
 inline void check_launch(const char* what, int kernels = 1) {
     g_launches += (unsigned long long)kernels;
     cudaError_t e = cudaGetLastError();

@@ -589,12 +589,13 @@ __global__ void k_rho_mirror(int K, int Kp, const double* __restrict__ up, doubl
     out[e] = j >= i ? up[(long long)i * Kp + j] : up[(long long)j * Kp + i];
 }
 
-// trace and Frobenius norm of H_N as the recurrence sees it (split pair)
+// trace and Frobenius norm of H_N as the recurrence sees it (split pair):
+// per-block partials, then a fixed-order sum
 template <bool BF>
-__global__ void __launch_bounds__(256) k_split_norms(int K, int Kp, const void* hh_, const void* hl_, double* out) {
+__global__ void __launch_bounds__(256) k_split_norms(int K, int Kp, const void* hh_, const void* hl_, double* part) {
     using T = typename H16<BF>::T;
     double tr = 0.0, fr = 0.0;
-    for (long long e = threadIdx.x; e < (long long)K * K; e += 256) {
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < (long long)K * K; e += (long long)gridDim.x * 256) {
         int i = (int)(e / K), j = (int)(e % K);
         long long q = (long long)i * Kp + j;
         double h = (double)H16<BF>::to_f(((const T*)hh_)[q]) + (double)H16<BF>::to_f(((const T*)hl_)[q]);
@@ -604,8 +605,22 @@ __global__ void __launch_bounds__(256) k_split_norms(int K, int Kp, const void* 
     tr = block_sum<256>(tr);
     fr = block_sum<256>(fr);
     if (threadIdx.x == 0) {
-        out[0] = tr;
-        out[1] = fr;
+        part[2 * blockIdx.x] = tr;
+        part[2 * blockIdx.x + 1] = fr;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sum_pairs(int np, const double* part, double* out) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < np; i += 256) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    a = block_sum<256>(a);
+    b = block_sum<256>(b);
+    if (threadIdx.x == 0) {
+        out[0] = a;
+        out[1] = b;
     }
 }
 
@@ -793,9 +808,11 @@ void tc_split_h(const Ctx& c, cudaStream_t s) {
     if (bf) tc::k_split_matrix<true><<<tc::blocks_for(n, 256), 256, 0, s>>>(c.K, c.Kp, c.d_H, c.K, c.d_h16[0], c.d_h16[1]);
     else tc::k_split_matrix<false><<<tc::blocks_for(n, 256), 256, 0, s>>>(c.K, c.Kp, c.d_H, c.K, c.d_h16[0], c.d_h16[1]);
     check_launch("split_h");
-    if (bf) tc::k_split_norms<true><<<1, 256, 0, s>>>(c.K, c.Kp, c.d_h16[0], c.d_h16[1], c.d_scal + SCAL_TRACE);
-    else tc::k_split_norms<false><<<1, 256, 0, s>>>(c.K, c.Kp, c.d_h16[0], c.d_h16[1], c.d_scal + SCAL_TRACE);
-    check_launch("split_norms");
+    int np = (int)std::min<long long>(1024, ((long long)c.K * c.K + 255) / 256);
+    if (bf) tc::k_split_norms<true><<<np, 256, 0, s>>>(c.K, c.Kp, c.d_h16[0], c.d_h16[1], c.d_part);
+    else tc::k_split_norms<false><<<np, 256, 0, s>>>(c.K, c.Kp, c.d_h16[0], c.d_h16[1], c.d_part);
+    tc::k_sum_pairs<<<1, 256, 0, s>>>(np, c.d_part, c.d_scal + SCAL_TRACE);
+    check_launch("split_norms", 2);
 }
 
 // X pair 0 = I, X pair 1 = H_N (split); rho = a0 I + a1 H_N if coef

@@ -203,32 +203,35 @@ __global__ void k_zero_upper(double* A, int K) {
     if (j > i) A[e] = 0.0;
 }
 
-// X = L^-1 by forward substitution, one column per thread; warps share row loops
-__global__ void __launch_bounds__(128) k_tri_inverse(const double* __restrict__ L, double* __restrict__ X, int K) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    int cw = (blockIdx.x * blockDim.x + (threadIdx.x & ~31));   // first column of this warp
-    if (cw >= K) return;
-    bool act = c < K;
-    for (int r = cw; r < K; ++r) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        const double* Lr = L + (long long)r * K;
-        int m = cw;
-        for (; m + 3 < r; m += 4) {
-            if (act) {
-                s0 = fma(Lr[m], X[(long long)m * K + c], s0);
-                s1 = fma(Lr[m + 1], X[(long long)(m + 1) * K + c], s1);
-                s2 = fma(Lr[m + 2], X[(long long)(m + 2) * K + c], s2);
-                s3 = fma(Lr[m + 3], X[(long long)(m + 3) * K + c], s3);
+constexpr int TIB = 32;  // leaf size of the recursive triangular inverse
+
+// inverse of an n x n (n <= TIB) lower-triangular block in shared memory, one
+// column per thread (forward substitution), written with leading dimension ld
+__global__ void __launch_bounds__(TIB) k_tri_inv_block(const double* __restrict__ L, double* __restrict__ X, int n,
+                                                       int ld) {
+    __shared__ double Ls[TIB][TIB + 1];
+    __shared__ double Xs[TIB][TIB + 1];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int i = e / n, j = e % n;
+        Ls[i][j] = L[(long long)i * ld + j];
+    }
+    __syncthreads();
+    const int c = threadIdx.x;
+    if (c < n) {
+        for (int r = 0; r < n; ++r) {
+            double v = 0.0;
+            if (r >= c) {
+                double acc = (r == c) ? 1.0 : 0.0;
+                for (int m = c; m < r; ++m) acc -= Ls[r][m] * Xs[m][c];
+                v = acc / Ls[r][r];
             }
+            Xs[r][c] = v;
         }
-        for (; m < r; ++m)
-            if (act) s0 = fma(Lr[m], X[(long long)m * K + c], s0);
-        if (act) {
-            double rhs = (r == c) ? 1.0 : 0.0;
-            double v = (r < c) ? 0.0 : (rhs - ((s0 + s1) + (s2 + s3))) / Lr[r];
-            X[(long long)r * K + c] = v;
-        }
-        __syncwarp();
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int i = e / n, j = e % n;
+        X[(long long)i * ld + j] = Xs[i][j];
     }
 }
 
@@ -513,12 +516,31 @@ void congruence_lower_t(int K, const double* Linv, const double* R, double* tmp,
     check_launch("congruence_lower_t", 3);
 }
 
-void tri_inverse_lower(const double* L, double* Linv, int K, cudaStream_t s) {
-    // the kernel writes rows r >= (first column of each warp) only; the strictly
-    // upper part above that is zero and must be cleared here
+namespace {
+// inverse of the n x n lower-triangular block at L (leading dimension ld) into
+// X (same layout), by the block identity
+//   [A 0; B C]^-1 = [A^-1 0; -C^-1 B A^-1  C^-1]
+// with FP64 GEMMs; tmp holds at least n^2 / 4 + n TIB doubles
+void tri_inv_rec(const double* L, double* X, int n, int ld, double* tmp, cudaStream_t s) {
+    if (n <= TIB) {
+        k_tri_inv_block<<<1, TIB, 0, s>>>(L, X, n, ld);
+        check_launch("tri_inv_block");
+        return;
+    }
+    int n1 = ((n / 2) + TIB - 1) / TIB * TIB;
+    int n2 = n - n1;
+    tri_inv_rec(L, X, n1, ld, tmp, s);
+    tri_inv_rec(L + (long long)n1 * ld + n1, X + (long long)n1 * ld + n1, n2, ld, tmp, s);
+    // tmp = B A^-1 (n2 x n1); X_21 = -C^-1 tmp
+    dgemm('N', 'N', n2, n1, n1, 1.0, L + (long long)n1 * ld, ld, X, ld, 0.0, tmp, n1, s);
+    dgemm('N', 'N', n2, n1, n2, -1.0, X + (long long)n1 * ld + n1, ld, tmp, n1, 0.0, X + (long long)n1 * ld, ld, s);
+}
+}  // namespace
+
+void tri_inverse_lower(const double* L, double* Linv, int K, double* tmp, cudaStream_t s) {
+    // the strictly upper part of L^-1 is zero
     DFT_CUDA_CHECK(cudaMemsetAsync(Linv, 0, sizeof(double) * (size_t)K * K, s));
-    k_tri_inverse<<<blocks_for(K, 128), 128, 0, s>>>(L, Linv, K);
-    check_launch("tri_inverse");
+    tri_inv_rec(L, Linv, K, K, tmp, s);
 }
 
 void launch_overlap_kinetic(const Ctx& c, double* S, double* T, cudaStream_t s) {
