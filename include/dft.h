@@ -26,6 +26,16 @@
  *    host (spectral bounds to fix the Chebyshev order, the info struct)
  *    synchronise that stream before returning.
  *  - Device pointers must be 16-byte aligned.
+ *
+ * Environment (mixed-precision paths)
+ *  - DFT_AUTOTUNE_CACHE: JSON file that keeps the tensor-core launch shape
+ *    tuned per (precision, size bucket, batch size); read at the first
+ *    tuned launch, rewritten after each tuning.
+ *  - DFT_AUTOTUNE_OFF: any value disables tuning (the default shape runs).
+ *  - DFT_TC_SHAPE="bk,persist,bn": forces one launch shape (k-block 32 or
+ *    64; 0 = one CTA per tile, 1 or 2 = that many persistent CTAs per SM;
+ *    tile width 256, or 128 with bk = 32) and disables tuning.  Malformed
+ *    values are ignored.
  */
 #ifndef DFT_H
 #define DFT_H

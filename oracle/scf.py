@@ -135,7 +135,7 @@ def kerker(sysm, q0):
 
     def apply(r):
         rr = r.reshape(nz, ny, nx)
-        return np.fft.irfftn(np.fft.rfftn(rr) * w, s=(nz, ny, nx)).reshape(r.shape)
+        return np.fft.irfftn(np.fft.rfftn(rr) * w, s=(nz, ny, nx), axes=(0, 1, 2)).reshape(r.shape)
     return apply
 
 

@@ -133,7 +133,7 @@ void build_basis(Ctx& c, const dft_basis_desc* b, const dft_grid_desc* g, const 
     c.cheb_cap = 1 << 16;
     if (c.p.precision != DFT_PREC_FP64) {
         c.Kp = tc_pad(c.K);
-        c.n_tc_tiles = (int)(tc_tiles(c.K).size() / 2);
+        c.n_tc_tiles = (int)((tc_tiles(c.K, 256).size() + tc_tiles(c.K, 128).size()) / 2);
         c.tile_cap = std::max(c.n_tc_tiles, 1 << 17);
     }
     c.part_cap = std::max<long long>({2LL * cheb_step_parts(c.K), 2LL * c.tile_cap, 3LL * 1184, 2048, 592LL * 16}) + 64;
@@ -419,11 +419,12 @@ void dm_prepare(Ctx& c, const double* F, cudaStream_t s, Timer* tm, int t0) {
 // repeated.  Returns the first step not yet run.
 int tc_pass2_tuned(TcBatch& b, int total_k, int Lmax, cudaStream_t s) {
     int l = 2;
-    TcCfg cand[4];
+    TcCfg cand[8];
     const int nc = tc_candidates(cand);
     const int per = 2, rounds = 2;
     if (tc_needs_tuning(b, total_k) && Lmax - 2 >= nc * per * rounds + 8) {
-        float best_ms[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+        float best_ms[8];
+        for (float& x : best_ms) x = 1e30f;
         cudaEvent_t e0, e1;
         DFT_CUDA_CHECK(cudaEventCreate(&e0));
         DFT_CUDA_CHECK(cudaEventCreate(&e1));
@@ -617,6 +618,13 @@ void fork_systems(std::vector<Ctx*>& cs, cudaStream_t s, F&& body) {
     for (auto& e : errs)
         if (e) std::rethrow_exception(e);
     for (Ctx* c : cs) DFT_CUDA_CHECK(cudaStreamWaitEvent(s, c->aux_done, 0));
+}
+
+// identifies a batch's tile list and launch shape for the graph cache
+long long batch_key(const TcBatch& b) {
+    long long k = (long long)b.ntiles[0] * 128 + b.nsys;
+    k = k * 4 + (b.cfg.bk == 64) + 2 * (b.cfg.bn == 128);
+    return k * 4 + b.cfg.persist;
 }
 
 // run a launch sequence through a CUDA graph cached in `lead` under (slot,
@@ -862,7 +870,7 @@ dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in
         int total_k = 0;
         for (int q = 0; q < n; ++q) total_k += cs[q]->K;
         b.cfg = tc_tuned(b, total_k);
-        const long long gkey1 = ((long long)b.ntiles * 128 + b.nsys) * 256 + b.cfg.bk + b.cfg.persist;
+        const long long gkey1 = batch_key(b);
         run_graph(lead, 0, Jmax, gkey1, s, [&](cudaStream_t gs) {
             for (int j = 1; j <= Jmax; ++j) {
                 tc_step_batch(b, j, j & 1, 2, gs);
@@ -879,7 +887,7 @@ dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in
         tc_set_limits(b, cs.data(), lim.data(), last.data(), s);
         tm.mark(3);
         const int l0 = tc_pass2_tuned(b, total_k, Lmax, s);
-        const long long gkey2 = (((long long)b.ntiles * 128 + b.nsys) * 256 + b.cfg.bk + b.cfg.persist) * 65536 + l0;
+        const long long gkey2 = batch_key(b) * 65536 + l0;
         run_graph(lead, 1, Lmax - l0, gkey2, s, [&](cudaStream_t gs) {
             for (int l = l0; l < Lmax; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, gs);
         });

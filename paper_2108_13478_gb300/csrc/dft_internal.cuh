@@ -33,7 +33,8 @@ struct Fn {
 // one system of a (possibly batched) tensor-core Chebyshev launch
 struct TcSys {
     int K, Kp, nk, lim;      // steps l >= lim skip this system
-    int n_c, part_off, mom_last, ntl;   // ntl: its tiles; part_off: first partial slot
+    int n_c, mom_last;
+    int part_off[2], ntl[2]; // per tile width (256, 128): its tiles and first partial slot
     void* x16[4];            // X pairs (hi, lo) x 2, Kp x Kp 16-bit
     double* rho;             // Kp x Kp FP64 upper triangle
     const double* coef;
@@ -43,12 +44,13 @@ struct TcTile {
     int sys, i, j, idx;      // system, row tile, column tile, index within the system
 };
 constexpr int TC_MAX_SYS = 64;
-constexpr int TC_MAPS_PER_SYS = 12;
+constexpr int TC_MAPS_PER_SYS = 16;
 
 // launch configuration of the tensor-core step (chosen by the autotuner)
 struct TcCfg {
-    int bk = 32;        // k-block width: 32 (4-stage ring) or 64 (2-stage ring)
+    int bk = 32;        // k-block width: 32 or 64 (64 only with 256-wide tiles)
     int persist = 0;    // 0: one CTA per tile; p > 0: p CTAs per SM, strided tile loop
+    int bn = 256;       // output tile width: 256 (one CTA per SM) or 128 (two CTAs per SM)
 };
 struct Ctx {
     // problem
@@ -113,7 +115,9 @@ struct Ctx {
     double* d_rho_tc = nullptr;  // [Kp x Kp] FP64, upper triangle accumulated
     CUtensorMap tm_h[2][2];      // host copies of this system's tensor maps,
     CUtensorMap tm_x[2][4];      // per k-block variant (32 or 64 wide)
-    // batch area (device): system table, tensor maps (6 per system), tile list
+    CUtensorMap tm_xn[4];        // X maps with 128-row boxes (128-wide tiles, 32-wide k-blocks)
+    // batch area (device): system table, tensor maps (16 per system), tile
+    // lists of both tile widths
     TcSys* d_systab = nullptr;
     CUtensorMap* d_maps = nullptr;
     TcTile* d_tiles = nullptr;
@@ -215,14 +219,15 @@ void launch_moment_reduce(int nparts, const double* part, double* mom, int idx_e
 
 // ---- tensor-core Chebyshev path (k_cheb_tc.cu) ----
 int tc_pad(int K);
-std::vector<int> tc_tiles(int K);
+std::vector<int> tc_tiles(int K, int bn);   // (row tile, column tile) pairs reaching the upper triangle
 void tc_setup(Ctx& c);
 void tc_split_h(const Ctx& c, cudaStream_t s);        // H_N -> 16-bit pair; trace, |H|^2 -> scal[SCAL_TRACE..+1]
 void tc_init(const Ctx& c, const double* coef, cudaStream_t s);
 // a launch over several systems whose tables sit in `leader`'s batch area
 struct TcBatch {
     const Ctx* leader = nullptr;
-    int nsys = 0, ntiles = 0;
+    int nsys = 0;
+    int ntiles[2] = {0, 0}, tile_off[2] = {0, 0};   // per tile width (256, 128)
     bool bf = false;
     TcCfg cfg;
 };

@@ -12,15 +12,17 @@
 // (about 48 bits): GB300's FP64 pipe issues 2 FMA per SM per clock, and two
 // FP64 products per element cost the moments pass ~20% of its time.
 //
-// Per CTA: one 128 x 256 output tile, 10 warps.  Warp 0 lane 0 drives TMA
-// loads of the four operand tiles per 64-wide k-block into a 2-stage ring;
-// warp 1 owns the tensor-memory allocation and lane 0 issues the MMAs.  The
-// k range is cut into chunks of GK k-blocks that alternate between two
-// accumulators in tensor memory; eight epilogue warps add every finished chunk
-// into FP32 registers with round-to-nearest (so no accumulation chain in the
-// tensor core is longer than one chunk) and then run the fused update.  Every
-// wait is bounded in time: on expiry the CTA records FLAG_TIMEOUT, drains what
-// it issued and returns.
+// Per CTA: one 128 x BN output tile (BN = 256 with one CTA per SM, or 128 with
+// two CTAs per SM, so that one CTA's epilogue overlaps the other's MMAs and
+// the last wave of tiles is finer).  Warp 0 lane 0 drives TMA loads of the
+// four operand tiles per k-block into a stage ring; warp 1 owns the
+// tensor-memory allocation and lane 0 issues the MMAs.  The k range is cut
+// into chunks of 256 that alternate between two accumulators in tensor memory;
+// the epilogue warps (four per 128 columns, one per tensor-memory lane
+// quadrant) add every finished chunk into FP32 registers with round-to-nearest
+// (so no accumulation chain in the tensor core is longer than one chunk) and
+// then run the fused update.  Every wait is bounded in time: on expiry the CTA
+// records FLAG_TIMEOUT, drains what it issued and returns.
 #include "dft_internal.cuh"
 
 #include <cuda.h>
@@ -40,24 +42,29 @@
 namespace dft {
 namespace tc {
 
-constexpr int BM = 128, BN = 256;
-constexpr int NEPI = 256;                             // epilogue threads (8 warps)
-constexpr int NTHREADS = 64 + NEPI;                   // + producer warp + MMA warp
-// k-block variants: 32 wide (64-byte rows and swizzle, 4 stages) or 64 wide
-// (128-byte rows and swizzle, 2 stages); either way a 192 KB operand ring and
-// chunks of 256 of K between promotions
-template <int BK_>
+constexpr int BM = 128;
+constexpr int CPT = 128;   // accumulator columns held by one epilogue thread
+// Launch variants.  256-wide tiles: k-blocks 32 wide (64-byte rows and
+// swizzle, 4 stages) or 64 wide (128-byte rows and swizzle, 2 stages), a
+// 192 KB operand ring, 512 tensor-memory columns, one CTA per SM.  128-wide
+// tiles: 32-wide k-blocks in a 3-stage 96 KB ring and 256 columns, so two
+// CTAs share an SM.  Chunks of 256 of K between promotions throughout.
+template <int BK_, int BN_>
 struct Cfg {
-    static constexpr int BK = BK_;
-    static constexpr int STAGES = BK_ == 64 ? 2 : 4;
+    static_assert(BN_ == 256 || (BN_ == 128 && BK_ == 32), "unsupported tile shape");
+    static constexpr int BK = BK_, BN = BN_;
+    static constexpr int NEPI = BN_;                  // epilogue threads: 4 warps per 128 columns
+    static constexpr int NTHREADS = 64 + NEPI;        // + producer warp + MMA warp
+    static constexpr int MINB = BN_ == 128 ? 2 : 1;   // resident CTAs per SM
+    static constexpr int STAGES = BN_ == 128 ? 3 : (BK_ == 64 ? 2 : 4);
     static constexpr int GK = 256 / BK_;
     static constexpr int ROW_BYTES = BK_ * 2;
     static constexpr int A_BYTES = BM * BK_ * 2;
-    static constexpr int B_BYTES = BN * BK_ * 2;
+    static constexpr int B_BYTES = BN_ * BK_ * 2;
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
+    static constexpr int TMEM_COLS = 2 * BN_;         // two chunk accumulators
 };
-constexpr int TMEM_COLS = 2 * BN;                     // two chunk accumulators
 constexpr unsigned long long WAIT_NS = 1000000000ull;   // 1 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -204,25 +211,27 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// barrier among the NEPI epilogue threads only (the producer and MMA warps
-// keep running their own loops)
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(NEPI) : "memory"); }
+// barrier among the N epilogue threads only (the producer and MMA warps keep
+// running their own loops)
+template <int N>
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
 
 // Persistent multi-system step.  Each CTA walks the tile list with stride
 // gridDim.x; a tile of system s is active when l < sys[s].lim.  Pipeline
 // phases (stage ring, chunk accumulators) run on across tiles, so the MMA
 // warp starts the next tile's first two chunks while the epilogue warps
 // finish the previous tile.
-template <bool BF, int BKV>
-__global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __restrict__ sys,
+template <bool BF, int BKV, int BNV>
+__global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) k_cheb_step_tc(const TcSys* __restrict__ sys,
                                                               const CUtensorMap* __restrict__ maps,
                                                               const TcTile* __restrict__ tiles, int ntiles, int l,
                                                               int cur, int mode, double* __restrict__ part,
                                                               int* __restrict__ flags) {
     using T = typename H16<BF>::T;
-    using C = Cfg<BKV>;
-    constexpr int BK = C::BK, STAGES = C::STAGES, GK = C::GK, STAGE_BYTES = C::STAGE_BYTES;
-    constexpr int A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
+    using C = Cfg<BKV, BNV>;
+    constexpr int BK = C::BK, BN = C::BN, STAGES = C::STAGES, GK = C::GK, STAGE_BYTES = C::STAGE_BYTES;
+    constexpr int A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES, NEPI = C::NEPI, TMEM_COLS = C::TMEM_COLS;
+    constexpr int V = BN == 128 ? 1 : 0;   // tile-width variant (partial-sum slots)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -275,7 +284,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
                 const TcTile tl = tiles[t];
                 const TcSys& S = sys[tl.sys];
                 if (l >= S.lim) continue;
-                const CUtensorMap* mp = maps + 12 * tl.sys + (BK == 64 ? 6 : 0);
+                const CUtensorMap* mp = maps + TC_MAPS_PER_SYS * tl.sys + (BK == 64 ? 6 : 0);
+                // X operand maps: 256-row boxes beside the H maps, or the 128-row set
+                const CUtensorMap* mb = BN == 128 ? maps + TC_MAPS_PER_SYS * tl.sys + 12 : mp + 2;
                 const int m0 = tl.i * BM, n0 = tl.j * BN;
                 const int nk = (S.K + BK - 1) / BK;
                 for (int kb = 0; kb < nk; ++kb, ++g) {
@@ -288,8 +299,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
                     mbar_expect_tx(&full[s], STAGE_BYTES);
                     tma_load_2d(sAh(s), mp + 0, kb * BK, m0, &full[s]);
                     tma_load_2d(sAl(s), mp + 1, kb * BK, m0, &full[s]);
-                    tma_load_2d(sBh(s), mp + 2 + 2 * cur, kb * BK, n0, &full[s]);
-                    tma_load_2d(sBl(s), mp + 3 + 2 * cur, kb * BK, n0, &full[s]);
+                    tma_load_2d(sBh(s), mb + 2 * cur, kb * BK, n0, &full[s]);
+                    tma_load_2d(sBl(s), mb + 1 + 2 * cur, kb * BK, n0, &full[s]);
                 }
             }
             if (*abort_flag) {
@@ -354,7 +365,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
         }
         __syncwarp();
     } else {
-        // ---- epilogue warps: quadrant = warp % 4 (tensor-memory lane group), half = column half ----
+        // ---- epilogue warps: quadrant = warp % 4 (tensor-memory lane group), half = 128-column group ----
         const int quad = warp & 3;
         const int half = (warp - 2) >> 2;
         long long qg = 0;
@@ -366,9 +377,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
             if (l >= S.lim) continue;
             const int nchunk = ((S.K + BK - 1) / BK + GK - 1) / GK;
             const int m0 = tl.i * BM, n0 = tl.j * BN;
-            float R[BN / 2];
+            float R[CPT];
 #pragma unroll
-            for (int i = 0; i < BN / 2; ++i) R[i] = 0.0f;
+            for (int i = 0; i < CPT; ++i) R[i] = 0.0f;
             for (int q = 0; q < nchunk; ++q, ++qg) {
                 const int a = (int)(qg & 1);
                 const bool got = mbar_wait(&accfull[a], (uint32_t)((qg >> 1) & 1));
@@ -377,10 +388,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
                 tc_fence_after();
                 // promote the chunk's partial sums: round-to-nearest FP32 adds in registers
 #pragma unroll
-                for (int cc = 0; cc < BN / 64; ++cc) {
+                for (int cc = 0; cc < CPT / 32; ++cc) {
                     uint32_t v[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * BN + half * (BN / 2) + cc * 32),
-                              v);
+                    tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * BN + half * CPT + cc * 32), v);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) R[cc * 32 + j] += __uint_as_float(v[j]);
                 }
@@ -401,8 +411,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
             if (r < K) {
                 const size_t rowoff = (size_t)r * Kp;
 #pragma unroll
-                for (int cc = 0; cc < BN / 64; ++cc) {
-                    const int cb = n0 + half * (BN / 2) + cc * 32;
+                for (int cc = 0; cc < CPT / 32; ++cc) {
+                    const int cb = n0 + half * CPT + cc * 32;
                     if (cb + 31 < r || cb >= K) continue;
                     const bool vec = (cb >= r) && (cb + 31 < K);
                     if (vec) {
@@ -502,17 +512,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
                     red[2 * (warp - 2)] = s_nn;
                     red[2 * (warp - 2) + 1] = s_nc;
                 }
-                epi_sync();
+                epi_sync<NEPI>();
                 if (threadIdx.x == 64) {
                     double a0 = 0.0, a1 = 0.0;
                     for (int w = 0; w < NEPI / 32; ++w) {
                         a0 += red[2 * w];
                         a1 += red[2 * w + 1];
                     }
-                    part[2 * (S.part_off + tl.idx)] = a0;
-                    part[2 * (S.part_off + tl.idx) + 1] = a1;
+                    part[2 * (S.part_off[V] + tl.idx)] = a0;
+                    part[2 * (S.part_off[V] + tl.idx) + 1] = a1;
                 }
-                epi_sync();
+                epi_sync<NEPI>();
             }
         }
         if (bad) atomicExch(&flags[FLAG_SPECTRUM], 1);
@@ -527,14 +537,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cheb_step_tc(const TcSys* __res
 }
 
 // per-system moment reduction: block b sums the partials of system b's tiles
+// (tile-width variant v)
 __global__ void __launch_bounds__(256) k_moment_reduce_multi(const TcSys* __restrict__ sys,
-                                                             const double* __restrict__ part, int j) {
+                                                             const double* __restrict__ part, int j, int v) {
     const TcSys& S = sys[blockIdx.x];
     if (j > S.mom_last) return;
     double s0 = 0.0, s1 = 0.0;
-    for (int i = threadIdx.x; i < S.ntl; i += 256) {
-        s0 += part[2 * (S.part_off + i)];
-        s1 += part[2 * (S.part_off + i) + 1];
+    for (int i = threadIdx.x; i < S.ntl[v]; i += 256) {
+        s0 += part[2 * (S.part_off[v] + i)];
+        s1 += part[2 * (S.part_off[v] + i) + 1];
     }
     s0 = block_sum<256>(s0);
     s1 = block_sum<256>(s1);
@@ -653,14 +664,14 @@ void make_map(CUtensorMap* m, const void* base, int Kp, int box_rows, int bk) {
 
 }  // namespace tc
 
-int tc_pad(int K) { return (K + tc::BN - 1) / tc::BN * tc::BN; }
+int tc_pad(int K) { return (K + 255) / 256 * 256; }
 
-std::vector<int> tc_tiles(int K) {
+std::vector<int> tc_tiles(int K, int bn) {
     std::vector<int> t;
-    int mt = (K + tc::BM - 1) / tc::BM, nt = (K + tc::BN - 1) / tc::BN;
+    int mt = (K + tc::BM - 1) / tc::BM, nt = (K + bn - 1) / bn;
     for (int i = 0; i < mt; ++i)
         for (int j = 0; j < nt; ++j)
-            if (j * tc::BN + tc::BN - 1 >= i * tc::BM) {
+            if (j * bn + bn - 1 >= i * tc::BM) {
                 t.push_back(i);
                 t.push_back(j);
             }
@@ -675,33 +686,33 @@ void tc_setup(Ctx& c) {
         const int bk = v ? 64 : 32;
         tc::make_map(&c.tm_h[v][0], c.d_h16[0], c.Kp, tc::BM, bk);
         tc::make_map(&c.tm_h[v][1], c.d_h16[1], c.Kp, tc::BM, bk);
-        for (int q = 0; q < 4; ++q) tc::make_map(&c.tm_x[v][q], c.d_x16[q], c.Kp, tc::BN, bk);
+        for (int q = 0; q < 4; ++q) tc::make_map(&c.tm_x[v][q], c.d_x16[q], c.Kp, 256, bk);
     }
+    for (int q = 0; q < 4; ++q) tc::make_map(&c.tm_xn[q], c.d_x16[q], c.Kp, 128, 32);
     static bool attr_done = false;
     if (!attr_done) {
-        DFT_CUDA_CHECK(cudaFuncSetAttribute(tc::k_cheb_step_tc<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            tc::Cfg<32>::SMEM_BYTES));
-        DFT_CUDA_CHECK(cudaFuncSetAttribute(tc::k_cheb_step_tc<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            tc::Cfg<32>::SMEM_BYTES));
-        DFT_CUDA_CHECK(cudaFuncSetAttribute(tc::k_cheb_step_tc<false, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            tc::Cfg<64>::SMEM_BYTES));
-        DFT_CUDA_CHECK(cudaFuncSetAttribute(tc::k_cheb_step_tc<true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            tc::Cfg<64>::SMEM_BYTES));
+        auto attr = [](auto kern, int bytes) {
+            DFT_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        };
+        attr(tc::k_cheb_step_tc<false, 32, 256>, tc::Cfg<32, 256>::SMEM_BYTES);
+        attr(tc::k_cheb_step_tc<true, 32, 256>, tc::Cfg<32, 256>::SMEM_BYTES);
+        attr(tc::k_cheb_step_tc<false, 64, 256>, tc::Cfg<64, 256>::SMEM_BYTES);
+        attr(tc::k_cheb_step_tc<true, 64, 256>, tc::Cfg<64, 256>::SMEM_BYTES);
+        attr(tc::k_cheb_step_tc<false, 32, 128>, tc::Cfg<32, 128>::SMEM_BYTES);
+        attr(tc::k_cheb_step_tc<true, 32, 128>, tc::Cfg<32, 128>::SMEM_BYTES);
         attr_done = true;
     }
 }
 
 namespace {
-TcSys sys_entry(const Ctx& c, int lim, int mom_last, int part_off, int ntl) {
+TcSys sys_entry(const Ctx& c, int lim, int mom_last) {
     TcSys e{};
     e.K = c.K;
     e.Kp = c.Kp;
     e.nk = 0;
     e.lim = lim;
     e.n_c = 0;
-    e.part_off = part_off;
     e.mom_last = mom_last;
-    e.ntl = ntl;
     for (int q = 0; q < 4; ++q) e.x16[q] = c.d_x16[q];
     e.rho = c.d_rho_tc;
     e.coef = c.d_coef;
@@ -723,30 +734,41 @@ int num_sms() {
 TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const int* mom_last, cudaStream_t s) {
     if (nsys < 1 || nsys > TC_MAX_SYS) throw Error(DFT_EINVAL, "batch size out of range");
     std::vector<TcSys> tab(nsys);
-    std::vector<CUtensorMap> maps(12 * (size_t)nsys);
+    std::vector<CUtensorMap> maps(TC_MAPS_PER_SYS * (size_t)nsys);
     std::vector<TcTile> tiles;
+    TcBatch b;
     int part_off = 0;
-    // interleave the systems' tiles so that consecutive CTAs mix large and small systems
-    std::vector<std::vector<int>> per(nsys);
-    for (int q = 0; q < nsys; ++q) per[q] = tc_tiles(sys[q]->K);
     for (int q = 0; q < nsys; ++q) {
         const Ctx& c = *sys[q];
         if (c.Kp == 0) throw Error(DFT_EINVAL, "batched step needs a mixed-precision context");
         if (c.p.precision != leader.p.precision) throw Error(DFT_EINVAL, "batch mixes precisions");
-        int ntl = (int)per[q].size() / 2;
-        tab[q] = sys_entry(c, lim[q], mom_last[q], part_off, ntl);
-        part_off += ntl;
+        tab[q] = sys_entry(c, lim[q], mom_last[q]);
+        CUtensorMap* m = &maps[TC_MAPS_PER_SYS * (size_t)q];
         for (int v = 0; v < 2; ++v) {
-            maps[12 * q + 6 * v + 0] = c.tm_h[v][0];
-            maps[12 * q + 6 * v + 1] = c.tm_h[v][1];
-            for (int k = 0; k < 4; ++k) maps[12 * q + 6 * v + 2 + k] = c.tm_x[v][k];
+            m[6 * v + 0] = c.tm_h[v][0];
+            m[6 * v + 1] = c.tm_h[v][1];
+            for (int k = 0; k < 4; ++k) m[6 * v + 2 + k] = c.tm_x[v][k];
         }
+        for (int k = 0; k < 4; ++k) m[12 + k] = c.tm_xn[k];
     }
-    size_t longest = 0;
-    for (auto& v : per) longest = std::max(longest, v.size() / 2);
-    for (size_t t = 0; t < longest; ++t)
-        for (int q = 0; q < nsys; ++q)
-            if (t < per[q].size() / 2) tiles.push_back(TcTile{q, per[q][2 * t], per[q][2 * t + 1], (int)t});
+    // one tile list per tile width; each interleaves the systems' tiles so
+    // that consecutive CTAs mix large and small systems
+    for (int v = 0; v < 2; ++v) {
+        std::vector<std::vector<int>> per(nsys);
+        for (int q = 0; q < nsys; ++q) {
+            per[q] = tc_tiles(sys[q]->K, v ? 128 : 256);
+            tab[q].ntl[v] = (int)per[q].size() / 2;
+            tab[q].part_off[v] = part_off;
+            part_off += tab[q].ntl[v];
+        }
+        b.tile_off[v] = (int)tiles.size();
+        size_t longest = 0;
+        for (auto& x : per) longest = std::max(longest, x.size() / 2);
+        for (size_t t = 0; t < longest; ++t)
+            for (int q = 0; q < nsys; ++q)
+                if (t < per[q].size() / 2) tiles.push_back(TcTile{q, per[q][2 * t], per[q][2 * t + 1], (int)t});
+        b.ntiles[v] = (int)tiles.size() - b.tile_off[v];
+    }
     if ((int)tiles.size() > leader.tile_cap) throw Error(DFT_ENOMEM, "batch tile list exceeds the leader's capacity");
     if ((long long)2 * part_off > leader.part_cap) throw Error(DFT_ENOMEM, "batch partial sums exceed the leader's capacity");
     DFT_CUDA_CHECK(cudaMemcpyAsync(leader.d_systab, tab.data(), sizeof(TcSys) * nsys, cudaMemcpyHostToDevice, s));
@@ -755,10 +777,8 @@ TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const i
     DFT_CUDA_CHECK(cudaMemcpyAsync(leader.d_tiles, tiles.data(), sizeof(TcTile) * tiles.size(),
                                    cudaMemcpyHostToDevice, s));
     DFT_CUDA_CHECK(cudaStreamSynchronize(s));   // host staging buffers go out of scope
-    TcBatch b;
     b.leader = &leader;
     b.nsys = nsys;
-    b.ntiles = (int)tiles.size();
     b.bf = leader.p.precision == DFT_PREC_BF16X3;
     return b;
 }
@@ -782,23 +802,31 @@ void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s) {
     // launch shape (tuned): one CTA per tile, with the hardware handing tiles
     // to SMs as they free up, or a persistent grid of `persist` CTAs per SM
     // walking the tile list with a fixed stride
-    int grid = b.cfg.persist > 0 ? std::min(b.ntiles, b.cfg.persist * num_sms()) : b.ntiles;
-    auto go = [&](auto kern, int smem) {
-        kern<<<grid, tc::NTHREADS, smem, s>>>(L.d_systab, L.d_maps, L.d_tiles, b.ntiles, l, cur, mode, L.d_part,
-                                             L.d_flags);
+    const int v = b.cfg.bn == 128 ? 1 : 0;
+    const int nt = b.ntiles[v];
+    if (nt == 0) return;
+    const TcTile* tiles = L.d_tiles + b.tile_off[v];
+    int grid = b.cfg.persist > 0 ? std::min(nt, b.cfg.persist * num_sms()) : nt;
+    auto go = [&](auto kern, auto cfg) {
+        using C = decltype(cfg);
+        kern<<<grid, C::NTHREADS, C::SMEM_BYTES, s>>>(L.d_systab, L.d_maps, tiles, nt, l, cur, mode, L.d_part,
+                                                      L.d_flags);
     };
-    if (b.cfg.bk == 64) {
-        if (b.bf) go(tc::k_cheb_step_tc<true, 64>, tc::Cfg<64>::SMEM_BYTES);
-        else go(tc::k_cheb_step_tc<false, 64>, tc::Cfg<64>::SMEM_BYTES);
+    if (v == 1) {
+        if (b.bf) go(tc::k_cheb_step_tc<true, 32, 128>, tc::Cfg<32, 128>{});
+        else go(tc::k_cheb_step_tc<false, 32, 128>, tc::Cfg<32, 128>{});
+    } else if (b.cfg.bk == 64) {
+        if (b.bf) go(tc::k_cheb_step_tc<true, 64, 256>, tc::Cfg<64, 256>{});
+        else go(tc::k_cheb_step_tc<false, 64, 256>, tc::Cfg<64, 256>{});
     } else {
-        if (b.bf) go(tc::k_cheb_step_tc<true, 32>, tc::Cfg<32>::SMEM_BYTES);
-        else go(tc::k_cheb_step_tc<false, 32>, tc::Cfg<32>::SMEM_BYTES);
+        if (b.bf) go(tc::k_cheb_step_tc<true, 32, 256>, tc::Cfg<32, 256>{});
+        else go(tc::k_cheb_step_tc<false, 32, 256>, tc::Cfg<32, 256>{});
     }
     check_launch("cheb_step_tc");
 }
 
 void tc_moment_reduce_batch(const TcBatch& b, int j, cudaStream_t s) {
-    tc::k_moment_reduce_multi<<<b.nsys, 256, 0, s>>>(b.leader->d_systab, b.leader->d_part, j);
+    tc::k_moment_reduce_multi<<<b.nsys, 256, 0, s>>>(b.leader->d_systab, b.leader->d_part, j, b.cfg.bn == 128 ? 1 : 0);
     check_launch("moment_reduce_multi");
 }
 
@@ -851,7 +879,8 @@ std::string tune_key(const TcBatch& b, int total_k) {
     return o.str();
 }
 
-// cache file: one entry per line, `"key": [bk, persist],` inside braces
+// cache file: one entry per line, `"key": [bk, persist, bn, ms...],` inside
+// braces (entries without bn are 256-wide)
 void tune_load() {
     if (g_tune_loaded) return;
     g_tune_loaded = true;
@@ -863,8 +892,10 @@ void tune_load() {
         size_t q0 = line.find('"'), q1 = line.find('"', q0 + 1), lb = line.find('[', q1 + 1);
         if (q0 == std::string::npos || q1 == std::string::npos || lb == std::string::npos) continue;
         TcCfg c;
-        if (std::sscanf(line.c_str() + lb, "[%d, %d]", &c.bk, &c.persist) == 2 && (c.bk == 32 || c.bk == 64) &&
-            c.persist >= 0 && c.persist <= 1)
+        int n = std::sscanf(line.c_str() + lb, "[%d, %d, %d", &c.bk, &c.persist, &c.bn);
+        if (n == 2) c.bn = 256;
+        if (n >= 2 && (c.bk == 32 || c.bk == 64) && c.persist >= 0 && c.persist <= 2 &&
+            (c.bn == 256 || (c.bn == 128 && c.bk == 32)))
             g_tuned[line.substr(q0 + 1, q1 - q0 - 1)] = c;
     }
 }
@@ -877,7 +908,7 @@ void tune_save() {
     size_t i = 0;
     for (auto& kv : g_tuned)
     {
-        f << "  \"" << kv.first << "\": [" << kv.second.bk << ", " << kv.second.persist;
+        f << "  \"" << kv.first << "\": [" << kv.second.bk << ", " << kv.second.persist << ", " << kv.second.bn;
         auto it = g_tune_ms.find(kv.first);
         if (it != g_tune_ms.end())
             for (float m : it->second) f << ", " << m;
@@ -888,19 +919,35 @@ void tune_save() {
 }  // namespace
 
 int tc_candidates(TcCfg* out) {
-    const TcCfg c[4] = {{32, 0}, {64, 0}, {32, 1}, {64, 1}};
-    for (int i = 0; i < 4; ++i) out[i] = c[i];
-    return 4;
+    const TcCfg c[6] = {{32, 0, 256}, {64, 0, 256}, {32, 1, 256}, {64, 1, 256}, {32, 0, 128}, {32, 2, 128}};
+    for (int i = 0; i < 6; ++i) out[i] = c[i];
+    return 6;
+}
+
+// launch shape forced through DFT_TC_SHAPE="bk,persist,bn"
+static bool forced_shape(TcCfg& c) {
+    const char* e = std::getenv("DFT_TC_SHAPE");
+    if (!e) return false;
+    TcCfg f;
+    if (std::sscanf(e, "%d,%d,%d", &f.bk, &f.persist, &f.bn) != 3) return false;
+    if (!((f.bk == 32 || f.bk == 64) && f.persist >= 0 && f.persist <= 2 &&
+          (f.bn == 256 || (f.bn == 128 && f.bk == 32))))
+        return false;
+    c = f;
+    return true;
 }
 
 bool tc_needs_tuning(const TcBatch& b, int total_k) {
-    if (std::getenv("DFT_AUTOTUNE_OFF")) return false;
+    TcCfg f;
+    if (std::getenv("DFT_AUTOTUNE_OFF") || forced_shape(f)) return false;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_load();
     return g_tuned.find(tune_key(b, total_k)) == g_tuned.end();
 }
 
 TcCfg tc_tuned(const TcBatch& b, int total_k) {
+    TcCfg f;
+    if (forced_shape(f)) return f;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_load();
     auto it = g_tuned.find(tune_key(b, total_k));
