@@ -174,6 +174,7 @@ size_t carve(Ctx& c, char* base) {
     size_t o_wz = L.off(sizeof(float) * 3 * 128 * (size_t)c.n_atoms);
     size_t o_wdc = L.off(sizeof(double) * 16 * (size_t)c.n_atoms);
     size_t o_h16[2] = {0, 0}, o_x16[4] = {0, 0, 0, 0}, o_rtc = 0, o_tiles = 0, o_systab = 0, o_maps = 0;
+    size_t o_cst = 0, o_skf = 0, o_skb = 0;
     if (c.Kp > 0) {
         size_t P16 = (size_t)c.Kp * c.Kp * 2;
         for (auto& o : o_h16) o = L.off(P16);
@@ -182,6 +183,9 @@ size_t carve(Ctx& c, char* base) {
         o_systab = L.off(sizeof(TcSys) * TC_MAX_SYS);
         o_maps = L.off(sizeof(CUtensorMap) * TC_MAPS_PER_SYS * TC_MAX_SYS);
         o_tiles = L.off(sizeof(TcTile) * (size_t)c.tile_cap);
+        o_cst = L.off(sizeof(int) * ((size_t)c.tile_cap + 1));
+        o_skf = L.off(sizeof(int) * (size_t)c.tile_cap);
+        o_skb = L.off(sizeof(float) * (size_t)TC_SK_MAX_CTAS * 256 * 128);
     }
     if (base) {
         c.d_fn = (Fn*)(base + o_fn);
@@ -220,6 +224,9 @@ size_t carve(Ctx& c, char* base) {
             c.d_systab = (TcSys*)(base + o_systab);
             c.d_maps = (CUtensorMap*)(base + o_maps);
             c.d_tiles = (TcTile*)(base + o_tiles);
+            c.d_cstart = (int*)(base + o_cst);
+            c.d_skflag = (int*)(base + o_skf);
+            c.d_skbuf = (float*)(base + o_skb);
         }
     }
     return L.total;
@@ -420,7 +427,7 @@ void dm_prepare(Ctx& c, const double* F, cudaStream_t s, Timer* tm, int t0) {
 int tc_pass2_tuned(TcBatch& b, int total_k, int Lmax, cudaStream_t s) {
     int l = 2;
     TcCfg cand[8];
-    const int nc = tc_candidates(cand);
+    const int nc = tc_candidates(b, cand);
     const int per = 2, rounds = 2;
     if (tc_needs_tuning(b, total_k) && Lmax - 2 >= nc * per * rounds + 8) {
         float best_ms[8];
@@ -624,7 +631,7 @@ void fork_systems(std::vector<Ctx*>& cs, cudaStream_t s, F&& body) {
 long long batch_key(const TcBatch& b) {
     long long k = (long long)b.ntiles[0] * 128 + b.nsys;
     k = k * 4 + (b.cfg.bk == 64) + 2 * (b.cfg.bn == 128);
-    return k * 4 + b.cfg.persist;
+    return (((k * 4 + b.cfg.persist) * 2 + b.cfg.streamk) * 65 + b.cfg.pf) * 2 + b.cfg.epf;
 }
 
 // run a launch sequence through a CUDA graph cached in `lead` under (slot,

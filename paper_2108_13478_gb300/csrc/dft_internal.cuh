@@ -44,6 +44,7 @@ struct TcTile {
     int sys, i, j, idx;      // system, row tile, column tile, index within the system
 };
 constexpr int TC_MAX_SYS = 64;
+constexpr int TC_SK_MAX_CTAS = 256;   // stream-K grid bound (one 128 KB partial-sum slot per CTA)
 constexpr int TC_MAPS_PER_SYS = 16;
 
 // launch configuration of the tensor-core step (chosen by the autotuner)
@@ -51,6 +52,9 @@ struct TcCfg {
     int bk = 32;        // k-block width: 32 or 64 (64 only with 256-wide tiles)
     int persist = 0;    // 0: one CTA per tile; p > 0: p CTAs per SM, strided tile loop
     int bn = 256;       // output tile width: 256 (one CTA per SM) or 128 (two CTAs per SM)
+    int streamk = 0;    // 1: cooperative grid, equal chunk ranges per CTA (256-wide tiles, one system)
+    int pf = 0;         // L2 prefetch distance in k-blocks (0: none)
+    int epf = 0;        // 1: prefetch the epilogue's rows into L2 before the last chunks
 };
 struct Ctx {
     // problem
@@ -122,6 +126,9 @@ struct Ctx {
     CUtensorMap* d_maps = nullptr;
     TcTile* d_tiles = nullptr;
     int tile_cap = 0;
+    int* d_cstart = nullptr;     // stream-K: first chunk of each 256-wide tile [tile_cap + 1]
+    int* d_skflag = nullptr;     // stream-K: partial sums handed over per tile [tile_cap]
+    float* d_skbuf = nullptr;    // stream-K: partial sums, one slot per CTA [TC_SK_MAX_CTAS x 128 x 256]
     int n_c_cur = 0;             // Chebyshev order of the density matrix in progress
     TcCfg tc_cfg;                // launch shape chosen for this system
     double e_bounds[2] = {0, 0}; // its spectral bounds
@@ -228,6 +235,7 @@ struct TcBatch {
     const Ctx* leader = nullptr;
     int nsys = 0;
     int ntiles[2] = {0, 0}, tile_off[2] = {0, 0};   // per tile width (256, 128)
+    long long nchunks = 0;                           // chunks of the 256-wide list (stream-K)
     bool bf = false;
     TcCfg cfg;
 };
@@ -237,7 +245,8 @@ struct TcBatch {
 TcCfg tc_tuned(const TcBatch& b, int total_k);
 bool tc_needs_tuning(const TcBatch& b, int total_k);
 void tc_record(const TcBatch& b, int total_k, TcCfg best, const float* ms, int ncand);
-int tc_candidates(TcCfg* out);
+int tc_candidates(const TcBatch& b, TcCfg* out);   // at most 8
+int tc_streamk_grid(const TcBatch& b);             // 0 where stream-K does not apply
 // fill leader's batch area with the given systems (pass lim/mom_last per system)
 TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const int* mom_last, cudaStream_t s);
 void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s);

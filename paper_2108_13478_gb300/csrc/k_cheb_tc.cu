@@ -108,6 +108,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return true;
 }
 
+// L2 prefetch of one tensor-map box (no shared memory, no completion signal)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(map), "r"(x), "r"(y)
+                 : "memory");
+}
+
+// L2 prefetch of a contiguous range (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
@@ -174,6 +185,21 @@ struct H16<true> {
     static __device__ __forceinline__ T from_d(double x) { return __double2bfloat16(x); }
 };
 
+// the 16 bits of a split part, and back
+template <class T>
+__device__ __forceinline__ uint32_t bits16(T x) {
+    unsigned short u;
+    memcpy(&u, &x, 2);
+    return u;
+}
+template <class T>
+__device__ __forceinline__ T from_bits16(uint32_t u) {
+    const unsigned short v = (unsigned short)u;
+    T x;
+    memcpy(&x, &v, 2);
+    return x;
+}
+
 template <int BS>
 __device__ double block_sum(double v) {
     __shared__ double red[BS / 32];
@@ -216,8 +242,63 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 template <int N>
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
 
-// Persistent multi-system step.  Each CTA walks the tile list with stride
-// gridDim.x; a tile of system s is active when l < sys[s].lim.  Pipeline
+// The pieces of work of one CTA.  Tile mode: whole tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Stream-K mode (one system, cooperative grid):
+// the tiles' chunks (256 of K each) form one sequence, cs[t] being the first
+// chunk of tile t, and CTA c takes chunks [c C / G, (c + 1) C / G), so every
+// CTA gets the same number of chunks whatever the tile count.  A piece is the
+// chunk range [q0, q1) of one tile.
+struct Cursor {
+    long long pos, hi;
+    int t, stride, ntiles;
+    const int* cs;
+    bool sk;
+    __device__ void init(bool stream_k, const int* cstart, long long nchunks, int ntiles_) {
+        sk = stream_k;
+        cs = cstart;
+        ntiles = ntiles_;
+        stride = gridDim.x;
+        if (sk) {
+            pos = (long long)blockIdx.x * nchunks / gridDim.x;
+            hi = (long long)(blockIdx.x + 1) * nchunks / gridDim.x;
+            int a = 0, b = ntiles;   // last tile with cs[t] <= pos
+            while (b - a > 1) {
+                int m = (a + b) >> 1;
+                if (cs[m] <= pos) a = m;
+                else b = m;
+            }
+            t = a;
+        } else {
+            t = blockIdx.x;
+            pos = hi = 0;
+        }
+    }
+    __device__ bool valid() const { return sk ? pos < hi : t < ntiles; }
+    __device__ int q0() const { return sk ? (int)(pos - cs[t]) : 0; }
+    __device__ int q1(int nchunk) const { return sk ? (int)(min(hi, (long long)cs[t + 1]) - cs[t]) : nchunk; }
+    __device__ void next() {
+        if (sk) {
+            pos = min(hi, (long long)cs[t + 1]);
+            ++t;
+        } else {
+            t += stride;
+        }
+    }
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Persistent multi-system step.  Each CTA walks its pieces (see Cursor); a
+// tile of system s is active when l < sys[s].lim.  In stream-K mode a tile
+// cut between CTAs is finished by the CTA holding its chunk 0 (the owner,
+// which reaches it last, at the end of its range): the others write their
+// FP32 partial sums to `skbuf` (one 128 KB slot per CTA; a CTA contributes at
+// most once, with its first piece) and count up `skflag[t]`; the owner waits
+// for the count (bounded), adds the partials in CTA order and resets it.  Pipeline
 // phases (stage ring, chunk accumulators) run on across tiles, so the MMA
 // warp starts the next tile's first two chunks while the epilogue warps
 // finish the previous tile.
@@ -226,12 +307,15 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                                                               const CUtensorMap* __restrict__ maps,
                                                               const TcTile* __restrict__ tiles, int ntiles, int l,
                                                               int cur, int mode, double* __restrict__ part,
-                                                              int* __restrict__ flags) {
+                                                              int* __restrict__ flags, const int* __restrict__ cstart,
+                                                              long long nchunks, float* __restrict__ skbuf,
+                                                              int* __restrict__ skflag, int pf, int epf) {
     using T = typename H16<BF>::T;
     using C = Cfg<BKV, BNV>;
     constexpr int BK = C::BK, BN = C::BN, STAGES = C::STAGES, GK = C::GK, STAGE_BYTES = C::STAGE_BYTES;
     constexpr int A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES, NEPI = C::NEPI, TMEM_COLS = C::TMEM_COLS;
     constexpr int V = BN == 128 ? 1 : 0;   // tile-width variant (partial-sum slots)
+    const bool sk = cstart != nullptr;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -239,9 +323,14 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
     uint64_t* accfull = empty + STAGES;
     uint64_t* accempty = accfull + 2;
     uint64_t* drain = accempty + 2;
-    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    uint64_t* epi_done = drain + 1;   // epilogue finished with the ring (staged sums)
+    uint32_t* tmem_slot = (uint32_t*)(epi_done + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    double* red = (double*)(smem + STAGES * STAGE_BYTES + 128);   // 2 x 8 doubles
+    double* red = (double*)(smem + STAGES * STAGE_BYTES + 128);   // 2 x 8 moment partials + 1 flag
+    // staged FP32 sums of a finished tile, over the operand ring
+    constexpr int RS = BN + 1;
+    static_assert(BM * RS * 4 <= STAGES * STAGE_BYTES, "staged tile does not fit the ring");
+    float* Rs = (float*)smem;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool do_rho = (mode & 1) != 0, do_mom = (mode & 2) != 0;
@@ -256,6 +345,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             mbar_init(&accempty[a], NEPI);
         }
         mbar_init(drain, 1);
+        mbar_init(epi_done, NEPI);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -280,18 +370,36 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
         if (lane == 0) {
             // producer: four operand tiles per k-block into the stage ring
             long long g = 0;   // k-blocks issued by this CTA
-            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-                const TcTile tl = tiles[t];
+            int nfin = 0;      // pieces whose epilogue runs here (over the ring)
+            Cursor cu;
+            cu.init(sk, cstart, nchunks, ntiles);
+            for (; cu.valid() && !*abort_flag; cu.next()) {
+                const TcTile tl = tiles[cu.t];
                 const TcSys& S = sys[tl.sys];
                 if (l >= S.lim) continue;
+                if (nfin > 0 && !mbar_wait(epi_done, (uint32_t)((nfin - 1) & 1))) {
+                    // the previous tile's epilogue still holds the ring
+                    *abort_flag = 1;
+                    break;
+                }
                 const CUtensorMap* mp = maps + TC_MAPS_PER_SYS * tl.sys + (BK == 64 ? 6 : 0);
                 // X operand maps: 256-row boxes beside the H maps, or the 128-row set
                 const CUtensorMap* mb = BN == 128 ? maps + TC_MAPS_PER_SYS * tl.sys + 12 : mp + 2;
                 const int m0 = tl.i * BM, n0 = tl.j * BN;
                 const int nk = (S.K + BK - 1) / BK;
-                for (int kb = 0; kb < nk; ++kb, ++g) {
+                const int nchunk = (nk + GK - 1) / GK;
+                const int kend = min(nk, cu.q1(nchunk) * GK);
+                for (int kb = cu.q0() * GK; kb < kend; ++kb, ++g) {
                     const int s = (int)(g % STAGES);
                     const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+                    if (pf > 0 && kb + pf < kend) {
+                        // pull the k-block pf ahead into L2 while the ring is full
+                        const int xp = (kb + pf) * BK;
+                        tma_prefetch_2d(mp + 0, xp, m0);
+                        tma_prefetch_2d(mp + 1, xp, m0);
+                        tma_prefetch_2d(mb + 2 * cur, xp, n0);
+                        tma_prefetch_2d(mb + 1 + 2 * cur, xp, n0);
+                    }
                     if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
                         *abort_flag = 1;
                         break;
@@ -302,6 +410,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                     tma_load_2d(sBh(s), mb + 2 * cur, kb * BK, n0, &full[s]);
                     tma_load_2d(sBl(s), mb + 1 + 2 * cur, kb * BK, n0, &full[s]);
                 }
+                if (!sk || cu.q0() == 0) ++nfin;
             }
             if (*abort_flag) {
                 // the last load issued into each stage must land before exit
@@ -316,14 +425,17 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             const uint32_t idesc = (1u << 4) | ((BF ? 1u : 0u) << 7) | ((BF ? 1u : 0u) << 10) |
                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
             long long g = 0, qg = 0;
-            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-                const TcTile tl = tiles[t];
+            Cursor cu;
+            cu.init(sk, cstart, nchunks, ntiles);
+            for (; cu.valid() && !*abort_flag; cu.next()) {
+                const TcTile tl = tiles[cu.t];
                 const TcSys& S = sys[tl.sys];
                 if (l >= S.lim) continue;
                 const int nk = (S.K + BK - 1) / BK;
                 const int nchunk = (nk + GK - 1) / GK;
-                int kb = 0;
-                for (int q = 0; q < nchunk; ++q, ++qg) {
+                const int qa = cu.q0(), qb = cu.q1(nchunk);
+                int kb = qa * GK;
+                for (int q = qa; q < qb; ++q, ++qg) {
                     const int a = (int)(qg & 1);
                     if (*abort_flag || !mbar_wait(&accempty[a], (uint32_t)(((qg >> 1) & 1) ^ 1))) {
                         *abort_flag = 1;
@@ -371,16 +483,34 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
         long long qg = 0;
         bool ok = true;
         bool bad = false;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const TcTile tl = tiles[t];
+        const int et = threadIdx.x - 64;   // epilogue thread index
+        Cursor cu;
+        cu.init(sk, cstart, nchunks, ntiles);
+        for (; cu.valid() && ok; cu.next()) {
+            const TcTile tl = tiles[cu.t];
             const TcSys& S = sys[tl.sys];
             if (l >= S.lim) continue;
             const int nchunk = ((S.K + BK - 1) / BK + GK - 1) / GK;
+            const int qa = cu.q0(), qb = cu.q1(nchunk);
             const int m0 = tl.i * BM, n0 = tl.j * BN;
             float R[CPT];
 #pragma unroll
             for (int i = 0; i < CPT; ++i) R[i] = 0.0f;
-            for (int q = 0; q < nchunk; ++q, ++qg) {
+            for (int q = qa; q < qb; ++q, ++qg) {
+                if (epf && q == max(qa, qb - 2) && (!sk || qa == 0)) {
+                    // the epilogue's rows into L2 while the last chunks run
+                    const int rr = m0 + 32 * quad + lane;
+                    if (rr < S.K) {
+                        const size_t e = (size_t)rr * S.Kp + n0 + half * CPT;
+                        bulk_prefetch_l2((const T*)S.x16[2 * (1 - cur)] + e, CPT * sizeof(T));
+                        bulk_prefetch_l2((const T*)S.x16[2 * (1 - cur) + 1] + e, CPT * sizeof(T));
+                        if (do_rho) bulk_prefetch_l2(S.rho + e, CPT * sizeof(double));
+                        if (do_mom) {
+                            bulk_prefetch_l2((const T*)S.x16[2 * cur] + e, CPT * sizeof(T));
+                            bulk_prefetch_l2((const T*)S.x16[2 * cur + 1] + e, CPT * sizeof(T));
+                        }
+                    }
+                }
                 const int a = (int)(qg & 1);
                 const bool got = mbar_wait(&accfull[a], (uint32_t)((qg >> 1) & 1));
                 ok = __all_sync(0xffffffffu, got && !*abort_flag);
@@ -398,7 +528,71 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 mbar_arrive(&accempty[a]);
             }
             if (!ok) break;
-            const int r = m0 + 32 * quad + lane;
+            if (sk && qa > 0) {
+                // not the owner: hand the partial sums over and go on
+                float4* dst = (float4*)(skbuf + ((size_t)blockIdx.x * NEPI + et) * CPT);
+#pragma unroll
+                for (int i = 0; i < CPT / 4; ++i) dst[i] = make_float4(R[4 * i], R[4 * i + 1], R[4 * i + 2], R[4 * i + 3]);
+                __threadfence();
+                epi_sync<NEPI>();
+                if (et == 0) {
+                    __threadfence();
+                    atomicAdd(&skflag[cu.t], 1);
+                }
+                continue;
+            }
+            if (sk && qb < nchunk) {
+                // owner of a tile that later CTAs finish: CTAs blockIdx.x + 1 ...
+                // whose ranges start inside it
+                const long long tend = cstart[cu.t + 1];
+                int nc = 0;
+                while (blockIdx.x + 1 + nc < gridDim.x &&
+                       (long long)(blockIdx.x + 1 + nc) * nchunks / gridDim.x < tend)
+                    ++nc;
+                if (et == 0) {
+                    bool arrived = ld_acquire(&skflag[cu.t]) >= nc;
+                    if (!arrived) {
+                        const unsigned long long t0 = globaltimer();
+                        while (!(arrived = ld_acquire(&skflag[cu.t]) >= nc)) {
+                            if (globaltimer() - t0 > WAIT_NS) break;
+                        }
+                    }
+                    red[16] = arrived ? 1.0 : 0.0;
+                    skflag[cu.t] = 0;
+                    __threadfence();
+                }
+                epi_sync<NEPI>();
+                ok = red[16] != 0.0;
+                epi_sync<NEPI>();
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
+                for (int k = 1; k <= nc; ++k) {
+                    const float4* src = (const float4*)(skbuf + ((size_t)(blockIdx.x + k) * NEPI + et) * CPT);
+#pragma unroll
+                    for (int i = 0; i < CPT / 4; ++i) {
+                        const float4 v4 = __ldcg(src + i);
+                        R[4 * i] += v4.x;
+                        R[4 * i + 1] += v4.y;
+                        R[4 * i + 2] += v4.z;
+                        R[4 * i + 3] += v4.w;
+                    }
+                }
+            }
+            // ---- fused update from shared memory ----
+            // The operand ring is idle now (every MMA of this tile has completed
+            // and the producer waits for epi_done before it loads again), so the
+            // tile's FP32 sums move there (row stride BN + 1: conflict-free for
+            // both the lane-per-row writes here and the lane-per-column reads
+            // below) and the registers are free for many loads in flight.
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            {
+                float* dst = Rs + (32 * quad + lane) * RS + half * CPT;
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) dst[j] = R[j];
+            }
+            epi_sync<NEPI>();
             const double al = do_rho ? S.coef[l] : 0.0;
             float snn_h = 0.0f, snn_l = 0.0f, snc_h = 0.0f, snc_l = 0.0f;
             T* xph = (T*)S.x16[2 * (1 - cur)];
@@ -408,100 +602,75 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             double* rho = S.rho;
             const int K = S.K;
             const size_t Kp = (size_t)S.Kp;
-            if (r < K) {
+            const int ew = et >> 5;   // epilogue warp
+            // rows: one warp per row, lane j takes columns j, j + 32, ...: every
+            // access of a warp is one contiguous run of the row.  X_{l+1} (hi, lo)
+            // goes back to shared memory, packed, for the mirror pass.
+            constexpr int NC = BN / 32;
+            for (int lr = ew; lr < BM; lr += NEPI / 32) {
+                const int r = m0 + lr;
+                if (r >= K) break;
                 const size_t rowoff = (size_t)r * Kp;
+                T ph[NC], pl[NC], ch[NC], cl[NC];
+                double rq[NC];
 #pragma unroll
-                for (int cc = 0; cc < CPT / 32; ++cc) {
-                    const int cb = n0 + half * CPT + cc * 32;
-                    if (cb + 31 < r || cb >= K) continue;
-                    const bool vec = (cb >= r) && (cb + 31 < K);
-                    if (vec) {
-                        // the whole 32-column run is upper and inside: 16-byte accesses
-                        // along the row, eight columns at a time
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const size_t e0 = rowoff + cb + 8 * i;
-                            const uint4 ph4 = *(const uint4*)(xph + e0);
-                            const uint4 pl4 = *(const uint4*)(xpl + e0);
-                            const T* phv = (const T*)&ph4;
-                            const T* plv = (const T*)&pl4;
-                            uint4 oh4, ol4;
-                            T* ohv = (T*)&oh4;
-                            T* olv = (T*)&ol4;
-                            float xn[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const float xp = H16<BF>::to_f(phv[j]) + H16<BF>::to_f(plv[j]);
-                                xn[j] = 2.0f * R[cc * 32 + 8 * i + j] - xp;
-                                const T h = H16<BF>::from_f(xn[j]);
-                                ohv[j] = h;
-                                olv[j] = H16<BF>::from_f(xn[j] - H16<BF>::to_f(h));
-                                bad |= !(fabsf(xn[j]) <= 4.0f);
-                            }
-                            *(uint4*)(xph + e0) = oh4;
-                            *(uint4*)(xpl + e0) = ol4;
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const int c = cb + 8 * i + j;
-                                if (c != r) {
-                                    const size_t et = (size_t)c * Kp + r;
-                                    xph[et] = ohv[j];
-                                    xpl[et] = olv[j];
-                                }
-                            }
-                            if (do_rho) {
-                                double2* rp = (double2*)(rho + e0);
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) {
-                                    double2 q2 = rp[k];
-                                    q2.x = fma(al, (double)xn[2 * k], q2.x);
-                                    q2.y = fma(al, (double)xn[2 * k + 1], q2.y);
-                                    rp[k] = q2;
-                                }
-                            }
-                            if (do_mom) {
-                                const uint4 ch4 = *(const uint4*)(xch + e0);
-                                const uint4 cl4 = *(const uint4*)(xcl + e0);
-                                const T* chv = (const T*)&ch4;
-                                const T* clv = (const T*)&cl4;
-#pragma unroll
-                                for (int j = 0; j < 8; ++j) {
-                                    const float wx = (cb + 8 * i + j == r) ? xn[j] : 2.0f * xn[j];
-                                    const float xc = H16<BF>::to_f(chv[j]) + H16<BF>::to_f(clv[j]);
-                                    acc_prod(snn_h, snn_l, wx, xn[j]);
-                                    acc_prod(snc_h, snc_l, wx, xc);
-                                }
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int c = cb + j;
-                            if (c < r || c >= K) continue;
-                            const size_t e = rowoff + c;
-                            const float xp = H16<BF>::to_f(xph[e]) + H16<BF>::to_f(xpl[e]);
-                            const float xn = 2.0f * R[cc * 32 + j] - xp;
-                            const T h = H16<BF>::from_f(xn);
-                            const T lo = H16<BF>::from_f(xn - H16<BF>::to_f(h));
-                            xph[e] = h;
-                            xpl[e] = lo;
-                            if (c != r) {
-                                const size_t et = (size_t)c * Kp + r;
-                                xph[et] = h;
-                                xpl[et] = lo;
-                            }
-                            if (do_rho) rho[e] = fma(al, (double)xn, rho[e]);
-                            if (do_mom) {
-                                const float wx = (c == r) ? xn : 2.0f * xn;
-                                const float xc = H16<BF>::to_f(xch[e]) + H16<BF>::to_f(xcl[e]);
-                                acc_prod(snn_h, snn_l, wx, xn);
-                                acc_prod(snc_h, snc_l, wx, xc);
-                            }
-                            bad |= !(fabsf(xn) <= 4.0f);
+                for (int k = 0; k < NC; ++k) {
+                    const int c = n0 + lane + 32 * k;
+                    if (c >= r && c < K) {
+                        ph[k] = xph[rowoff + c];
+                        pl[k] = xpl[rowoff + c];
+                        if (do_rho) rq[k] = rho[rowoff + c];
+                        if (do_mom) {
+                            ch[k] = xch[rowoff + c];
+                            cl[k] = xcl[rowoff + c];
                         }
                     }
                 }
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    const int c = n0 + lane + 32 * k;
+                    if (c >= r && c < K) {
+                        float* rs = Rs + lr * RS + lane + 32 * k;
+                        const float xp = H16<BF>::to_f(ph[k]) + H16<BF>::to_f(pl[k]);
+                        const float xn = 2.0f * *rs - xp;
+                        const T h = H16<BF>::from_f(xn);
+                        const T lo = H16<BF>::from_f(xn - H16<BF>::to_f(h));
+                        xph[rowoff + c] = h;
+                        xpl[rowoff + c] = lo;
+                        *(uint32_t*)rs = bits16(h) | (bits16(lo) << 16);
+                        if (do_rho) rho[rowoff + c] = fma(al, (double)xn, rq[k]);
+                        if (do_mom) {
+                            const float wx = (c == r) ? xn : 2.0f * xn;
+                            const float xc = H16<BF>::to_f(ch[k]) + H16<BF>::to_f(cl[k]);
+                            acc_prod(snn_h, snn_l, wx, xn);
+                            acc_prod(snc_h, snc_l, wx, xc);
+                        }
+                        bad |= !(fabsf(xn) <= 4.0f);
+                    }
+                }
             }
+            epi_sync<NEPI>();
+            // mirror: column c of the tile becomes row c below the diagonal;
+            // lane j takes tile rows j, j + 32, ... (contiguous in the row)
+            for (int lc = ew; lc < BN; lc += NEPI / 32) {
+                const int c = n0 + lc;
+                if (c >= K) break;
+                const size_t rowoff = (size_t)c * Kp;
+#pragma unroll
+                for (int k = 0; k < BM / 32; ++k) {
+                    const int lr = lane + 32 * k;
+                    const int r = m0 + lr;
+                    if (r < c && r < K) {
+                        const uint32_t v = *(const uint32_t*)(Rs + lr * RS + lc);
+                        xph[rowoff + r] = from_bits16<T>(v & 0xffffu);
+                        xpl[rowoff + r] = from_bits16<T>(v >> 16);
+                    }
+                }
+            }
+            // hand the ring back to the producer (generic accesses before its
+            // next asynchronous writes)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(epi_done);
             if (do_mom) {
                 double s_nn = (double)snn_h + (double)snn_l, s_nc = (double)snc_h + (double)snc_l;
                 for (int o = 16; o > 0; o >>= 1) {
@@ -731,6 +900,24 @@ int num_sms() {
 }
 }  // namespace
 
+// Stream-K grid of a batch, or 0 where the mode does not apply.  It needs one
+// system (every tile active in every step) and at least two chunks per CTA
+// (every CTA range non-empty); the grid is one CTA per SM, at most
+// TC_SK_MAX_CTAS (partial-sum slots), all resident together.
+int tc_streamk_grid(const TcBatch& b) {
+    static int occ = -1;
+    if (occ < 0) {
+        int a = 0, c = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, tc::k_cheb_step_tc<false, 32, 256>, tc::Cfg<32, 256>::NTHREADS,
+                                                      tc::Cfg<32, 256>::SMEM_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, tc::k_cheb_step_tc<false, 64, 256>, tc::Cfg<64, 256>::NTHREADS,
+                                                      tc::Cfg<64, 256>::SMEM_BYTES);
+        occ = std::min(a, c);
+    }
+    if (b.nsys != 1 || occ < 1 || b.nchunks < 2) return 0;
+    return (int)std::min<long long>({(long long)num_sms(), (long long)TC_SK_MAX_CTAS, b.nchunks / 2});
+}
+
 TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const int* mom_last, cudaStream_t s) {
     if (nsys < 1 || nsys > TC_MAX_SYS) throw Error(DFT_EINVAL, "batch size out of range");
     std::vector<TcSys> tab(nsys);
@@ -770,12 +957,17 @@ TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const i
         b.ntiles[v] = (int)tiles.size() - b.tile_off[v];
     }
     if ((int)tiles.size() > leader.tile_cap) throw Error(DFT_ENOMEM, "batch tile list exceeds the leader's capacity");
+    // chunk offsets of the 256-wide list (stream-K); a chunk is 256 of K
+    std::vector<int> cst(b.ntiles[0] + 1, 0);
+    for (int t = 0; t < b.ntiles[0]; ++t) cst[t + 1] = cst[t] + (sys[tiles[t].sys]->K + 255) / 256;
+    b.nchunks = cst.back();
     if ((long long)2 * part_off > leader.part_cap) throw Error(DFT_ENOMEM, "batch partial sums exceed the leader's capacity");
     DFT_CUDA_CHECK(cudaMemcpyAsync(leader.d_systab, tab.data(), sizeof(TcSys) * nsys, cudaMemcpyHostToDevice, s));
     DFT_CUDA_CHECK(cudaMemcpyAsync(leader.d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
                                    cudaMemcpyHostToDevice, s));
     DFT_CUDA_CHECK(cudaMemcpyAsync(leader.d_tiles, tiles.data(), sizeof(TcTile) * tiles.size(),
                                    cudaMemcpyHostToDevice, s));
+    DFT_CUDA_CHECK(cudaMemcpyAsync(leader.d_cstart, cst.data(), sizeof(int) * cst.size(), cudaMemcpyHostToDevice, s));
     DFT_CUDA_CHECK(cudaStreamSynchronize(s));   // host staging buffers go out of scope
     b.leader = &leader;
     b.nsys = nsys;
@@ -784,6 +976,9 @@ TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const i
 }
 
 void tc_set_limits(const TcBatch& b, Ctx* const* sys, const int* lim, const int* mom_last, cudaStream_t s) {
+    // stream-K hand-over counters start every pass at zero
+    if (b.ntiles[0] > 0)
+        DFT_CUDA_CHECK(cudaMemsetAsync(b.leader->d_skflag, 0, sizeof(int) * (size_t)b.ntiles[0], s));
     for (int q = 0; q < b.nsys; ++q) {
         int v[2] = {lim[q], mom_last[q]};
         DFT_CUDA_CHECK(cudaMemcpyAsync((char*)(b.leader->d_systab + q) + offsetof(TcSys, lim), &v[0], sizeof(int),
@@ -806,11 +1001,43 @@ void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s) {
     const int nt = b.ntiles[v];
     if (nt == 0) return;
     const TcTile* tiles = L.d_tiles + b.tile_off[v];
+    const int skg = b.cfg.streamk ? tc_streamk_grid(b) : 0;
+    if (skg > 0) {
+        // all CTAs resident at once (cooperative launch): owners wait for
+        // partial sums of CTAs with higher indices
+        const int grid = skg;
+        auto go = [&](auto kern, auto cfg) {
+            using C = decltype(cfg);
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3(grid);
+            lc.blockDim = dim3(C::NTHREADS);
+            lc.dynamicSmemBytes = C::SMEM_BYTES;
+            lc.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeCooperative;
+            at[0].val.cooperative = 1;
+            lc.attrs = at;
+            lc.numAttrs = 1;
+            DFT_CUDA_CHECK(cudaLaunchKernelEx(&lc, kern, (const TcSys*)L.d_systab, (const CUtensorMap*)L.d_maps,
+                                              tiles, nt, l, cur, mode, L.d_part, L.d_flags,
+                                              (const int*)L.d_cstart, b.nchunks, L.d_skbuf, L.d_skflag, b.cfg.pf,
+                                              b.cfg.epf));
+        };
+        if (b.cfg.bk == 64) {
+            if (b.bf) go(tc::k_cheb_step_tc<true, 64, 256>, tc::Cfg<64, 256>{});
+            else go(tc::k_cheb_step_tc<false, 64, 256>, tc::Cfg<64, 256>{});
+        } else {
+            if (b.bf) go(tc::k_cheb_step_tc<true, 32, 256>, tc::Cfg<32, 256>{});
+            else go(tc::k_cheb_step_tc<false, 32, 256>, tc::Cfg<32, 256>{});
+        }
+        check_launch("cheb_step_tc");
+        return;
+    }
     int grid = b.cfg.persist > 0 ? std::min(nt, b.cfg.persist * num_sms()) : nt;
     auto go = [&](auto kern, auto cfg) {
         using C = decltype(cfg);
         kern<<<grid, C::NTHREADS, C::SMEM_BYTES, s>>>(L.d_systab, L.d_maps, tiles, nt, l, cur, mode, L.d_part,
-                                                      L.d_flags);
+                                                      L.d_flags, nullptr, 0LL, nullptr, nullptr, b.cfg.pf, b.cfg.epf);
     };
     if (v == 1) {
         if (b.bf) go(tc::k_cheb_step_tc<true, 32, 128>, tc::Cfg<32, 128>{});
@@ -879,8 +1106,8 @@ std::string tune_key(const TcBatch& b, int total_k) {
     return o.str();
 }
 
-// cache file: one entry per line, `"key": [bk, persist, bn, ms...],` inside
-// braces (entries without bn are 256-wide)
+// cache file: one entry per line, `"key": [bk, persist, bn, streamk, ms...],`
+// inside braces (entries without bn are 256-wide, without streamk tile mode)
 void tune_load() {
     if (g_tune_loaded) return;
     g_tune_loaded = true;
@@ -892,10 +1119,11 @@ void tune_load() {
         size_t q0 = line.find('"'), q1 = line.find('"', q0 + 1), lb = line.find('[', q1 + 1);
         if (q0 == std::string::npos || q1 == std::string::npos || lb == std::string::npos) continue;
         TcCfg c;
-        int n = std::sscanf(line.c_str() + lb, "[%d, %d, %d", &c.bk, &c.persist, &c.bn);
+        int n = std::sscanf(line.c_str() + lb, "[%d, %d, %d, %d", &c.bk, &c.persist, &c.bn, &c.streamk);
         if (n == 2) c.bn = 256;
+        if (n < 4) c.streamk = 0;
         if (n >= 2 && (c.bk == 32 || c.bk == 64) && c.persist >= 0 && c.persist <= 2 &&
-            (c.bn == 256 || (c.bn == 128 && c.bk == 32)))
+            (c.bn == 256 || (c.bn == 128 && c.bk == 32)) && (c.streamk == 0 || (c.streamk == 1 && c.bn == 256)))
             g_tuned[line.substr(q0 + 1, q1 - q0 - 1)] = c;
     }
 }
@@ -908,7 +1136,8 @@ void tune_save() {
     size_t i = 0;
     for (auto& kv : g_tuned)
     {
-        f << "  \"" << kv.first << "\": [" << kv.second.bk << ", " << kv.second.persist << ", " << kv.second.bn;
+        f << "  \"" << kv.first << "\": [" << kv.second.bk << ", " << kv.second.persist << ", " << kv.second.bn << ", "
+          << kv.second.streamk;
         auto it = g_tune_ms.find(kv.first);
         if (it != g_tune_ms.end())
             for (float m : it->second) f << ", " << m;
@@ -918,10 +1147,13 @@ void tune_save() {
 }
 }  // namespace
 
-int tc_candidates(TcCfg* out) {
-    const TcCfg c[6] = {{32, 0, 256}, {64, 0, 256}, {32, 1, 256}, {64, 1, 256}, {32, 0, 128}, {32, 2, 128}};
-    for (int i = 0; i < 6; ++i) out[i] = c[i];
-    return 6;
+int tc_candidates(const TcBatch& b, TcCfg* out) {
+    const TcCfg c[8] = {{32, 0, 256, 0}, {64, 0, 256, 0}, {32, 1, 256, 0}, {64, 1, 256, 0},
+                        {32, 0, 128, 0}, {32, 2, 128, 0}, {32, 0, 256, 1}, {64, 0, 256, 1}};
+    // stream-K only where it applies and where it can balance a ragged last wave
+    const int n = (tc_streamk_grid(b) == std::min(num_sms(), TC_SK_MAX_CTAS)) ? 8 : 6;
+    for (int i = 0; i < n; ++i) out[i] = c[i];
+    return n;
 }
 
 // launch shape forced through DFT_TC_SHAPE="bk,persist,bn"
@@ -929,9 +1161,14 @@ static bool forced_shape(TcCfg& c) {
     const char* e = std::getenv("DFT_TC_SHAPE");
     if (!e) return false;
     TcCfg f;
-    if (std::sscanf(e, "%d,%d,%d", &f.bk, &f.persist, &f.bn) != 3) return false;
+    int n = std::sscanf(e, "%d,%d,%d,%d,%d,%d", &f.bk, &f.persist, &f.bn, &f.streamk, &f.pf, &f.epf);
+    if (n < 3) return false;
+    if (n == 3) f.streamk = 0;
+    if (n <= 4) f.pf = 0;
+    if (n <= 5) f.epf = TcCfg{}.epf;
+    if (f.pf < 0 || f.pf > 64 || f.epf < 0 || f.epf > 1) return false;
     if (!((f.bk == 32 || f.bk == 64) && f.persist >= 0 && f.persist <= 2 &&
-          (f.bn == 256 || (f.bn == 128 && f.bk == 32))))
+          (f.bn == 256 || (f.bn == 128 && f.bk == 32)) && (f.streamk == 0 || (f.streamk == 1 && f.bn == 256))))
         return false;
     c = f;
     return true;

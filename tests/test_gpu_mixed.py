@@ -85,14 +85,17 @@ def test_mixed_grid_kernels_fp32():
     ctx.close()
 
 
-SHAPES = ["32,0,256", "64,0,256", "32,1,256", "64,1,256", "32,0,128", "32,2,128"]
+SHAPES = ["32,0,256", "64,0,256", "32,1,256", "64,1,256", "32,0,128", "32,2,128", "32,0,256,1", "64,0,256,1"]
 
 
 @pytest.mark.parametrize("name", ["tiny37", "cluster64"])
 def test_mixed_launch_shapes(name, monkeypatch):
     """Every tensor-core launch shape (k-block width, persistent grid, 256- or
-    128-wide tiles with one or two CTAs per SM) gives the oracle's density
-    matrix; K = 370 leaves a ragged row and column tile, K = 640 a padded one."""
+    128-wide tiles with one or two CTAs per SM, stream-K chunk ranges) gives
+    the oracle's density matrix; K = 370 leaves a ragged row and column tile,
+    K = 640 a padded one.  Stream-K runs 5 CTAs on 10 chunks at K = 370 (no
+    tile cut) and 16 CTAs on 33 chunks at K = 640, where most tiles are cut
+    between two CTAs and finished from handed-over partial sums."""
     s, st, F, lo, hi, n_c, ref = case(name)
     Ps = []
     for shape in SHAPES:
