@@ -167,6 +167,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // 16-bit storage type of the split operands
 template <bool BF>
 struct H16;
@@ -236,6 +246,9 @@ __device__ __forceinline__ void acc_prod(float& hi, float& lo, float x, float y)
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+
+// column swizzle of the staged tile's row lr (a multiple of 4 below 32)
+__device__ __forceinline__ int rs_swz(int lr) { return ((lr ^ (lr >> 2)) & 7) << 2; }
 
 // barrier among the N epilogue threads only (the producer and MMA warps keep
 // running their own loops)
@@ -328,8 +341,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     double* red = (double*)(smem + STAGES * STAGE_BYTES + 128);   // 2 x 8 moment partials + 1 flag
     // staged FP32 sums of a finished tile, over the operand ring
-    constexpr int RS = BN + 1;
-    static_assert(BM * RS * 4 <= STAGES * STAGE_BYTES, "staged tile does not fit the ring");
+    static_assert(BM * BN * 4 <= STAGES * STAGE_BYTES, "staged tile does not fit the ring");
     float* Rs = (float*)smem;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -518,11 +530,11 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 tc_fence_after();
                 // promote the chunk's partial sums: round-to-nearest FP32 adds in registers
 #pragma unroll
-                for (int cc = 0; cc < CPT / 32; ++cc) {
-                    uint32_t v[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * BN + half * CPT + cc * 32), v);
+                for (int cc = 0; cc < CPT / 16; ++cc) {
+                    uint32_t v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * BN + half * CPT + cc * 16), v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) R[cc * 32 + j] += __uint_as_float(v[j]);
+                    for (int j = 0; j < 16; ++j) R[cc * 16 + j] += __uint_as_float(v[j]);
                 }
                 tc_fence_before();
                 mbar_arrive(&accempty[a]);
@@ -583,14 +595,20 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             // ---- fused update from shared memory ----
             // The operand ring is idle now (every MMA of this tile has completed
             // and the producer waits for epi_done before it loads again), so the
-            // tile's FP32 sums move there (row stride BN + 1: conflict-free for
-            // both the lane-per-row writes here and the lane-per-column reads
-            // below) and the registers are free for many loads in flight.
+            // tile's FP32 sums move there and the registers are free for many
+            // loads in flight.  Rs holds element (lr, lc) at lr * BN + (lc ^
+            // rs_swz(lr)): the XOR moves 4-column groups within their 32-column
+            // bank window, so the 16-byte accesses of all three passes below
+            // (lane per row here, lane per 4 columns of one row, lane per 4 rows
+            // of 4 columns in the mirror) are free of bank conflicts.
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             {
-                float* dst = Rs + (32 * quad + lane) * RS + half * CPT;
+                const int lr = 32 * quad + lane;
+                float* rowp = Rs + lr * BN;
+                const int sw = rs_swz(lr);
 #pragma unroll
-                for (int j = 0; j < CPT; ++j) dst[j] = R[j];
+                for (int j = 0; j < CPT; j += 4)
+                    *(float4*)(rowp + ((half * CPT + j) ^ sw)) = make_float4(R[j], R[j + 1], R[j + 2], R[j + 3]);
             }
             epi_sync<NEPI>();
             const double al = do_rho ? S.coef[l] : 0.0;
@@ -603,67 +621,144 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             const int K = S.K;
             const size_t Kp = (size_t)S.Kp;
             const int ew = et >> 5;   // epilogue warp
-            // rows: one warp per row, lane j takes columns j, j + 32, ...: every
-            // access of a warp is one contiguous run of the row.  X_{l+1} (hi, lo)
-            // goes back to shared memory, packed, for the mirror pass.
-            constexpr int NC = BN / 32;
-            for (int lr = ew; lr < BM; lr += NEPI / 32) {
-                const int r = m0 + lr;
-                if (r >= K) break;
-                const size_t rowoff = (size_t)r * Kp;
-                T ph[NC], pl[NC], ch[NC], cl[NC];
-                double rq[NC];
+            constexpr int NW = NEPI / 32;
+            // rows: each warp takes RB consecutive rows at a time; lane j takes
+            // columns 4j .. 4j + 3 of every 128-column group, so one warp access
+            // is a contiguous 256-byte (16-bit pair parts) or 1 KB (rho) run of a
+            // row, and RB * BN / 128 such runs per array are in flight per lane.
+            // Every vector lies inside the Kp x Kp buffers (Kp is a multiple of
+            // 256), so loads are unconditional; stores keep to the upper triangle
+            // c >= r and c < K, per element where a vector crosses either edge.
+            // X_{l+1} (hi, lo) goes back to shared memory, packed, for the mirror.
+            constexpr int RB = 512 / BN, NG = BN / 128;   // 4 (row, group) slots per lane
+            for (int lr0 = RB * ew; lr0 < BM; lr0 += RB * NW) {
+                if (m0 + lr0 >= K) break;
+                uint2 ph[RB][NG], pl[RB][NG], ch[RB][NG], cl[RB][NG];
+                double2 rq[RB][NG][2];
 #pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                    const int c = n0 + lane + 32 * k;
-                    if (c >= r && c < K) {
-                        ph[k] = xph[rowoff + c];
-                        pl[k] = xpl[rowoff + c];
-                        if (do_rho) rq[k] = rho[rowoff + c];
+                for (int u = 0; u < RB; ++u) {
+                    const int r = min(m0 + lr0 + u, K - 1);
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) {
+                        const size_t e = (size_t)r * Kp + n0 + 128 * g + 4 * lane;
+                        ph[u][g] = __ldcs((const uint2*)(xph + e));
+                        pl[u][g] = __ldcs((const uint2*)(xpl + e));
+                        if (do_rho) {
+                            rq[u][g][0] = __ldcs((const double2*)(rho + e));
+                            rq[u][g][1] = __ldcs((const double2*)(rho + e) + 1);
+                        }
                         if (do_mom) {
-                            ch[k] = xch[rowoff + c];
-                            cl[k] = xcl[rowoff + c];
+                            ch[u][g] = *(const uint2*)(xch + e);
+                            cl[u][g] = *(const uint2*)(xcl + e);
                         }
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                    const int c = n0 + lane + 32 * k;
-                    if (c >= r && c < K) {
-                        float* rs = Rs + lr * RS + lane + 32 * k;
-                        const float xp = H16<BF>::to_f(ph[k]) + H16<BF>::to_f(pl[k]);
-                        const float xn = 2.0f * *rs - xp;
-                        const T h = H16<BF>::from_f(xn);
-                        const T lo = H16<BF>::from_f(xn - H16<BF>::to_f(h));
-                        xph[rowoff + c] = h;
-                        xpl[rowoff + c] = lo;
-                        *(uint32_t*)rs = bits16(h) | (bits16(lo) << 16);
-                        if (do_rho) rho[rowoff + c] = fma(al, (double)xn, rq[k]);
-                        if (do_mom) {
-                            const float wx = (c == r) ? xn : 2.0f * xn;
-                            const float xc = H16<BF>::to_f(ch[k]) + H16<BF>::to_f(cl[k]);
-                            acc_prod(snn_h, snn_l, wx, xn);
-                            acc_prod(snc_h, snc_l, wx, xc);
+                for (int u = 0; u < RB; ++u) {
+                    const int lr = lr0 + u;
+                    const int r = m0 + lr;
+                    if (r >= K) break;
+                    const size_t rowoff = (size_t)r * Kp;
+                    const int sw = rs_swz(lr);
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) {
+                        const int lc = 128 * g + 4 * lane;
+                        const int c0 = n0 + lc;
+                        if (c0 + 3 < r || c0 >= K) continue;
+                        const bool full = c0 >= r && c0 + 3 < K;
+                        float* rs = Rs + lr * BN + (lc ^ sw);
+                        const float4 acc = *(const float4*)rs;
+                        const float av[4] = {acc.x, acc.y, acc.z, acc.w};
+                        const uint32_t phw[2] = {ph[u][g].x, ph[u][g].y}, plw[2] = {pl[u][g].x, pl[u][g].y};
+                        const uint32_t chw[2] = {ch[u][g].x, ch[u][g].y}, clw[2] = {cl[u][g].x, cl[u][g].y};
+                        const double rv[4] = {rq[u][g][0].x, rq[u][g][0].y, rq[u][g][1].x, rq[u][g][1].y};
+                        uint32_t hb[4], lb[4];
+                        double rn[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int c = c0 + i;
+                            const int sh = 16 * (i & 1);
+                            const float xp = H16<BF>::to_f(from_bits16<T>(phw[i >> 1] >> sh)) +
+                                             H16<BF>::to_f(from_bits16<T>(plw[i >> 1] >> sh));
+                            const float xn = 2.0f * av[i] - xp;
+                            const T h = H16<BF>::from_f(xn);
+                            const T lo = H16<BF>::from_f(xn - H16<BF>::to_f(h));
+                            hb[i] = bits16(h);
+                            lb[i] = bits16(lo);
+                            rn[i] = do_rho ? fma(al, (double)xn, rv[i]) : 0.0;
+                            const bool ok_i = c >= r && c < K;
+                            if (ok_i) {
+                                if (do_mom) {
+                                    const float wx = (c == r) ? xn : 2.0f * xn;
+                                    const float xc = H16<BF>::to_f(from_bits16<T>(chw[i >> 1] >> sh)) +
+                                                     H16<BF>::to_f(from_bits16<T>(clw[i >> 1] >> sh));
+                                    acc_prod(snn_h, snn_l, wx, xn);
+                                    acc_prod(snc_h, snc_l, wx, xc);
+                                }
+                                bad |= !(fabsf(xn) <= 4.0f);
+                            }
                         }
-                        bad |= !(fabsf(xn) <= 4.0f);
+                        *(uint4*)rs = make_uint4(hb[0] | (lb[0] << 16), hb[1] | (lb[1] << 16), hb[2] | (lb[2] << 16),
+                                                 hb[3] | (lb[3] << 16));
+                        const size_t e = rowoff + c0;
+                        if (full) {
+                            *(uint2*)(xph + e) = make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
+                            *(uint2*)(xpl + e) = make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+                            if (do_rho) {
+                                __stcs((double2*)(rho + e), make_double2(rn[0], rn[1]));
+                                __stcs((double2*)(rho + e) + 1, make_double2(rn[2], rn[3]));
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int c = c0 + i;
+                                if (c >= r && c < K) {
+                                    xph[e + i] = from_bits16<T>(hb[i]);
+                                    xpl[e + i] = from_bits16<T>(lb[i]);
+                                    if (do_rho) rho[e + i] = rn[i];
+                                }
+                            }
+                        }
                     }
                 }
             }
             epi_sync<NEPI>();
-            // mirror: column c of the tile becomes row c below the diagonal;
-            // lane j takes tile rows j, j + 32, ... (contiguous in the row)
-            for (int lc = ew; lc < BN; lc += NEPI / 32) {
-                const int c = n0 + lc;
-                if (c >= K) break;
-                const size_t rowoff = (size_t)c * Kp;
+            // mirror: tile column c becomes row c below the diagonal.  Each warp
+            // takes 4 tile columns at a time; lane j reads the 4 x 4 block of
+            // tile rows 4j .. 4j + 3, so every output row is one contiguous
+            // 256-byte run per part across the warp.
+            for (int lc0 = 4 * ew; lc0 < BN; lc0 += 4 * NW) {
+                if (n0 + lc0 >= K) break;
+                uint32_t v[4][4];
 #pragma unroll
-                for (int k = 0; k < BM / 32; ++k) {
-                    const int lr = lane + 32 * k;
-                    const int r = m0 + lr;
-                    if (r < c && r < K) {
-                        const uint32_t v = *(const uint32_t*)(Rs + lr * RS + lc);
-                        xph[rowoff + r] = from_bits16<T>(v & 0xffffu);
-                        xpl[rowoff + r] = from_bits16<T>(v >> 16);
+                for (int i = 0; i < 4; ++i) {
+                    const int lr = 4 * lane + i;
+                    const uint4 q = *(const uint4*)(Rs + lr * BN + (lc0 ^ rs_swz(lr)));
+                    v[i][0] = q.x;
+                    v[i][1] = q.y;
+                    v[i][2] = q.z;
+                    v[i][3] = q.w;
+                }
+                const int r0 = m0 + 4 * lane;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int c = n0 + lc0 + t;
+                    if (c >= K) break;
+                    if (r0 >= c || r0 >= K) continue;
+                    const size_t e = (size_t)c * Kp + r0;
+                    if (r0 + 3 < c && r0 + 3 < K) {
+                        *(uint2*)(xph + e) =
+                            make_uint2((v[0][t] & 0xffffu) | (v[1][t] << 16), (v[2][t] & 0xffffu) | (v[3][t] << 16));
+                        *(uint2*)(xpl + e) = make_uint2((v[0][t] >> 16) | (v[1][t] & 0xffff0000u),
+                                                        (v[2][t] >> 16) | (v[3][t] & 0xffff0000u));
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if (r0 + i < c && r0 + i < K) {
+                                xph[e + i] = from_bits16<T>(v[i][t] & 0xffffu);
+                                xpl[e + i] = from_bits16<T>(v[i][t] >> 16);
+                            }
+                        }
                     }
                 }
             }
