@@ -174,7 +174,7 @@ size_t carve(Ctx& c, char* base) {
     size_t o_wz = L.off(sizeof(float) * 3 * 128 * (size_t)c.n_atoms);
     size_t o_wdc = L.off(sizeof(double) * 16 * (size_t)c.n_atoms);
     size_t o_h16[2] = {0, 0}, o_x16[4] = {0, 0, 0, 0}, o_rtc = 0, o_tiles = 0, o_systab = 0, o_maps = 0;
-    size_t o_cst = 0, o_skf = 0, o_skb = 0;
+    size_t o_cst = 0, o_skf = 0, o_skb = 0, o_cnt = 0, o_macc = 0;
     if (c.Kp > 0) {
         size_t P16 = (size_t)c.Kp * c.Kp * 2;
         for (auto& o : o_h16) o = L.off(P16);
@@ -186,6 +186,8 @@ size_t carve(Ctx& c, char* base) {
         o_cst = L.off(sizeof(int) * ((size_t)c.tile_cap + 1));
         o_skf = L.off(sizeof(int) * (size_t)c.tile_cap);
         o_skb = L.off(sizeof(float) * (size_t)TC_SK_MAX_CTAS * 256 * 128);
+        o_cnt = L.off(sizeof(int) * 3 * (size_t)c.tile_cap);
+        o_macc = L.off(sizeof(long long) * (size_t)c.cheb_cap);
     }
     if (base) {
         c.d_fn = (Fn*)(base + o_fn);
@@ -227,6 +229,8 @@ size_t carve(Ctx& c, char* base) {
             c.d_cstart = (int*)(base + o_cst);
             c.d_skflag = (int*)(base + o_skf);
             c.d_skbuf = (float*)(base + o_skb);
+            c.d_cnt = (int*)(base + o_cnt);
+            c.d_macc = (long long*)(base + o_macc);
         }
     }
     return L.total;
@@ -421,16 +425,19 @@ void dm_prepare(Ctx& c, const double* F, cudaStream_t s, Timer* tm, int t0) {
 // In-flight tuning of the tensor-core launch shape on the weighted pass
 // (the dominant one): while the shape of this (precision, size, batch) is
 // untuned, the first steps l = 2, 3, ... run each candidate shape on two
-// rounds of two real steps, timed by events, and the fastest (minimum over
+// rounds of real steps (two per-step launches, or one dataflow launch of
+// eight steps), timed by events, and the fastest per step (minimum over
 // rounds) is kept for the rest of the pass and for later calls; no step is
 // repeated.  Returns the first step not yet run.
 int tc_pass2_tuned(TcBatch& b, int total_k, int Lmax, cudaStream_t s) {
     int l = 2;
-    TcCfg cand[8];
+    TcCfg cand[12];
     const int nc = tc_candidates(b, cand);
-    const int per = 2, rounds = 2;
-    if (tc_needs_tuning(b, total_k) && Lmax - 2 >= nc * per * rounds + 8) {
-        float best_ms[8];
+    const int per = 2, per_flow = 8, rounds = 2;
+    int need = 0;
+    for (int i = 0; i < nc; ++i) need += rounds * (cand[i].flow ? per_flow : per);
+    if (tc_needs_tuning(b, total_k) && Lmax - 2 >= need + 8) {
+        float best_ms[12];
         for (float& x : best_ms) x = 1e30f;
         cudaEvent_t e0, e1;
         DFT_CUDA_CHECK(cudaEventCreate(&e0));
@@ -438,13 +445,19 @@ int tc_pass2_tuned(TcBatch& b, int total_k, int Lmax, cudaStream_t s) {
         for (int r = 0; r < rounds; ++r)
             for (int i = 0; i < nc; ++i) {
                 b.cfg = cand[i];
+                const int n = cand[i].flow ? per_flow : per;
                 DFT_CUDA_CHECK(cudaEventRecord(e0, s));
-                for (int k = 0; k < per; ++k, ++l) tc_step_batch(b, l, (l + 1) & 1, 1, s);
+                if (cand[i].flow) {
+                    tc_run_flow(b, l, n, 1, 1, s);
+                    l += n;
+                } else {
+                    for (int k = 0; k < n; ++k, ++l) tc_step_batch(b, l, (l + 1) & 1, 1, s);
+                }
                 DFT_CUDA_CHECK(cudaEventRecord(e1, s));
                 DFT_CUDA_CHECK(cudaEventSynchronize(e1));
                 float ms = 0.f;
                 DFT_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
-                best_ms[i] = std::min(best_ms[i], ms);
+                best_ms[i] = std::min(best_ms[i], ms / n);
             }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -466,6 +479,11 @@ void dm_pass1(Ctx& c, cudaStream_t s) {
         TcBatch b = tc_batch(c, &cp, 1, &lim, &last, s);
         tc_set_limits(b, &cp, &lim, &last, s);
         b.cfg = tc_tuned(b, K);
+        if (b.cfg.flow) {
+            tc_run_flow(b, 1, J, 0, 2, s);
+            tc_moments_from_fixed(b, J, s);
+            return;
+        }
         for (int j = 1; j <= J; ++j) {
             tc_step_batch(b, j, j & 1, 2, s);
             tc_moment_reduce_batch(b, j, s);
@@ -501,7 +519,10 @@ void dm_pass2(Ctx& c, cudaStream_t s) {
         int lim = n_c, last = 0;
         TcBatch b = tc_batch(c, &cp, 1, &lim, &last, s);
         tc_set_limits(b, &cp, &lim, &last, s);
-        for (int l = tc_pass2_tuned(b, K, n_c, s); l < n_c; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, s);
+        const int l0 = tc_pass2_tuned(b, K, n_c, s);
+        if (b.cfg.flow) tc_run_flow(b, l0, n_c - l0, 1, 1, s);
+        else
+            for (int l = l0; l < n_c; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, s);
         tc_rho_finish(c, s);
         return;
     }
@@ -878,12 +899,17 @@ dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in
         for (int q = 0; q < n; ++q) total_k += cs[q]->K;
         b.cfg = tc_tuned(b, total_k);
         const long long gkey1 = batch_key(b);
-        run_graph(lead, 0, Jmax, gkey1, s, [&](cudaStream_t gs) {
-            for (int j = 1; j <= Jmax; ++j) {
-                tc_step_batch(b, j, j & 1, 2, gs);
-                tc_moment_reduce_batch(b, j, gs);
-            }
-        });
+        if (b.cfg.flow) {
+            tc_run_flow(b, 1, Jmax, 0, 2, s);
+            tc_moments_from_fixed(b, Jmax, s);
+        } else {
+            run_graph(lead, 0, Jmax, gkey1, s, [&](cudaStream_t gs) {
+                for (int j = 1; j <= Jmax; ++j) {
+                    tc_step_batch(b, j, j & 1, 2, gs);
+                    tc_moment_reduce_batch(b, j, gs);
+                }
+            });
+        }
         tm.mark(2);
         for (int q = 0; q < n; ++q) {
             dm_mu(*cs[q], s);
@@ -895,9 +921,13 @@ dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in
         tm.mark(3);
         const int l0 = tc_pass2_tuned(b, total_k, Lmax, s);
         const long long gkey2 = batch_key(b) * 65536 + l0;
-        run_graph(lead, 1, Lmax - l0, gkey2, s, [&](cudaStream_t gs) {
-            for (int l = l0; l < Lmax; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, gs);
-        });
+        if (b.cfg.flow) {
+            tc_run_flow(b, l0, Lmax - l0, 1, 1, s);
+        } else {
+            run_graph(lead, 1, Lmax - l0, gkey2, s, [&](cudaStream_t gs) {
+                for (int l = l0; l < Lmax; ++l) tc_step_batch(b, l, (l + 1) & 1, 1, gs);
+            });
+        }
         tm.mark(4);
         fork_systems(cs, s, [&](Ctx& c, int q, cudaStream_t as) {
             tc_rho_finish(c, as);

@@ -39,6 +39,10 @@ struct TcSys {
     double* rho;             // Kp x Kp FP64 upper triangle
     const double* coef;
     double* mom;
+    // dataflow mode: 256 x 256 blocks per side, 128-row tiles, block pairs and
+    // the first counter of this system; fixed-point moment sums (2^-44 units)
+    int nb, mt, npair, cnt_off;
+    long long* macc;
 };
 struct TcTile {
     int sys, i, j, idx;      // system, row tile, column tile, index within the system
@@ -46,6 +50,17 @@ struct TcTile {
 constexpr int TC_MAX_SYS = 64;
 constexpr int TC_SK_MAX_CTAS = 256;   // stream-K grid bound (one 128 KB partial-sum slot per CTA)
 constexpr int TC_MAPS_PER_SYS = 16;
+constexpr int TC_LISTS = 3;           // tile lists: 256-wide, 128-wide, 256-wide in block order (dataflow)
+
+// Dataflow pass: steps l0 .. l0 + nsteps - 1 in one persistent launch; X_l is
+// pair (l + cshift) & 1.  Per system and unordered pair {p, q} of 256 x 256
+// blocks, cnt holds W (tiles that finished writing the pair's blocks of the
+// newest iterate) and R[0], R[1] (tiles that finished reading the pair from
+// X pair 0 / 1), each counting up over the whole pass.
+struct TcFlow {
+    int l0 = 0, nsteps = 0, cshift = 0;
+    int* cnt = nullptr;
+};
 
 // launch configuration of the tensor-core step (chosen by the autotuner)
 struct TcCfg {
@@ -55,6 +70,7 @@ struct TcCfg {
     int streamk = 0;    // 1: cooperative grid, equal chunk ranges per CTA (256-wide tiles, one system)
     int pf = 0;         // L2 prefetch distance in k-blocks (0: none)
     int epf = 0;        // 1: prefetch the epilogue's rows into L2 before the last chunks
+    int flow = 0;       // 1: one cooperative launch per pass, tiles wait on block counters (256-wide tiles)
 };
 struct Ctx {
     // problem
@@ -129,6 +145,8 @@ struct Ctx {
     int* d_cstart = nullptr;     // stream-K: first chunk of each 256-wide tile [tile_cap + 1]
     int* d_skflag = nullptr;     // stream-K: partial sums handed over per tile [tile_cap]
     float* d_skbuf = nullptr;    // stream-K: partial sums, one slot per CTA [TC_SK_MAX_CTAS x 128 x 256]
+    int* d_cnt = nullptr;        // dataflow: block-pair counters of a batch led by this context [3 x tile_cap]
+    long long* d_macc = nullptr; // dataflow: fixed-point moment sums of this system [cheb_cap]
     int n_c_cur = 0;             // Chebyshev order of the density matrix in progress
     TcCfg tc_cfg;                // launch shape chosen for this system
     double e_bounds[2] = {0, 0}; // its spectral bounds
@@ -234,7 +252,9 @@ void tc_init(const Ctx& c, const double* coef, cudaStream_t s);
 struct TcBatch {
     const Ctx* leader = nullptr;
     int nsys = 0;
-    int ntiles[2] = {0, 0}, tile_off[2] = {0, 0};   // per tile width (256, 128)
+    int ntiles[TC_LISTS] = {0, 0, 0}, tile_off[TC_LISTS] = {0, 0, 0};   // per list (256, 128, 256 block order)
+    int ncnt = 0;                                    // dataflow counters in use (3 per block pair)
+    long long* macc[TC_MAX_SYS] = {};                // each system's fixed-point moment sums
     long long nchunks = 0;                           // chunks of the 256-wide list (stream-K)
     bool bf = false;
     TcCfg cfg;
@@ -250,6 +270,12 @@ int tc_streamk_grid(const TcBatch& b);             // 0 where stream-K does not 
 // fill leader's batch area with the given systems (pass lim/mom_last per system)
 TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const int* mom_last, cudaStream_t s);
 void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s);
+// dataflow pass (b.cfg.flow): steps l0 .. l0 + nsteps - 1 in one launch; in the
+// moments pass (mode 2) the sums go to each system's macc, zeroed here
+void tc_run_flow(const TcBatch& b, int l0, int nsteps, int cshift, int mode, cudaStream_t s);
+// m_{2j+2}, m_{2j+1} for j = 1 .. jmax from the fixed-point sums of a dataflow moments pass
+void tc_moments_from_fixed(const TcBatch& b, int jmax, cudaStream_t s);
+void tc_moments_from_fixed_range(const TcBatch& b, int j0, int j1, cudaStream_t s);
 void tc_moment_reduce_batch(const TcBatch& b, int j, cudaStream_t s);
 void tc_set_limits(const TcBatch& b, Ctx* const* sys, const int* lim, const int* mom_last, cudaStream_t s);
 void tc_rho_finish(const Ctx& c, cudaStream_t s);

@@ -260,18 +260,42 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n
 // the tiles' chunks (256 of K each) form one sequence, cs[t] being the first
 // chunk of tile t, and CTA c takes chunks [c C / G, (c + 1) C / G), so every
 // CTA gets the same number of chunks whatever the tile count.  A piece is the
-// chunk range [q0, q1) of one tile.
+// chunk range [q0, q1) of one tile.  Dataflow mode (cooperative grid): the
+// items (step, tile) of all steps of the pass in step-major order, CTA c
+// taking items c, c + G, ...; every CTA finishes its items of step s before
+// it starts one of step s + 1, and an item only waits on items of earlier
+// steps, so the waits resolve in step order.
 struct Cursor {
     long long pos, hi;
     int t, stride, ntiles;
     const int* cs;
-    bool sk;
-    __device__ void init(bool stream_k, const int* cstart, long long nchunks, int ntiles_) {
+    bool sk, fl;
+    int l, cur, s;   // step, X_l pair and step index within the pass of the current piece
+    TcFlow f;
+    __device__ void set_flow() {
+        if (pos < hi) {
+            t = (int)(pos % ntiles);
+            s = (int)(pos / ntiles);
+            l = f.l0 + s;
+            cur = (l + f.cshift) & 1;
+        }
+    }
+    __device__ void init(bool stream_k, const int* cstart, long long nchunks, int ntiles_, int l_, int cur_,
+                         const TcFlow& flow) {
         sk = stream_k;
+        fl = flow.cnt != nullptr;
+        f = flow;
         cs = cstart;
         ntiles = ntiles_;
         stride = gridDim.x;
-        if (sk) {
+        l = l_;
+        cur = cur_;
+        s = 0;
+        if (fl) {
+            pos = blockIdx.x;
+            hi = (long long)f.nsteps * ntiles;
+            set_flow();
+        } else if (sk) {
             pos = (long long)blockIdx.x * nchunks / gridDim.x;
             hi = (long long)(blockIdx.x + 1) * nchunks / gridDim.x;
             int a = 0, b = ntiles;   // last tile with cs[t] <= pos
@@ -286,11 +310,14 @@ struct Cursor {
             pos = hi = 0;
         }
     }
-    __device__ bool valid() const { return sk ? pos < hi : t < ntiles; }
+    __device__ bool valid() const { return (sk || fl) ? pos < hi : t < ntiles; }
     __device__ int q0() const { return sk ? (int)(pos - cs[t]) : 0; }
     __device__ int q1(int nchunk) const { return sk ? (int)(min(hi, (long long)cs[t + 1]) - cs[t]) : nchunk; }
     __device__ void next() {
-        if (sk) {
+        if (fl) {
+            pos += stride;
+            set_flow();
+        } else if (sk) {
             pos = min(hi, (long long)cs[t + 1]);
             ++t;
         } else {
@@ -299,10 +326,33 @@ struct Cursor {
     }
 };
 
+// index of the unordered block pair {p, q}, p <= q < nb
+__device__ __forceinline__ int pair_idx(int p, int q, int nb) { return p * nb - (p * (p - 1)) / 2 + (q - p); }
+
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ int ld_acquire(const int* p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// bounded wait until *c >= need; false (and FLAG_TIMEOUT set) after WAIT_NS,
+// or at once when another CTA has already given up
+__device__ bool wait_count(const int* c, int need, int* flags) {
+    if (ld_acquire(c) >= need) return true;
+    const unsigned long long t0 = globaltimer();
+    while (ld_acquire(c) < need) {
+        if (*(volatile int*)&flags[FLAG_TIMEOUT] != 0) return false;
+        if (globaltimer() - t0 > WAIT_NS) {
+            atomicExch(&flags[FLAG_TIMEOUT], 1);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
 }
 
 // Persistent multi-system step.  Each CTA walks its pieces (see Cursor); a
@@ -314,21 +364,28 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 // for the count (bounded), adds the partials in CTA order and resets it.  Pipeline
 // phases (stage ring, chunk accumulators) run on across tiles, so the MMA
 // warp starts the next tile's first two chunks while the epilogue warps
-// finish the previous tile.
+// finish the previous tile.  In dataflow mode (flow.cnt set) the producer
+// waits, before each chunk b of tile (i, j) at pass step s > 0, until both
+// writers of block pair {j, b} have finished step s - 1 (W); the epilogue
+// counts each chunk it has read (R of the pair read), waits before its first
+// store until every reader of the pair it overwrites has finished reading it
+// at step s - 1, and counts its own pair written (W) at the end.  Moment sums
+// go to fixed-point accumulators (integer adds: order-independent).
 template <bool BF, int BKV, int BNV>
 __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) k_cheb_step_tc(const TcSys* __restrict__ sys,
                                                               const CUtensorMap* __restrict__ maps,
-                                                              const TcTile* __restrict__ tiles, int ntiles, int l,
-                                                              int cur, int mode, double* __restrict__ part,
+                                                              const TcTile* __restrict__ tiles, int ntiles, int l_arg,
+                                                              int cur_arg, int mode, double* __restrict__ part,
                                                               int* __restrict__ flags, const int* __restrict__ cstart,
                                                               long long nchunks, float* __restrict__ skbuf,
-                                                              int* __restrict__ skflag, int pf, int epf) {
+                                                              int* __restrict__ skflag, int pf, int epf, TcFlow flow) {
     using T = typename H16<BF>::T;
     using C = Cfg<BKV, BNV>;
     constexpr int BK = C::BK, BN = C::BN, STAGES = C::STAGES, GK = C::GK, STAGE_BYTES = C::STAGE_BYTES;
     constexpr int A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES, NEPI = C::NEPI, TMEM_COLS = C::TMEM_COLS;
     constexpr int V = BN == 128 ? 1 : 0;   // tile-width variant (partial-sum slots)
     const bool sk = cstart != nullptr;
+    const bool fl = flow.cnt != nullptr;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -384,10 +441,11 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             long long g = 0;   // k-blocks issued by this CTA
             int nfin = 0;      // pieces whose epilogue runs here (over the ring)
             Cursor cu;
-            cu.init(sk, cstart, nchunks, ntiles);
+            cu.init(sk, cstart, nchunks, ntiles, l_arg, cur_arg, flow);
             for (; cu.valid() && !*abort_flag; cu.next()) {
                 const TcTile tl = tiles[cu.t];
                 const TcSys& S = sys[tl.sys];
+                const int l = cu.l, cur = cu.cur;
                 if (l >= S.lim) continue;
                 if (nfin > 0 && !mbar_wait(epi_done, (uint32_t)((nfin - 1) & 1))) {
                     // the previous tile's epilogue still holds the ring
@@ -411,6 +469,17 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                         tma_prefetch_2d(mp + 1, xp, m0);
                         tma_prefetch_2d(mb + 2 * cur, xp, n0);
                         tma_prefetch_2d(mb + 1 + 2 * cur, xp, n0);
+                    }
+                    if (fl && cu.s > 0 && kb % GK == 0) {
+                        // both writers of block pair {j, b} have finished the previous step
+                        const int bb = kb / GK, p = min(tl.j, bb), q = max(tl.j, bb);
+                        if (!wait_count(flow.cnt + S.cnt_off + pair_idx(p, q, S.nb), cu.s * min(2, S.mt - 2 * p),
+                                        flags)) {
+                            *abort_flag = 1;
+                            break;
+                        }
+                        // generic-proxy writes of other CTAs before this CTA's TMA reads
+                        asm volatile("fence.proxy.async.global;" ::: "memory");
                     }
                     if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
                         *abort_flag = 1;
@@ -438,10 +507,11 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
             long long g = 0, qg = 0;
             Cursor cu;
-            cu.init(sk, cstart, nchunks, ntiles);
+            cu.init(sk, cstart, nchunks, ntiles, l_arg, cur_arg, flow);
             for (; cu.valid() && !*abort_flag; cu.next()) {
                 const TcTile tl = tiles[cu.t];
                 const TcSys& S = sys[tl.sys];
+                const int l = cu.l, cur = cu.cur;
                 if (l >= S.lim) continue;
                 const int nk = (S.K + BK - 1) / BK;
                 const int nchunk = (nk + GK - 1) / GK;
@@ -497,10 +567,11 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
         bool bad = false;
         const int et = threadIdx.x - 64;   // epilogue thread index
         Cursor cu;
-        cu.init(sk, cstart, nchunks, ntiles);
+        cu.init(sk, cstart, nchunks, ntiles, l_arg, cur_arg, flow);
         for (; cu.valid() && ok; cu.next()) {
             const TcTile tl = tiles[cu.t];
             const TcSys& S = sys[tl.sys];
+            const int l = cu.l, cur = cu.cur;
             if (l >= S.lim) continue;
             const int nchunk = ((S.K + BK - 1) / BK + GK - 1) / GK;
             const int qa = cu.q0(), qb = cu.q1(nchunk);
@@ -538,6 +609,11 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 }
                 tc_fence_before();
                 mbar_arrive(&accempty[a]);
+                if (fl && et == 0) {
+                    // this tile has read chunk q of X_l (its loads landed before the MMAs ran)
+                    const int p = min(tl.j, q), qq = max(tl.j, q);
+                    red_release_add(flow.cnt + S.cnt_off + (1 + cur) * S.npair + pair_idx(p, qq, S.nb), 1);
+                }
             }
             if (!ok) break;
             if (sk && qa > 0) {
@@ -609,6 +685,24 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
 #pragma unroll
                 for (int j = 0; j < CPT; j += 4)
                     *(float4*)(rowp + ((half * CPT + j) ^ sw)) = make_float4(R[j], R[j + 1], R[j + 2], R[j + 3]);
+            }
+            if (fl && cu.s > 0) {
+                // the pair this tile overwrites (X pair 1 - cur) has been read by
+                // every tile of the previous step that reads it
+                if (et == 0) {
+                    const int p = tl.i >> 1, q = tl.j;
+                    const int rd = min(2 * p + 2, S.mt) + (p != q ? min(2 * q + 2, S.mt) : 0);
+                    red[16] = wait_count(flow.cnt + S.cnt_off + (2 - cur) * S.npair + pair_idx(p, q, S.nb),
+                                         rd * ((cu.s + 1) / 2), flags)
+                                  ? 1.0
+                                  : 0.0;
+                }
+                epi_sync<NEPI>();
+                ok = red[16] != 0.0;
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
             }
             epi_sync<NEPI>();
             const double al = do_rho ? S.coef[l] : 0.0;
@@ -783,10 +877,21 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                         a0 += red[2 * w];
                         a1 += red[2 * w + 1];
                     }
-                    part[2 * (S.part_off[V] + tl.idx)] = a0;
-                    part[2 * (S.part_off[V] + tl.idx) + 1] = a1;
+                    if (fl) {
+                        atomicAdd((unsigned long long*)&S.macc[2 * l + 2], (unsigned long long)llrint(a0 * 0x1p44));
+                        atomicAdd((unsigned long long*)&S.macc[2 * l + 1], (unsigned long long)llrint(a1 * 0x1p44));
+                    } else {
+                        part[2 * (S.part_off[V] + tl.idx)] = a0;
+                        part[2 * (S.part_off[V] + tl.idx) + 1] = a1;
+                    }
                 }
                 epi_sync<NEPI>();
+            }
+            if (fl) {
+                // every store of this tile is visible before its pair counts as written
+                __threadfence();
+                epi_sync<NEPI>();
+                if (et == 0) red_release_add(flow.cnt + S.cnt_off + pair_idx(tl.i >> 1, tl.j, S.nb), 1);
             }
         }
         if (bad) atomicExch(&flags[FLAG_SPECTRUM], 1);
@@ -814,6 +919,19 @@ __global__ void __launch_bounds__(256) k_moment_reduce_multi(const TcSys* __rest
     s0 = block_sum<256>(s0);
     s1 = block_sum<256>(s1);
     if (threadIdx.x == 0) {
+        const int ie = 2 * j + 2, io = 2 * j + 1;
+        if (ie < S.n_c) S.mom[ie] = 2.0 * s0 - (double)S.K;
+        if (io < S.n_c) S.mom[io] = 2.0 * s1 - S.mom[1];
+    }
+}
+
+// m_{2j+2} = 2 ||X_{j+1}||^2 - K and m_{2j+1} = 2 <X_{j+1}, X_j> - m_1 from the
+// fixed-point sums of a dataflow moments pass, j = j0 .. j1 (block b: system b)
+__global__ void __launch_bounds__(256) k_moments_fixed(const TcSys* __restrict__ sys, int j0, int j1) {
+    const TcSys& S = sys[blockIdx.x];
+    const int je = min(j1, S.mom_last);
+    for (int j = j0 + (int)threadIdx.x; j <= je; j += 256) {
+        const double s0 = (double)S.macc[2 * j + 2] * 0x1p-44, s1 = (double)S.macc[2 * j + 1] * 0x1p-44;
         const int ie = 2 * j + 2, io = 2 * j + 1;
         if (ie < S.n_c) S.mom[ie] = 2.0 * s0 - (double)S.K;
         if (io < S.n_c) S.mom[io] = 2.0 * s1 - S.mom[1];
@@ -981,6 +1099,11 @@ TcSys sys_entry(const Ctx& c, int lim, int mom_last) {
     e.rho = c.d_rho_tc;
     e.coef = c.d_coef;
     e.mom = c.d_mom;
+    e.nb = c.Kp / 256;
+    e.mt = (c.K + tc::BM - 1) / tc::BM;
+    e.npair = e.nb * (e.nb + 1) / 2;
+    e.cnt_off = 0;
+    e.macc = c.d_macc;
     return e;
 }
 int num_sms() {
@@ -1025,6 +1148,7 @@ TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const i
         if (c.Kp == 0) throw Error(DFT_EINVAL, "batched step needs a mixed-precision context");
         if (c.p.precision != leader.p.precision) throw Error(DFT_EINVAL, "batch mixes precisions");
         tab[q] = sys_entry(c, lim[q], mom_last[q]);
+        b.macc[q] = c.d_macc;
         CUtensorMap* m = &maps[TC_MAPS_PER_SYS * (size_t)q];
         for (int v = 0; v < 2; ++v) {
             m[6 * v + 0] = c.tm_h[v][0];
@@ -1051,7 +1175,33 @@ TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const i
                 if (t < per[q].size() / 2) tiles.push_back(TcTile{q, per[q][2 * t], per[q][2 * t + 1], (int)t});
         b.ntiles[v] = (int)tiles.size() - b.tile_off[v];
     }
+    // dataflow list: 256-wide tiles by 256 x 256 blocks, the block rows in
+    // order and within one the blocks left to right, both tiles of a block
+    // together, so the blocks of an iterate complete in the order in which
+    // the next step's tiles ask for them; systems interleaved as above
+    {
+        std::vector<std::vector<int>> per(nsys);
+        for (int q = 0; q < nsys; ++q) {
+            const int nb = tab[q].nb, mt = tab[q].mt;
+            for (int bp = 0; bp < nb; ++bp)
+                for (int bq = bp; bq < nb; ++bq)
+                    for (int i = 2 * bp; i < std::min(2 * bp + 2, mt); ++i) {
+                        per[q].push_back(i);
+                        per[q].push_back(bq);
+                    }
+            tab[q].cnt_off = b.ncnt;
+            b.ncnt += 3 * tab[q].npair;
+        }
+        b.tile_off[2] = (int)tiles.size();
+        size_t longest = 0;
+        for (auto& x : per) longest = std::max(longest, x.size() / 2);
+        for (size_t t = 0; t < longest; ++t)
+            for (int q = 0; q < nsys; ++q)
+                if (t < per[q].size() / 2) tiles.push_back(TcTile{q, per[q][2 * t], per[q][2 * t + 1], (int)t});
+        b.ntiles[2] = (int)tiles.size() - b.tile_off[2];
+    }
     if ((int)tiles.size() > leader.tile_cap) throw Error(DFT_ENOMEM, "batch tile list exceeds the leader's capacity");
+    if ((long long)b.ncnt > 3LL * leader.tile_cap) throw Error(DFT_ENOMEM, "batch block counters exceed the leader's capacity");
     // chunk offsets of the 256-wide list (stream-K); a chunk is 256 of K
     std::vector<int> cst(b.ntiles[0] + 1, 0);
     for (int t = 0; t < b.ntiles[0]; ++t) cst[t + 1] = cst[t] + (sys[tiles[t].sys]->K + 255) / 256;
@@ -1088,6 +1238,11 @@ void tc_set_limits(const TcBatch& b, Ctx* const* sys, const int* lim, const int*
 }
 
 void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s) {
+    if (b.cfg.flow) {
+        tc_run_flow(b, l, 1, (cur - l) & 1, mode, s);
+        if (mode & 2) tc_moments_from_fixed_range(b, l, l, s);
+        return;
+    }
     const Ctx& L = *b.leader;
     // launch shape (tuned): one CTA per tile, with the hardware handing tiles
     // to SMs as they free up, or a persistent grid of `persist` CTAs per SM
@@ -1116,7 +1271,7 @@ void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s) {
             DFT_CUDA_CHECK(cudaLaunchKernelEx(&lc, kern, (const TcSys*)L.d_systab, (const CUtensorMap*)L.d_maps,
                                               tiles, nt, l, cur, mode, L.d_part, L.d_flags,
                                               (const int*)L.d_cstart, b.nchunks, L.d_skbuf, L.d_skflag, b.cfg.pf,
-                                              b.cfg.epf));
+                                              b.cfg.epf, TcFlow{}));
         };
         if (b.cfg.bk == 64) {
             if (b.bf) go(tc::k_cheb_step_tc<true, 64, 256>, tc::Cfg<64, 256>{});
@@ -1132,7 +1287,8 @@ void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s) {
     auto go = [&](auto kern, auto cfg) {
         using C = decltype(cfg);
         kern<<<grid, C::NTHREADS, C::SMEM_BYTES, s>>>(L.d_systab, L.d_maps, tiles, nt, l, cur, mode, L.d_part,
-                                                      L.d_flags, nullptr, 0LL, nullptr, nullptr, b.cfg.pf, b.cfg.epf);
+                                                      L.d_flags, nullptr, 0LL, nullptr, nullptr, b.cfg.pf, b.cfg.epf,
+                                                      TcFlow{});
     };
     if (v == 1) {
         if (b.bf) go(tc::k_cheb_step_tc<true, 32, 128>, tc::Cfg<32, 128>{});
@@ -1147,7 +1303,58 @@ void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s) {
     check_launch("cheb_step_tc");
 }
 
+void tc_run_flow(const TcBatch& b, int l0, int nsteps, int cshift, int mode, cudaStream_t s) {
+    const Ctx& L = *b.leader;
+    const int nt = b.ntiles[2];
+    if (nt == 0 || nsteps <= 0) return;
+    DFT_CUDA_CHECK(cudaMemsetAsync(L.d_cnt, 0, sizeof(int) * (size_t)b.ncnt, s));
+    if (mode & 2)
+        for (int q = 0; q < b.nsys; ++q) DFT_CUDA_CHECK(cudaMemsetAsync(b.macc[q], 0, sizeof(long long) * (size_t)(2 * (l0 + nsteps) + 4), s));
+    TcFlow f;
+    f.l0 = l0;
+    f.nsteps = nsteps;
+    f.cshift = cshift;
+    f.cnt = L.d_cnt;
+    const TcTile* tiles = L.d_tiles + b.tile_off[2];
+    auto go = [&](auto kern, auto cfg) {
+        using C = decltype(cfg);
+        int occ = 0;
+        DFT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::NTHREADS, C::SMEM_BYTES));
+        if (occ < 1) throw Error(DFT_ECUDA, "tensor-core step does not fit on an SM");
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)std::min<long long>((long long)occ * num_sms(), (long long)nt * nsteps));
+        lc.blockDim = dim3(C::NTHREADS);
+        lc.dynamicSmemBytes = C::SMEM_BYTES;
+        lc.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        DFT_CUDA_CHECK(cudaLaunchKernelEx(&lc, kern, (const TcSys*)L.d_systab, (const CUtensorMap*)L.d_maps, tiles, nt,
+                                          l0, 0, mode, L.d_part, L.d_flags, (const int*)nullptr, 0LL, (float*)nullptr,
+                                          (int*)nullptr, b.cfg.pf, b.cfg.epf, f));
+    };
+    if (b.cfg.bk == 64) {
+        if (b.bf) go(tc::k_cheb_step_tc<true, 64, 256>, tc::Cfg<64, 256>{});
+        else go(tc::k_cheb_step_tc<false, 64, 256>, tc::Cfg<64, 256>{});
+    } else {
+        if (b.bf) go(tc::k_cheb_step_tc<true, 32, 256>, tc::Cfg<32, 256>{});
+        else go(tc::k_cheb_step_tc<false, 32, 256>, tc::Cfg<32, 256>{});
+    }
+    check_launch("cheb_step_tc", nsteps > 0 ? 1 : 0);
+}
+
+void tc_moments_from_fixed_range(const TcBatch& b, int j0, int j1, cudaStream_t s) {
+    tc::k_moments_fixed<<<b.nsys, 256, 0, s>>>(b.leader->d_systab, j0, j1);
+    check_launch("moments_fixed");
+}
+
+void tc_moments_from_fixed(const TcBatch& b, int jmax, cudaStream_t s) { tc_moments_from_fixed_range(b, 1, jmax, s); }
+
+// (dataflow passes convert their fixed-point sums instead: nothing to do)
 void tc_moment_reduce_batch(const TcBatch& b, int j, cudaStream_t s) {
+    if (b.cfg.flow) return;
     tc::k_moment_reduce_multi<<<b.nsys, 256, 0, s>>>(b.leader->d_systab, b.leader->d_part, j, b.cfg.bn == 128 ? 1 : 0);
     check_launch("moment_reduce_multi");
 }
@@ -1201,8 +1408,9 @@ std::string tune_key(const TcBatch& b, int total_k) {
     return o.str();
 }
 
-// cache file: one entry per line, `"key": [bk, persist, bn, streamk, ms...],`
-// inside braces (entries without bn are 256-wide, without streamk tile mode)
+// cache file: one entry per line, `"key": [bk, persist, bn, streamk, flow, ms...],`
+// inside braces (entries without bn are 256-wide, without streamk tile mode;
+// ms are the candidates' times per step)
 void tune_load() {
     if (g_tune_loaded) return;
     g_tune_loaded = true;
@@ -1214,11 +1422,13 @@ void tune_load() {
         size_t q0 = line.find('"'), q1 = line.find('"', q0 + 1), lb = line.find('[', q1 + 1);
         if (q0 == std::string::npos || q1 == std::string::npos || lb == std::string::npos) continue;
         TcCfg c;
-        int n = std::sscanf(line.c_str() + lb, "[%d, %d, %d, %d", &c.bk, &c.persist, &c.bn, &c.streamk);
+        int n = std::sscanf(line.c_str() + lb, "[%d, %d, %d, %d, %d", &c.bk, &c.persist, &c.bn, &c.streamk, &c.flow);
         if (n == 2) c.bn = 256;
         if (n < 4) c.streamk = 0;
+        if (n < 5) c.flow = 0;
         if (n >= 2 && (c.bk == 32 || c.bk == 64) && c.persist >= 0 && c.persist <= 2 &&
-            (c.bn == 256 || (c.bn == 128 && c.bk == 32)) && (c.streamk == 0 || (c.streamk == 1 && c.bn == 256)))
+            (c.bn == 256 || (c.bn == 128 && c.bk == 32)) && (c.streamk == 0 || (c.streamk == 1 && c.bn == 256)) &&
+            (c.flow == 0 || c.flow == 1))
             g_tuned[line.substr(q0 + 1, q1 - q0 - 1)] = c;
     }
 }
@@ -1232,7 +1442,7 @@ void tune_save() {
     for (auto& kv : g_tuned)
     {
         f << "  \"" << kv.first << "\": [" << kv.second.bk << ", " << kv.second.persist << ", " << kv.second.bn << ", "
-          << kv.second.streamk;
+          << kv.second.streamk << ", " << kv.second.flow;
         auto it = g_tune_ms.find(kv.first);
         if (it != g_tune_ms.end())
             for (float m : it->second) f << ", " << m;
@@ -1245,25 +1455,37 @@ void tune_save() {
 int tc_candidates(const TcBatch& b, TcCfg* out) {
     const TcCfg c[8] = {{32, 0, 256, 0}, {64, 0, 256, 0}, {32, 1, 256, 0}, {64, 1, 256, 0},
                         {32, 0, 128, 0}, {32, 2, 128, 0}, {32, 0, 256, 1}, {64, 0, 256, 1}};
+    int n = 0;
+    for (int i = 0; i < 6; ++i) out[n++] = c[i];
     // stream-K only where it applies and where it can balance a ragged last wave
-    const int n = (tc_streamk_grid(b) == std::min(num_sms(), TC_SK_MAX_CTAS)) ? 8 : 6;
-    for (int i = 0; i < n; ++i) out[i] = c[i];
+    if (tc_streamk_grid(b) == std::min(num_sms(), TC_SK_MAX_CTAS)) {
+        out[n++] = c[6];
+        out[n++] = c[7];
+    }
+    for (int bk : {32, 64}) {
+        TcCfg f;
+        f.bk = bk;
+        f.flow = 1;
+        out[n++] = f;
+    }
     return n;
 }
 
-// launch shape forced through DFT_TC_SHAPE="bk,persist,bn"
+// launch shape forced through DFT_TC_SHAPE="bk,persist,bn[,streamk[,pf[,epf[,flow]]]]"
 static bool forced_shape(TcCfg& c) {
     const char* e = std::getenv("DFT_TC_SHAPE");
     if (!e) return false;
     TcCfg f;
-    int n = std::sscanf(e, "%d,%d,%d,%d,%d,%d", &f.bk, &f.persist, &f.bn, &f.streamk, &f.pf, &f.epf);
+    int n = std::sscanf(e, "%d,%d,%d,%d,%d,%d,%d", &f.bk, &f.persist, &f.bn, &f.streamk, &f.pf, &f.epf, &f.flow);
     if (n < 3) return false;
     if (n == 3) f.streamk = 0;
     if (n <= 4) f.pf = 0;
     if (n <= 5) f.epf = TcCfg{}.epf;
-    if (f.pf < 0 || f.pf > 64 || f.epf < 0 || f.epf > 1) return false;
+    if (n <= 6) f.flow = 0;
+    if (f.pf < 0 || f.pf > 64 || f.epf < 0 || f.epf > 1 || f.flow < 0 || f.flow > 1) return false;
     if (!((f.bk == 32 || f.bk == 64) && f.persist >= 0 && f.persist <= 2 &&
-          (f.bn == 256 || (f.bn == 128 && f.bk == 32)) && (f.streamk == 0 || (f.streamk == 1 && f.bn == 256))))
+          (f.bn == 256 || (f.bn == 128 && f.bk == 32)) && (f.streamk == 0 || (f.streamk == 1 && f.bn == 256)) &&
+          (f.flow == 0 || (f.bn == 256 && f.streamk == 0))))
         return false;
     c = f;
     return true;

@@ -26,7 +26,12 @@ def make(name):
     return ctx
 
 
-def test_batched_equals_one_by_one():
+@pytest.mark.parametrize("shape", [None, "32,0,256,0,0,0,1"])
+def test_batched_equals_one_by_one(shape, monkeypatch):
+    """Tuned launch shape, and the dataflow shape (each pass one launch over
+    all systems' tiles, block counters per system, fixed-point moments)."""
+    if shape:
+        monkeypatch.setenv("DFT_TC_SHAPE", shape)
     solo = [make(n) for n in NAMES]
     dens_solo = [c.initial_density() for c in solo]
     batch = [make(n) for n in NAMES]

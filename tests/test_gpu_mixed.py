@@ -85,7 +85,8 @@ def test_mixed_grid_kernels_fp32():
     ctx.close()
 
 
-SHAPES = ["32,0,256", "64,0,256", "32,1,256", "64,1,256", "32,0,128", "32,2,128", "32,0,256,1", "64,0,256,1"]
+SHAPES = ["32,0,256", "64,0,256", "32,1,256", "64,1,256", "32,0,128", "32,2,128", "32,0,256,1", "64,0,256,1",
+          "32,0,256,0,0,0,1", "64,0,256,0,0,0,1"]
 
 
 @pytest.mark.parametrize("name", ["tiny37", "cluster64"])
@@ -95,7 +96,11 @@ def test_mixed_launch_shapes(name, monkeypatch):
     the oracle's density matrix; K = 370 leaves a ragged row and column tile,
     K = 640 a padded one.  Stream-K runs 5 CTAs on 10 chunks at K = 370 (no
     tile cut) and 16 CTAs on 33 chunks at K = 640, where most tiles are cut
-    between two CTAs and finished from handed-over partial sums."""
+    between two CTAs and finished from handed-over partial sums.  The dataflow
+    shapes run each pass as one launch: with 5 (K = 370) or 11 (K = 640)
+    tiles per step, the grid holds items of 14 to 30 consecutive steps at
+    once, so almost every chunk load waits on the block counters of the step
+    before and every epilogue on the readers of the block it overwrites."""
     s, st, F, lo, hi, n_c, ref = case(name)
     Ps = []
     for shape in SHAPES:
