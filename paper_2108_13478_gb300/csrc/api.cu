@@ -222,7 +222,7 @@ size_t carve(Ctx& c, char* base) {
         if (c.Kp > 0) {
             for (int q = 0; q < 2; ++q) c.d_h16[q] = base + o_h16[q];
             for (int q = 0; q < 4; ++q) c.d_x16[q] = base + o_x16[q];
-            c.d_rho_tc = (double*)(base + o_rtc);
+            c.d_rho_tc = (float2*)(base + o_rtc);
             c.d_systab = (TcSys*)(base + o_systab);
             c.d_maps = (CUtensorMap*)(base + o_maps);
             c.d_tiles = (TcTile*)(base + o_tiles);

@@ -36,7 +36,7 @@ struct TcSys {
     int n_c, mom_last;
     int part_off[2], ntl[2]; // per tile width (256, 128): its tiles and first partial slot
     void* x16[4];            // X pairs (hi, lo) x 2, Kp x Kp 16-bit
-    double* rho;             // Kp x Kp FP64 upper triangle
+    float2* rho;             // Kp x Kp compensated FP32 pairs (hi, lo), upper triangle
     const double* coef;
     double* mom;
     // dataflow mode: 256 x 256 blocks per side, 128-row tiles, block pairs and
@@ -132,7 +132,7 @@ struct Ctx {
     int n_tc_tiles = 0;
     void* d_h16[2] = {nullptr, nullptr};   // H_N hi, lo  [Kp x Kp] 16-bit
     void* d_x16[4] = {nullptr, nullptr, nullptr, nullptr};  // X pairs (hi, lo) x 2
-    double* d_rho_tc = nullptr;  // [Kp x Kp] FP64, upper triangle accumulated
+    float2* d_rho_tc = nullptr;  // [Kp x Kp] compensated FP32 pairs (hi + lo), upper triangle accumulated
     CUtensorMap tm_h[2][2];      // host copies of this system's tensor maps,
     CUtensorMap tm_x[2][4];      // per k-block variant (32 or 64 wide)
     CUtensorMap tm_xn[4];        // X maps with 128-row boxes (128-wide tiles, 32-wide k-blocks)

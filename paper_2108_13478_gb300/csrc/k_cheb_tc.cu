@@ -7,10 +7,11 @@
 //
 // Both H_N and X_l are symmetric polynomials of H_N, so only output tiles that
 // reach the upper triangle are computed; each tile writes its upper elements and
-// mirrors them into the lower triangle.  rho = sum_l a_l X_l is accumulated in
-// FP64 on the upper triangle.  The moment partials use compensated FP32 pairs
-// (about 48 bits): GB300's FP64 pipe issues 2 FMA per SM per clock, and two
-// FP64 products per element cost the moments pass ~20% of its time.
+// mirrors them into the lower triangle.  rho = sum_l a_l X_l is accumulated on
+// the upper triangle, and the moment partials are summed, in compensated FP32
+// pairs (hi + lo, about 48 bits): GB300's FP64 pipe issues 2 FMA per SM per
+// clock, which made one FP64 multiply-add and conversion per element half of
+// the weighted pass's epilogue time.
 //
 // Per CTA: one 128 x BN output tile (BN = 256 with one CTA per SM, or 128 with
 // two CTAs per SM, so that one CTA's epilogue overlaps the other's MMAs and
@@ -243,6 +244,19 @@ __device__ __forceinline__ void acc_prod(float& hi, float& lo, float x, float y)
     lo += e + pe;
 }
 
+// (hi, lo) += (ah + al) * x for a coefficient split into FP32 parts: the
+// product ah * x exactly (FMA TwoProduct), al * x rounded, then renormalised
+// so that |lo| <= ulp(hi) / 2
+__device__ __forceinline__ void acc_axpy(float& hi, float& lo, float ah, float al, float x) {
+    const float p = ah * x;
+    const float pe = fmaf(ah, x, -p);
+    float s, e;
+    two_sum(hi, p, s, e);
+    const float t = lo + (e + fmaf(al, x, pe));
+    hi = s + t;
+    lo = t - (hi - s);
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -336,6 +350,12 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
 __device__ __forceinline__ int ld_acquire(const int* p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -459,6 +479,28 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 const int nk = (S.K + BK - 1) / BK;
                 const int nchunk = (nk + GK - 1) / GK;
                 const int kend = min(nk, cu.q1(nchunk) * GK);
+                // dataflow: one batch of relaxed reads of the block counters this
+                // tile needs (chunks below 64), then one acquire fence; only the
+                // chunks not complete yet are waited for one by one below
+                unsigned long long rmask = 0;
+                if (fl && cu.s > 0) {
+                    const int nch = min(nchunk, 64);
+                    for (int b0 = 0; b0 < nch; b0 += 8) {
+                        int v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int bb = b0 + u, p = min(tl.j, bb), q = max(tl.j, bb);
+                            v[u] = bb < nch ? ld_relaxed(flow.cnt + S.cnt_off + pair_idx(p, q, S.nb)) : 0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int bb = b0 + u, p = min(tl.j, bb);
+                            if (bb < nch && v[u] >= cu.s * min(2, S.mt - 2 * p)) rmask |= 1ull << bb;
+                        }
+                    }
+                    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                }
                 for (int kb = cu.q0() * GK; kb < kend; ++kb, ++g) {
                     const int s = (int)(g % STAGES);
                     const uint32_t ph = (uint32_t)((g / STAGES) & 1);
@@ -470,7 +512,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                         tma_prefetch_2d(mb + 2 * cur, xp, n0);
                         tma_prefetch_2d(mb + 1 + 2 * cur, xp, n0);
                     }
-                    if (fl && cu.s > 0 && kb % GK == 0) {
+                    if (fl && cu.s > 0 && kb % GK == 0 && !(kb / GK < 64 && ((rmask >> (kb / GK)) & 1))) {
                         // both writers of block pair {j, b} have finished the previous step
                         const int bb = kb / GK, p = min(tl.j, bb), q = max(tl.j, bb);
                         if (!wait_count(flow.cnt + S.cnt_off + pair_idx(p, q, S.nb), cu.s * min(2, S.mt - 2 * p),
@@ -511,7 +553,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             for (; cu.valid() && !*abort_flag; cu.next()) {
                 const TcTile tl = tiles[cu.t];
                 const TcSys& S = sys[tl.sys];
-                const int l = cu.l, cur = cu.cur;
+                const int l = cu.l;
                 if (l >= S.lim) continue;
                 const int nk = (S.K + BK - 1) / BK;
                 const int nchunk = (nk + GK - 1) / GK;
@@ -587,7 +629,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                         const size_t e = (size_t)rr * S.Kp + n0 + half * CPT;
                         bulk_prefetch_l2((const T*)S.x16[2 * (1 - cur)] + e, CPT * sizeof(T));
                         bulk_prefetch_l2((const T*)S.x16[2 * (1 - cur) + 1] + e, CPT * sizeof(T));
-                        if (do_rho) bulk_prefetch_l2(S.rho + e, CPT * sizeof(double));
+                        if (do_rho) bulk_prefetch_l2(S.rho + e, CPT * sizeof(float2));
                         if (do_mom) {
                             bulk_prefetch_l2((const T*)S.x16[2 * cur] + e, CPT * sizeof(T));
                             bulk_prefetch_l2((const T*)S.x16[2 * cur + 1] + e, CPT * sizeof(T));
@@ -706,12 +748,13 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             }
             epi_sync<NEPI>();
             const double al = do_rho ? S.coef[l] : 0.0;
+            const float al_h = (float)al, al_l = (float)(al - (double)al_h);
             float snn_h = 0.0f, snn_l = 0.0f, snc_h = 0.0f, snc_l = 0.0f;
             T* xph = (T*)S.x16[2 * (1 - cur)];
             T* xpl = (T*)S.x16[2 * (1 - cur) + 1];
             const T* xch = (const T*)S.x16[2 * cur];
             const T* xcl = (const T*)S.x16[2 * cur + 1];
-            double* rho = S.rho;
+            float2* rho = S.rho;
             const int K = S.K;
             const size_t Kp = (size_t)S.Kp;
             const int ew = et >> 5;   // epilogue warp
@@ -728,7 +771,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             for (int lr0 = RB * ew; lr0 < BM; lr0 += RB * NW) {
                 if (m0 + lr0 >= K) break;
                 uint2 ph[RB][NG], pl[RB][NG], ch[RB][NG], cl[RB][NG];
-                double2 rq[RB][NG][2];
+                float4 rq[RB][NG][2];   // rho pairs (hi, lo) of 4 columns
 #pragma unroll
                 for (int u = 0; u < RB; ++u) {
                     const int r = min(m0 + lr0 + u, K - 1);
@@ -738,8 +781,8 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                         ph[u][g] = __ldcs((const uint2*)(xph + e));
                         pl[u][g] = __ldcs((const uint2*)(xpl + e));
                         if (do_rho) {
-                            rq[u][g][0] = __ldcs((const double2*)(rho + e));
-                            rq[u][g][1] = __ldcs((const double2*)(rho + e) + 1);
+                            rq[u][g][0] = __ldcs((const float4*)(rho + e));
+                            rq[u][g][1] = __ldcs((const float4*)(rho + e) + 1);
                         }
                         if (do_mom) {
                             ch[u][g] = *(const uint2*)(xch + e);
@@ -765,9 +808,9 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                         const float av[4] = {acc.x, acc.y, acc.z, acc.w};
                         const uint32_t phw[2] = {ph[u][g].x, ph[u][g].y}, plw[2] = {pl[u][g].x, pl[u][g].y};
                         const uint32_t chw[2] = {ch[u][g].x, ch[u][g].y}, clw[2] = {cl[u][g].x, cl[u][g].y};
-                        const double rv[4] = {rq[u][g][0].x, rq[u][g][0].y, rq[u][g][1].x, rq[u][g][1].y};
+                        float rh[4] = {rq[u][g][0].x, rq[u][g][0].z, rq[u][g][1].x, rq[u][g][1].z};
+                        float rl[4] = {rq[u][g][0].y, rq[u][g][0].w, rq[u][g][1].y, rq[u][g][1].w};
                         uint32_t hb[4], lb[4];
-                        double rn[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const int c = c0 + i;
@@ -779,7 +822,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                             const T lo = H16<BF>::from_f(xn - H16<BF>::to_f(h));
                             hb[i] = bits16(h);
                             lb[i] = bits16(lo);
-                            rn[i] = do_rho ? fma(al, (double)xn, rv[i]) : 0.0;
+                            if (do_rho) acc_axpy(rh[i], rl[i], al_h, al_l, xn);
                             const bool ok_i = c >= r && c < K;
                             if (ok_i) {
                                 if (do_mom) {
@@ -799,8 +842,8 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                             *(uint2*)(xph + e) = make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
                             *(uint2*)(xpl + e) = make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
                             if (do_rho) {
-                                __stcs((double2*)(rho + e), make_double2(rn[0], rn[1]));
-                                __stcs((double2*)(rho + e) + 1, make_double2(rn[2], rn[3]));
+                                __stcs((float4*)(rho + e), make_float4(rh[0], rl[0], rh[1], rl[1]));
+                                __stcs((float4*)(rho + e) + 1, make_float4(rh[2], rl[2], rh[3], rl[3]));
                             }
                         } else {
 #pragma unroll
@@ -809,7 +852,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                                 if (c >= r && c < K) {
                                     xph[e + i] = from_bits16<T>(hb[i]);
                                     xpl[e + i] = from_bits16<T>(lb[i]);
-                                    if (do_rho) rho[e + i] = rn[i];
+                                    if (do_rho) rho[e + i] = make_float2(rh[i], rl[i]);
                                 }
                             }
                         }
@@ -965,21 +1008,24 @@ __global__ void k_identity16(int K, int Kp, void* hi_, void* lo_) {
 // rho (ld Kp) = a0 I + a1 H_N  (H_N from the split pair, as the recurrence sees it)
 template <bool BF>
 __global__ void k_rho_init(int K, int Kp, const void* hh_, const void* hl_, const double* __restrict__ a,
-                           double* rho) {
+                           float2* rho) {
     using T = typename H16<BF>::T;
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)Kp * Kp) return;
     int i = (int)(e / Kp), j = (int)(e % Kp);
     double h = (double)H16<BF>::to_f(((const T*)hh_)[e]) + (double)H16<BF>::to_f(((const T*)hl_)[e]);
-    rho[e] = (i < K && j < K) ? a[0] * (i == j ? 1.0 : 0.0) + a[1] * h : 0.0;
+    const double v = (i < K && j < K) ? a[0] * (i == j ? 1.0 : 0.0) + a[1] * h : 0.0;
+    const float vh = (float)v;
+    rho[e] = make_float2(vh, (float)(v - (double)vh));
 }
 
 // full symmetric K x K rho from the upper triangle of the Kp-strided buffer
-__global__ void k_rho_mirror(int K, int Kp, const double* __restrict__ up, double* __restrict__ out) {
+__global__ void k_rho_mirror(int K, int Kp, const float2* __restrict__ up, double* __restrict__ out) {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)K * K) return;
     int i = (int)(e / K), j = (int)(e % K);
-    out[e] = j >= i ? up[(long long)i * Kp + j] : up[(long long)j * Kp + i];
+    const float2 v = j >= i ? up[(long long)i * Kp + j] : up[(long long)j * Kp + i];
+    out[e] = (double)v.x + (double)v.y;
 }
 
 // trace and Frobenius norm of H_N as the recurrence sees it (split pair):
