@@ -63,7 +63,9 @@ struct Cfg {
     static constexpr int A_BYTES = BM * BK_ * 2;
     static constexpr int B_BYTES = BN_ * BK_ * 2;
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
+    // 256-wide tiles: two 16 KB mirror buffers of the off-diagonal epilogue
+    static constexpr int MIR_BYTES = BN_ == 256 ? 2 * 16384 : 0;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + MIR_BYTES + 1024 + 512;
     static constexpr int TMEM_COLS = 2 * BN_;         // two chunk accumulators
 };
 constexpr unsigned long long WAIT_NS = 1000000000ull;   // 1 s per wait
@@ -108,6 +110,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     }
     return true;
 }
+
+// shared -> global tensor-map store of one box (bulk async group of this thread)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x), "r"(y),
+                 "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// this thread's bulk stores have finished reading shared memory / have completed
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 
 // L2 prefetch of one tensor-map box (no shared memory, no completion signal)
 __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
@@ -177,6 +191,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // 16-bit storage type of the split operands
 template <bool BF>
@@ -408,15 +434,18 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
     const bool fl = flow.cnt != nullptr;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    uint8_t* mirbuf = smem + STAGES * STAGE_BYTES;   // [2 halves][hi, lo][2 boxes of 32 x 128 B]
+    uint64_t* full = (uint64_t*)(mirbuf + C::MIR_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* accfull = empty + STAGES;
     uint64_t* accempty = accfull + 2;
     uint64_t* drain = accempty + 2;
     uint64_t* epi_done = drain + 1;   // epilogue finished with the ring (staged sums)
-    uint32_t* tmem_slot = (uint32_t*)(epi_done + 1);
+    uint64_t* ebar = epi_done + 1;    // [4] epilogue slab loads (off-diagonal tiles)
+    uint32_t* tmem_slot = (uint32_t*)(ebar + 4);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    double* red = (double*)(smem + STAGES * STAGE_BYTES + 128);   // 2 x 8 moment partials + 1 flag
+    double* red = (double*)(mirbuf + C::MIR_BYTES + 256);   // 2 x 8 moment partials + 1 flag
+    static_assert((2 * STAGES + 10) * 8 + 8 <= 256, "barriers overlap the reduction slots");
     // staged FP32 sums of a finished tile, over the operand ring
     static_assert(BM * BN * 4 <= STAGES * STAGE_BYTES, "staged tile does not fit the ring");
     float* Rs = (float*)smem;
@@ -435,6 +464,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
         }
         mbar_init(drain, 1);
         mbar_init(epi_done, NEPI);
+        for (int b = 0; b < 4; ++b) mbar_init(&ebar[b], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -719,16 +749,8 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             // bank window, so the 16-byte accesses of all three passes below
             // (lane per row here, lane per 4 columns of one row, lane per 4 rows
             // of 4 columns in the mirror) are free of bank conflicts.
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            {
-                const int lr = 32 * quad + lane;
-                float* rowp = Rs + lr * BN;
-                const int sw = rs_swz(lr);
-#pragma unroll
-                for (int j = 0; j < CPT; j += 4)
-                    *(float4*)(rowp + ((half * CPT + j) ^ sw)) = make_float4(R[j], R[j + 1], R[j + 2], R[j + 3]);
-            }
-            if (fl && cu.s > 0) {
+            const bool fast = !sk && BN == 256 && (tl.i >> 1) != tl.j && !(do_rho && do_mom);
+            if (fl && cu.s > 0 && !fast) {
                 // the pair this tile overwrites (X pair 1 - cur) has been read by
                 // every tile of the previous step that reads it
                 if (et == 0) {
@@ -746,7 +768,6 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                     break;
                 }
             }
-            epi_sync<NEPI>();
             const double al = do_rho ? S.coef[l] : 0.0;
             const float al_h = (float)al, al_l = (float)(al - (double)al_h);
             float snn_h = 0.0f, snn_l = 0.0f, snc_h = 0.0f, snc_l = 0.0f;
@@ -757,152 +778,327 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             float2* rho = S.rho;
             const int K = S.K;
             const size_t Kp = (size_t)S.Kp;
-            const int ew = et >> 5;   // epilogue warp
-            constexpr int NW = NEPI / 32;
-            // rows: each warp takes RB consecutive rows at a time; lane j takes
-            // columns 4j .. 4j + 3 of every 128-column group, so one warp access
-            // is a contiguous 256-byte (16-bit pair parts) or 1 KB (rho) run of a
-            // row, and RB * BN / 128 such runs per array are in flight per lane.
-            // Every vector lies inside the Kp x Kp buffers (Kp is a multiple of
-            // 256), so loads are unconditional; stores keep to the upper triangle
-            // c >= r and c < K, per element where a vector crosses either edge.
-            // X_{l+1} (hi, lo) goes back to shared memory, packed, for the mirror.
-            constexpr int RB = 512 / BN, NG = BN / 128;   // 4 (row, group) slots per lane
-            for (int lr0 = RB * ew; lr0 < BM; lr0 += RB * NW) {
-                if (m0 + lr0 >= K) break;
-                uint2 ph[RB][NG], pl[RB][NG], ch[RB][NG], cl[RB][NG];
-                float4 rq[RB][NG][2];   // rho pairs (hi, lo) of 4 columns
-#pragma unroll
-                for (int u = 0; u < RB; ++u) {
-                    const int r = min(m0 + lr0 + u, K - 1);
-#pragma unroll
-                    for (int g = 0; g < NG; ++g) {
-                        const size_t e = (size_t)r * Kp + n0 + 128 * g + 4 * lane;
-                        ph[u][g] = __ldcs((const uint2*)(xph + e));
-                        pl[u][g] = __ldcs((const uint2*)(xpl + e));
-                        if (do_rho) {
-                            rq[u][g][0] = __ldcs((const float4*)(rho + e));
-                            rq[u][g][1] = __ldcs((const float4*)(rho + e) + 1);
-                        }
-                        if (do_mom) {
-                            ch[u][g] = *(const uint2*)(xch + e);
-                            cl[u][g] = *(const uint2*)(xcl + e);
-                        }
+            // Off-diagonal tiles (block row i / 2 < block column j) lie wholly above
+            // the diagonal and inside the Kp x Kp buffers, so whole boxes move: the
+            // sums stay in registers (thread = tile row, 128 columns), and each
+            // half of the epilogue streams its four 32-column slabs (X_{l-1} pair,
+            // rho pairs or X_l pair; 48 KB) through two ring buffers with TMA
+            // loads, updates them in place and TMA-stores them back; the mirror
+            // goes out from registers, one contiguous 64-byte run per warp and
+            // column.  Diagonal tiles take the masked path below.
+            if (fast) {
+                const int r_loc = 32 * quad + lane;
+                const bool th = (et & 127) == 0;   // issues this half's bulk copies
+                const CUtensorMap* mx = maps + TC_MAPS_PER_SYS * tl.sys + 12;   // X pairs, 32 x 128 boxes
+                const CUtensorMap* mr = maps + TC_MAPS_PER_SYS * tl.sys + 16;   // rho pairs
+                const CUtensorMap* mm = maps + TC_MAPS_PER_SYS * tl.sys + 18;   // X pairs, 64 x 32 boxes
+                constexpr int SLAB = 48 * 1024;
+                static_assert(BN != 256 || 4 * SLAB <= STAGES * STAGE_BYTES, "slab buffers exceed the ring");
+                const uint32_t slab_bytes = do_rho ? 49152u : (do_mom ? 32768u : 16384u);
+                auto issue_load = [&](int sl) {
+                    uint8_t* bf = smem + (2 * half + (sl & 1)) * SLAB;
+                    uint64_t* bar = &ebar[2 * half + (sl & 1)];
+                    const int x = n0 + 128 * half + 32 * sl;
+                    mbar_expect_tx(bar, slab_bytes);
+                    tma_load_2d(bf, mx + 2 * (1 - cur), x, m0, bar);
+                    tma_load_2d(bf + 8192, mx + 2 * (1 - cur) + 1, x, m0, bar);
+                    if (do_rho) {
+                        tma_load_2d(bf + 16384, mr, 2 * x, m0, bar);
+                        tma_load_2d(bf + 32768, mr, 2 * x + 32, m0, bar);
                     }
+                    if (do_mom) {
+                        tma_load_2d(bf + 16384, mx + 2 * cur, x, m0, bar);
+                        tma_load_2d(bf + 24576, mx + 2 * cur + 1, x, m0, bar);
+                    }
+                };
+                // the slab loads read only this tile's own positions: they go out
+                // before anything else, ahead of the wait for the block's readers
+                if (th) {
+                    issue_load(0);
+                    issue_load(1);
                 }
+                // the final sums go back to tensor memory (both chunk accumulators
+                // stay idle until this tile hands the ring back), freeing registers
+                const uint32_t tacc = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(half * CPT);
 #pragma unroll
-                for (int u = 0; u < RB; ++u) {
-                    const int lr = lr0 + u;
-                    const int r = m0 + lr;
-                    if (r >= K) break;
-                    const size_t rowoff = (size_t)r * Kp;
-                    const int sw = rs_swz(lr);
+                for (int cc = 0; cc < CPT / 16; ++cc) tmem_st16(tacc + 16 * cc, &R[16 * cc]);
+                tmem_wait_st();
+                const int xsw = (r_loc >> 1) & 3, rsw = r_loc & 7;   // 64- and 128-byte swizzle of this row
+                // mirror of this thread's row: column r_loc of the 32 x 128 mirror
+                // boxes (box r_loc / 64, 128-byte swizzle on the 16-byte chunk)
+                uint8_t* mb = mirbuf + half * 16384 + (r_loc >> 6) * 4096;
+                const int rb = (r_loc & 63) * 2;
+                bool got_all = true, war_ok = true;
+#pragma unroll 1
+                for (int sl = 0; sl < 4; ++sl) {
+                    uint8_t* bf = smem + (2 * half + (sl & 1)) * SLAB;
+                    got_all &= mbar_wait(&ebar[2 * half + (sl & 1)], (uint32_t)((sl >> 1) & 1));
+                    uint32_t av[32];
+                    tmem_ld32(tacc + 32 * sl, av);
 #pragma unroll
-                    for (int g = 0; g < NG; ++g) {
-                        const int lc = 128 * g + 4 * lane;
-                        const int c0 = n0 + lc;
-                        if (c0 + 3 < r || c0 >= K) continue;
-                        const bool full = c0 >= r && c0 + 3 < K;
-                        float* rs = Rs + lr * BN + (lc ^ sw);
-                        const float4 acc = *(const float4*)rs;
-                        const float av[4] = {acc.x, acc.y, acc.z, acc.w};
-                        const uint32_t phw[2] = {ph[u][g].x, ph[u][g].y}, plw[2] = {pl[u][g].x, pl[u][g].y};
-                        const uint32_t chw[2] = {ch[u][g].x, ch[u][g].y}, clw[2] = {cl[u][g].x, cl[u][g].y};
-                        float rh[4] = {rq[u][g][0].x, rq[u][g][0].z, rq[u][g][1].x, rq[u][g][1].z};
-                        float rl[4] = {rq[u][g][0].y, rq[u][g][0].w, rq[u][g][1].y, rq[u][g][1].w};
-                        uint32_t hb[4], lb[4];
+                    for (int c8 = 0; c8 < 4; ++c8) {
+                        uint4* hp = (uint4*)(bf + r_loc * 64 + ((c8 ^ xsw) << 4));
+                        uint4* lp = (uint4*)(bf + 8192 + r_loc * 64 + ((c8 ^ xsw) << 4));
+                        const uint4 hv = *hp, lv = *lp;
+                        uint4 chv = make_uint4(0, 0, 0, 0), clv = chv;
+                        if (do_mom) {
+                            chv = *(const uint4*)(bf + 16384 + r_loc * 64 + ((c8 ^ xsw) << 4));
+                            clv = *(const uint4*)(bf + 24576 + r_loc * 64 + ((c8 ^ xsw) << 4));
+                        }
+                        // rho pairs of these 8 columns: box c8 / 2, 16-byte chunks 4 (c8 & 1) .. + 3
+                        uint8_t* rrow = bf + 16384 + (c8 >> 1) * 16384 + r_loc * 128;
+                        float4 rv[4];
+                        if (do_rho)
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int c = c0 + i;
-                            const int sh = 16 * (i & 1);
-                            const float xp = H16<BF>::to_f(from_bits16<T>(phw[i >> 1] >> sh)) +
-                                             H16<BF>::to_f(from_bits16<T>(plw[i >> 1] >> sh));
-                            const float xn = 2.0f * av[i] - xp;
+                            for (int k = 0; k < 4; ++k) rv[k] = *(const float4*)(rrow + (((4 * (c8 & 1) + k) ^ rsw) << 4));
+                        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
+                        const uint32_t chw[4] = {chv.x, chv.y, chv.z, chv.w}, clw[4] = {clv.x, clv.y, clv.z, clv.w};
+                        uint32_t ho[4], lo_[4];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int sh = 16 * (e & 1);
+                            const float xp = H16<BF>::to_f(from_bits16<T>(hw[e >> 1] >> sh)) +
+                                             H16<BF>::to_f(from_bits16<T>(lw[e >> 1] >> sh));
+                            const float xn = 2.0f * __uint_as_float(av[8 * c8 + e]) - xp;
                             const T h = H16<BF>::from_f(xn);
                             const T lo = H16<BF>::from_f(xn - H16<BF>::to_f(h));
-                            hb[i] = bits16(h);
-                            lb[i] = bits16(lo);
-                            if (do_rho) acc_axpy(rh[i], rl[i], al_h, al_l, xn);
-                            const bool ok_i = c >= r && c < K;
-                            if (ok_i) {
-                                if (do_mom) {
-                                    const float wx = (c == r) ? xn : 2.0f * xn;
-                                    const float xc = H16<BF>::to_f(from_bits16<T>(chw[i >> 1] >> sh)) +
-                                                     H16<BF>::to_f(from_bits16<T>(clw[i >> 1] >> sh));
-                                    acc_prod(snn_h, snn_l, wx, xn);
-                                    acc_prod(snc_h, snc_l, wx, xc);
-                                }
-                                bad |= !(fabsf(xn) <= 4.0f);
+                            if (e & 1) {
+                                ho[e >> 1] |= bits16(h) << 16;
+                                lo_[e >> 1] |= bits16(lo) << 16;
+                            } else {
+                                ho[e >> 1] = bits16(h);
+                                lo_[e >> 1] = bits16(lo);
+                            }
+                            if (do_rho) {
+                                float4& q = rv[e >> 1];
+                                if (e & 1) acc_axpy(q.z, q.w, al_h, al_l, xn);
+                                else acc_axpy(q.x, q.y, al_h, al_l, xn);
+                            }
+                            if (do_mom) {
+                                const float xc = H16<BF>::to_f(from_bits16<T>(chw[e >> 1] >> sh)) +
+                                                 H16<BF>::to_f(from_bits16<T>(clw[e >> 1] >> sh));
+                                acc_prod(snn_h, snn_l, 2.0f * xn, xn);
+                                acc_prod(snc_h, snc_l, 2.0f * xn, xc);
+                            }
+                            bad |= !(fabsf(xn) <= 4.0f);
+                            // mirror row c = 8 c8 + e of the slab, column r_loc
+                            const int cm = 8 * c8 + e;
+                            const int mo = cm * 128 + ((((rb >> 4) ^ (cm & 7))) << 4) + (rb & 15);
+                            *(T*)(mb + mo) = h;
+                            *(T*)(mb + 8192 + mo) = lo;
+                        }
+                        *hp = make_uint4(ho[0], ho[1], ho[2], ho[3]);
+                        *lp = make_uint4(lo_[0], lo_[1], lo_[2], lo_[3]);
+                        if (do_rho)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) *(float4*)(rrow + (((4 * (c8 & 1) + k) ^ rsw) << 4)) = rv[k];
+                    }
+                    // the half's generic writes of this slab before its bulk stores
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("bar.sync %0, 128;" ::"r"(2 + half) : "memory");
+                    if (th) {
+                        if (sl == 0 && fl && cu.s > 0) {
+                            // the block pair this tile overwrites (X pair 1 - cur) has
+                            // been read by every tile of the previous step that reads it
+                            const int p = tl.i >> 1, q = tl.j;
+                            const int rd = min(2 * p + 2, S.mt) + min(2 * q + 2, S.mt);
+                            war_ok = wait_count(flow.cnt + S.cnt_off + (2 - cur) * S.npair + pair_idx(p, q, S.nb),
+                                                rd * ((cu.s + 1) / 2), flags);
+                        }
+                        const int x = n0 + 128 * half + 32 * sl;
+                        if (war_ok) {
+                            // mirror: rows x .. x + 31, columns m0 .. m0 + 127 (two boxes per part)
+                            tma_store_2d(mm + 2 * (1 - cur), m0, x, mirbuf + half * 16384);
+                            tma_store_2d(mm + 2 * (1 - cur), m0 + 64, x, mirbuf + half * 16384 + 4096);
+                            tma_store_2d(mm + 2 * (1 - cur) + 1, m0, x, mirbuf + half * 16384 + 8192);
+                            tma_store_2d(mm + 2 * (1 - cur) + 1, m0 + 64, x, mirbuf + half * 16384 + 12288);
+                            bulk_commit();
+                            tma_store_2d(mx + 2 * (1 - cur), x, m0, bf);
+                            tma_store_2d(mx + 2 * (1 - cur) + 1, x, m0, bf + 8192);
+                            if (do_rho) {
+                                tma_store_2d(mr, 2 * x, m0, bf + 16384);
+                                tma_store_2d(mr, 2 * x + 32, m0, bf + 32768);
+                            }
+                            bulk_commit();
+                        }
+                        if (sl + 2 < 4) {
+                            bulk_wait_read0();   // slab and mirror buffers free again
+                            issue_load(sl + 2);
+                        } else {
+                            bulk_wait_read1();   // mirror buffer free again
+                        }
+                    }
+                    asm volatile("bar.sync %0, 128;" ::"r"(2 + half) : "memory");
+                }
+                if (th) {
+                    bulk_wait0();
+                    // the bulk stores (async proxy) before this tile counts as written
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    if (!war_ok) *abort_flag = 1;
+                }
+                if (!got_all) atomicExch(&flags[FLAG_TIMEOUT], 1);
+                epi_sync<NEPI>();
+                if (*abort_flag) ok = false;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(epi_done);
+            } else {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                {
+                    const int lr = 32 * quad + lane;
+                    float* rowp = Rs + lr * BN;
+                    const int sw = rs_swz(lr);
+#pragma unroll
+                    for (int j = 0; j < CPT; j += 4)
+                        *(float4*)(rowp + ((half * CPT + j) ^ sw)) = make_float4(R[j], R[j + 1], R[j + 2], R[j + 3]);
+                }
+                epi_sync<NEPI>();
+                const int ew = et >> 5;   // epilogue warp
+                constexpr int NW = NEPI / 32;
+                // rows: each warp takes RB consecutive rows at a time; lane j takes
+                // columns 4j .. 4j + 3 of every 128-column group, so one warp access
+                // is a contiguous 256-byte (16-bit pair parts) or 1 KB (rho) run of a
+                // row, and RB * BN / 128 such runs per array are in flight per lane.
+                // Every vector lies inside the Kp x Kp buffers (Kp is a multiple of
+                // 256), so loads are unconditional; stores keep to the upper triangle
+                // c >= r and c < K, per element where a vector crosses either edge.
+                // X_{l+1} (hi, lo) goes back to shared memory, packed, for the mirror.
+                constexpr int RB = 512 / BN, NG = BN / 128;   // 4 (row, group) slots per lane
+                for (int lr0 = RB * ew; lr0 < BM; lr0 += RB * NW) {
+                    if (m0 + lr0 >= K) break;
+                    uint2 ph[RB][NG], pl[RB][NG], ch[RB][NG], cl[RB][NG];
+                    float4 rq[RB][NG][2];   // rho pairs (hi, lo) of 4 columns
+#pragma unroll
+                    for (int u = 0; u < RB; ++u) {
+                        const int r = min(m0 + lr0 + u, K - 1);
+#pragma unroll
+                        for (int g = 0; g < NG; ++g) {
+                            const size_t e = (size_t)r * Kp + n0 + 128 * g + 4 * lane;
+                            ph[u][g] = __ldcs((const uint2*)(xph + e));
+                            pl[u][g] = __ldcs((const uint2*)(xpl + e));
+                            if (do_rho) {
+                                rq[u][g][0] = __ldcs((const float4*)(rho + e));
+                                rq[u][g][1] = __ldcs((const float4*)(rho + e) + 1);
+                            }
+                            if (do_mom) {
+                                ch[u][g] = *(const uint2*)(xch + e);
+                                cl[u][g] = *(const uint2*)(xcl + e);
                             }
                         }
-                        *(uint4*)rs = make_uint4(hb[0] | (lb[0] << 16), hb[1] | (lb[1] << 16), hb[2] | (lb[2] << 16),
-                                                 hb[3] | (lb[3] << 16));
-                        const size_t e = rowoff + c0;
-                        if (full) {
-                            *(uint2*)(xph + e) = make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
-                            *(uint2*)(xpl + e) = make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
-                            if (do_rho) {
-                                __stcs((float4*)(rho + e), make_float4(rh[0], rl[0], rh[1], rl[1]));
-                                __stcs((float4*)(rho + e) + 1, make_float4(rh[2], rl[2], rh[3], rl[3]));
-                            }
-                        } else {
+                    }
+#pragma unroll
+                    for (int u = 0; u < RB; ++u) {
+                        const int lr = lr0 + u;
+                        const int r = m0 + lr;
+                        if (r >= K) break;
+                        const size_t rowoff = (size_t)r * Kp;
+                        const int sw = rs_swz(lr);
+#pragma unroll
+                        for (int g = 0; g < NG; ++g) {
+                            const int lc = 128 * g + 4 * lane;
+                            const int c0 = n0 + lc;
+                            if (c0 + 3 < r || c0 >= K) continue;
+                            const bool full = c0 >= r && c0 + 3 < K;
+                            float* rs = Rs + lr * BN + (lc ^ sw);
+                            const float4 acc = *(const float4*)rs;
+                            const float av[4] = {acc.x, acc.y, acc.z, acc.w};
+                            const uint32_t phw[2] = {ph[u][g].x, ph[u][g].y}, plw[2] = {pl[u][g].x, pl[u][g].y};
+                            const uint32_t chw[2] = {ch[u][g].x, ch[u][g].y}, clw[2] = {cl[u][g].x, cl[u][g].y};
+                            float rh[4] = {rq[u][g][0].x, rq[u][g][0].z, rq[u][g][1].x, rq[u][g][1].z};
+                            float rl[4] = {rq[u][g][0].y, rq[u][g][0].w, rq[u][g][1].y, rq[u][g][1].w};
+                            uint32_t hb[4], lb[4];
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
                                 const int c = c0 + i;
-                                if (c >= r && c < K) {
-                                    xph[e + i] = from_bits16<T>(hb[i]);
-                                    xpl[e + i] = from_bits16<T>(lb[i]);
-                                    if (do_rho) rho[e + i] = make_float2(rh[i], rl[i]);
+                                const int sh = 16 * (i & 1);
+                                const float xp = H16<BF>::to_f(from_bits16<T>(phw[i >> 1] >> sh)) +
+                                                 H16<BF>::to_f(from_bits16<T>(plw[i >> 1] >> sh));
+                                const float xn = 2.0f * av[i] - xp;
+                                const T h = H16<BF>::from_f(xn);
+                                const T lo = H16<BF>::from_f(xn - H16<BF>::to_f(h));
+                                hb[i] = bits16(h);
+                                lb[i] = bits16(lo);
+                                if (do_rho) acc_axpy(rh[i], rl[i], al_h, al_l, xn);
+                                const bool ok_i = c >= r && c < K;
+                                if (ok_i) {
+                                    if (do_mom) {
+                                        const float wx = (c == r) ? xn : 2.0f * xn;
+                                        const float xc = H16<BF>::to_f(from_bits16<T>(chw[i >> 1] >> sh)) +
+                                                         H16<BF>::to_f(from_bits16<T>(clw[i >> 1] >> sh));
+                                        acc_prod(snn_h, snn_l, wx, xn);
+                                        acc_prod(snc_h, snc_l, wx, xc);
+                                    }
+                                    bad |= !(fabsf(xn) <= 4.0f);
+                                }
+                            }
+                            *(uint4*)rs = make_uint4(hb[0] | (lb[0] << 16), hb[1] | (lb[1] << 16), hb[2] | (lb[2] << 16),
+                                                     hb[3] | (lb[3] << 16));
+                            const size_t e = rowoff + c0;
+                            if (full) {
+                                *(uint2*)(xph + e) = make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
+                                *(uint2*)(xpl + e) = make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+                                if (do_rho) {
+                                    __stcs((float4*)(rho + e), make_float4(rh[0], rl[0], rh[1], rl[1]));
+                                    __stcs((float4*)(rho + e) + 1, make_float4(rh[2], rl[2], rh[3], rl[3]));
+                                }
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) {
+                                    const int c = c0 + i;
+                                    if (c >= r && c < K) {
+                                        xph[e + i] = from_bits16<T>(hb[i]);
+                                        xpl[e + i] = from_bits16<T>(lb[i]);
+                                        if (do_rho) rho[e + i] = make_float2(rh[i], rl[i]);
+                                    }
                                 }
                             }
                         }
                     }
                 }
-            }
-            epi_sync<NEPI>();
-            // mirror: tile column c becomes row c below the diagonal.  Each warp
-            // takes 4 tile columns at a time; lane j reads the 4 x 4 block of
-            // tile rows 4j .. 4j + 3, so every output row is one contiguous
-            // 256-byte run per part across the warp.
-            for (int lc0 = 4 * ew; lc0 < BN; lc0 += 4 * NW) {
-                if (n0 + lc0 >= K) break;
-                uint32_t v[4][4];
+                epi_sync<NEPI>();
+                // mirror: tile column c becomes row c below the diagonal.  Each warp
+                // takes 4 tile columns at a time; lane j reads the 4 x 4 block of
+                // tile rows 4j .. 4j + 3, so every output row is one contiguous
+                // 256-byte run per part across the warp.
+                for (int lc0 = 4 * ew; lc0 < BN; lc0 += 4 * NW) {
+                    if (n0 + lc0 >= K) break;
+                    uint32_t v[4][4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int lr = 4 * lane + i;
-                    const uint4 q = *(const uint4*)(Rs + lr * BN + (lc0 ^ rs_swz(lr)));
-                    v[i][0] = q.x;
-                    v[i][1] = q.y;
-                    v[i][2] = q.z;
-                    v[i][3] = q.w;
-                }
-                const int r0 = m0 + 4 * lane;
+                    for (int i = 0; i < 4; ++i) {
+                        const int lr = 4 * lane + i;
+                        const uint4 q = *(const uint4*)(Rs + lr * BN + (lc0 ^ rs_swz(lr)));
+                        v[i][0] = q.x;
+                        v[i][1] = q.y;
+                        v[i][2] = q.z;
+                        v[i][3] = q.w;
+                    }
+                    const int r0 = m0 + 4 * lane;
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int c = n0 + lc0 + t;
-                    if (c >= K) break;
-                    if (r0 >= c || r0 >= K) continue;
-                    const size_t e = (size_t)c * Kp + r0;
-                    if (r0 + 3 < c && r0 + 3 < K) {
-                        *(uint2*)(xph + e) =
-                            make_uint2((v[0][t] & 0xffffu) | (v[1][t] << 16), (v[2][t] & 0xffffu) | (v[3][t] << 16));
-                        *(uint2*)(xpl + e) = make_uint2((v[0][t] >> 16) | (v[1][t] & 0xffff0000u),
-                                                        (v[2][t] >> 16) | (v[3][t] & 0xffff0000u));
-                    } else {
+                    for (int t = 0; t < 4; ++t) {
+                        const int c = n0 + lc0 + t;
+                        if (c >= K) break;
+                        if (r0 >= c || r0 >= K) continue;
+                        const size_t e = (size_t)c * Kp + r0;
+                        if (r0 + 3 < c && r0 + 3 < K) {
+                            *(uint2*)(xph + e) =
+                                make_uint2((v[0][t] & 0xffffu) | (v[1][t] << 16), (v[2][t] & 0xffffu) | (v[3][t] << 16));
+                            *(uint2*)(xpl + e) = make_uint2((v[0][t] >> 16) | (v[1][t] & 0xffff0000u),
+                                                            (v[2][t] >> 16) | (v[3][t] & 0xffff0000u));
+                        } else {
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            if (r0 + i < c && r0 + i < K) {
-                                xph[e + i] = from_bits16<T>(v[i][t] & 0xffffu);
-                                xpl[e + i] = from_bits16<T>(v[i][t] >> 16);
+                            for (int i = 0; i < 4; ++i) {
+                                if (r0 + i < c && r0 + i < K) {
+                                    xph[e + i] = from_bits16<T>(v[i][t] & 0xffffu);
+                                    xpl[e + i] = from_bits16<T>(v[i][t] >> 16);
+                                }
                             }
                         }
                     }
                 }
+                // hand the ring back to the producer (generic accesses before its
+                // next asynchronous writes)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(epi_done);
             }
-            // hand the ring back to the producer (generic accesses before its
-            // next asynchronous writes)
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(epi_done);
             if (do_mom) {
                 double s_nn = (double)snn_h + (double)snn_l, s_nc = (double)snc_h + (double)snc_l;
                 for (int o = 16; o > 0; o >>= 1) {
@@ -1090,6 +1286,32 @@ void make_map(CUtensorMap* m, const void* base, int Kp, int box_rows, int bk) {
     if (r != CUDA_SUCCESS) throw Error(DFT_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
+// rho pairs (Kp x Kp float2) seen as a 2 Kp x Kp FP32 matrix: boxes of 32
+// floats (16 pairs, 128 bytes) by 128 rows with 128-byte swizzle
+void make_map_rho(CUtensorMap* m, const void* base, int Kp) {
+    cuuint64_t dims[2] = {(cuuint64_t)2 * Kp, (cuuint64_t)Kp};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * 8};
+    cuuint32_t box[2] = {32, 128};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error(DFT_ECUDA, "cuTensorMapEncodeTiled (rho) failed (" + std::to_string((int)r) + ")");
+}
+
+// X pair part (Kp x Kp 16-bit) with boxes of 64 columns by 32 rows, 128-byte
+// swizzle: the transposed copy of a 32-column epilogue slab
+void make_map_mirror(CUtensorMap* m, const void* base, int Kp) {
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)Kp};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    cuuint32_t box[2] = {64, 32};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error(DFT_ECUDA, "cuTensorMapEncodeTiled (mirror) failed (" + std::to_string((int)r) + ")");
+}
+
 }  // namespace tc
 
 int tc_pad(int K) { return (K + 255) / 256 * 256; }
@@ -1117,6 +1339,8 @@ void tc_setup(Ctx& c) {
         for (int q = 0; q < 4; ++q) tc::make_map(&c.tm_x[v][q], c.d_x16[q], c.Kp, 256, bk);
     }
     for (int q = 0; q < 4; ++q) tc::make_map(&c.tm_xn[q], c.d_x16[q], c.Kp, 128, 32);
+    tc::make_map_rho(&c.tm_rho, c.d_rho_tc, c.Kp);
+    for (int q = 0; q < 4; ++q) tc::make_map_mirror(&c.tm_xm[q], c.d_x16[q], c.Kp);
     static bool attr_done = false;
     if (!attr_done) {
         auto attr = [](auto kern, int bytes) {
@@ -1202,6 +1426,9 @@ TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const i
             for (int k = 0; k < 4; ++k) m[6 * v + 2 + k] = c.tm_x[v][k];
         }
         for (int k = 0; k < 4; ++k) m[12 + k] = c.tm_xn[k];
+        m[16] = c.tm_rho;
+        m[17] = c.tm_rho;
+        for (int k = 0; k < 4; ++k) m[18 + k] = c.tm_xm[k];
     }
     // one tile list per tile width; each interleaves the systems' tiles so
     // that consecutive CTAs mix large and small systems
