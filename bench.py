@@ -17,6 +17,7 @@ rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import tempfile
 import json
 import os
 import statistics
@@ -362,6 +363,19 @@ def run_reference(args, sysm, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def tuned_shape():
+    """Launch shape(s) the tuner picked in this process: {key: {bk, persist, bn, streamk, flow}}."""
+    path = os.environ.get("DFT_AUTOTUNE_CACHE")
+    if not path or not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    return {k: dict(zip(("bk", "persist", "bn", "streamk", "flow"), v[:5])) for k, v in d.items()}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -380,6 +394,9 @@ def main():
         return
     import torch
     import torch.distributed as dist
+    # the library's launch-shape tuner writes its choice here (read back for the report)
+    if "DFT_AUTOTUNE_CACHE" not in os.environ:
+        os.environ["DFT_AUTOTUNE_CACHE"] = os.path.join(tempfile.mkdtemp(prefix="dft_tune_"), "autotune.json")
     import paper_2108_13478_gb300 as dft
     torch.cuda.set_device(local)
     if world > 1:
@@ -493,6 +510,9 @@ def main():
             "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
             "stages_ms": [round(x, 3) for x in infos[-1].ms_stage],
             "energy_per_atom": infos[-1].e_total / sysm.n_atoms}
+    shape = tuned_shape()
+    if shape is not None and prec != dft.DFT_PREC_FP64:
+        line["roofline"]["launch_shape"] = shape
     if rank == 0 and not args.no_compare:
         line["mixed_vs_fp64"] = compare_precisions(dft, torch, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
