@@ -34,13 +34,13 @@ __global__ void k_build_tables(const Fn* __restrict__ fn, int K, int W, double o
     tab[idx] = val;
 }
 
-// stage the 8-point slices of FCH functions' tables for the tile at t0
-template <typename R>
+// stage the 8-point slices of NCH functions' tables for the tile at t0
+template <typename R, int NCH = FCH>
 __device__ __forceinline__ void stage_slices(const Fn* __restrict__ fn, const double* __restrict__ tab,
                                              int W, const int* __restrict__ list, int n_t, int c0,
                                              const int t0[3], R (*sx)[TILE], R (*sy)[TILE],
                                              R (*sz)[TILE]) {
-    for (int e = threadIdx.x; e < FCH * 3 * TILE; e += blockDim.x) {
+    for (int e = threadIdx.x; e < NCH * 3 * TILE; e += blockDim.x) {
         int fl = e / (3 * TILE);
         int d = (e / TILE) % 3;
         int q = e % TILE;
@@ -125,21 +125,27 @@ __global__ void __launch_bounds__(256) k_collocate(
 }
 
 // V_ab += h^3 sum_{g in tile} phi_a v phi_b for all pairs of the tile's list
-// (Eq. A.6).  Chunk pairs (ca <= cb); the off-diagonal chunk blocks are
-// mirrored.  Contributions of different tiles meet through FP64 atomics.
-constexpr int QPTS = 64;
+// (Eq. A.6).  Chunks of QCH = 64 functions, chunk pairs (ca <= cb), the
+// off-diagonal chunk blocks mirrored.  Per block of QPTS points, the values
+// phi_a(g) and v(g) phi_b(g) of both chunks are formed in shared memory once;
+// each thread then accumulates a 4 x 4 register block of pairs (a = ty + 16 i,
+// b = tx + 16 j), two shared-memory reads per four multiply-adds.  Every pair
+// sums its points in the order g = 0 .. 511.  Contributions of different
+// tiles meet through FP64 atomics.
+constexpr int QCH = 64;
 template <typename R>
 __global__ void __launch_bounds__(256) k_quadrature(
     const Fn* __restrict__ fn, const double* __restrict__ tab, int W, const int* __restrict__ tile_ptr,
     const int* __restrict__ tile_fn, int ntx, int nty, int nx, int ny, int nz, int K, double h3,
     const double* __restrict__ v, double* __restrict__ V) {
-    __shared__ R sxa[FCH][TILE], sya[FCH][TILE], sza[FCH][TILE];
-    __shared__ R sxb[FCH][TILE], syb[FCH][TILE], szb[FCH][TILE];
+    constexpr int QPTS = sizeof(R) == 4 ? 32 : 16;
+    __shared__ R sxa[QCH][TILE], sya[QCH][TILE], sza[QCH][TILE];
+    __shared__ R sxb[QCH][TILE], syb[QCH][TILE], szb[QCH][TILE];
     __shared__ R sv[TILE_PTS];
-    __shared__ R pa[QPTS][FCH + 1], pb[QPTS][FCH + 1];
+    __shared__ R pa[QPTS][QCH], pb[QPTS][QCH];
     const int t = blockIdx.x;
-    const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
-    const int t0[3] = {tx * TILE, ty * TILE, tz * TILE};
+    const int tx = t % ntx, ty_ = (t / ntx) % nty, tz = t / (ntx * nty);
+    const int t0[3] = {tx * TILE, ty_ * TILE, tz * TILE};
     const int* list = tile_fn + tile_ptr[t];
     const int n_t = tile_ptr[t + 1] - tile_ptr[t];
     if (n_t == 0) return;
@@ -147,19 +153,22 @@ __global__ void __launch_bounds__(256) k_quadrature(
         int gx = t0[0] + (p & 7), gy = t0[1] + ((p >> 3) & 7), gz = t0[2] + (p >> 6);
         sv[p] = (R)((gx < nx && gy < ny && gz < nz) ? v[((long long)gz * ny + gy) * nx + gx] : 0.0);
     }
-    const int a = threadIdx.x & 31;
-    const int b0 = (threadIdx.x >> 5) * 4;
-    for (int ca = 0; ca < n_t; ca += FCH) {
+    const int ux = threadIdx.x & 15, uy = threadIdx.x >> 4;   // b = ux + 16 j, a = uy + 16 i
+    for (int ca = 0; ca < n_t; ca += QCH) {
         __syncthreads();
-        stage_slices(fn, tab, W, list, n_t, ca, t0, sxa, sya, sza);
-        for (int cb = ca; cb < n_t; cb += FCH) {
+        stage_slices<R, QCH>(fn, tab, W, list, n_t, ca, t0, sxa, sya, sza);
+        for (int cb = ca; cb < n_t; cb += QCH) {
             __syncthreads();
-            stage_slices(fn, tab, W, list, n_t, cb, t0, sxb, syb, szb);
-            R acc[4] = {(R)0, (R)0, (R)0, (R)0};
+            stage_slices<R, QCH>(fn, tab, W, list, n_t, cb, t0, sxb, syb, szb);
+            R acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = (R)0;
             for (int p0 = 0; p0 < TILE_PTS; p0 += QPTS) {
                 __syncthreads();
-                for (int e = threadIdx.x; e < QPTS * FCH; e += blockDim.x) {
-                    int pp = e / FCH, f = e % FCH;
+                for (int e = threadIdx.x; e < QPTS * QCH; e += blockDim.x) {
+                    int pp = e / QCH, f = e % QCH;
                     int p = p0 + pp;
                     int x = p & 7, y = (p >> 3) & 7, z = p >> 6;
                     pa[pp][f] = sxa[f][x] * sya[f][y] * sza[f][z];
@@ -168,21 +177,30 @@ __global__ void __launch_bounds__(256) k_quadrature(
                 __syncthreads();
 #pragma unroll 4
                 for (int pp = 0; pp < QPTS; ++pp) {
-                    R va = pa[pp][a];
+                    R va[4], vb[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[q] = fma(va, pb[pp][b0 + q], acc[q]);
+                    for (int i = 0; i < 4; ++i) va[i] = pa[pp][uy + 16 * i];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) vb[j] = pb[pp][ux + 16 * j];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fma(va[i], vb[j], acc[i][j]);
                 }
             }
-            if (ca + a < n_t) {
-                int fa = list[ca + a];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (cb + b0 + q < n_t) {
-                        int fb = list[cb + b0 + q];
-                        double val = h3 * (double)acc[q];
-                        atomicAdd(&V[(long long)fa * K + fb], val);
-                        if (ca != cb) atomicAdd(&V[(long long)fb * K + fa], val);
-                    }
+            for (int i = 0; i < 4; ++i) {
+                const int la = ca + uy + 16 * i;
+                if (la >= n_t) continue;
+                const int fa = list[la];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int lb = cb + ux + 16 * j;
+                    if (lb >= n_t) continue;
+                    const int fb = list[lb];
+                    const double val = h3 * (double)acc[i][j];
+                    atomicAdd(&V[(long long)fa * K + fb], val);
+                    if (ca != cb) atomicAdd(&V[(long long)fb * K + fa], val);
                 }
             }
         }
