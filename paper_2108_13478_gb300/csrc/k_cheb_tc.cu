@@ -373,6 +373,32 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Epilogue slabs of off-diagonal 256-wide tiles: 32 columns x 128 rows of the
+// X_{l-1} pair (2 x 8 KB) and the rho pairs (2 x 16 KB) or the X_l pair
+// (2 x 8 KB), 48 KB per buffer.  Buffer b (half b / 2, slab parity b % 2)
+// lies in the ring stages that follow the tile's last k-block (gend), so the
+// producer can fill each as soon as the MMAs have freed its stage.
+constexpr int SLAB_BYTES = 48 * 1024;
+template <int STAGES, int STAGE_BYTES>
+__device__ __forceinline__ uint8_t* slab_buf(uint8_t* smem, long long gend, int b) {
+    constexpr int NBS = STAGE_BYTES >= SLAB_BYTES ? STAGE_BYTES / SLAB_BYTES : 1;   // slab buffers per stage
+    return smem + (int)((gend + b / NBS) % STAGES) * STAGE_BYTES + (b % NBS) * SLAB_BYTES;
+}
+__device__ __forceinline__ void slab_load(uint8_t* bf, uint64_t* bar, const CUtensorMap* mx, const CUtensorMap* mr,
+                                          int cur, bool do_rho, bool do_mom, int x, int y) {
+    mbar_expect_tx(bar, do_rho ? 49152u : (do_mom ? 32768u : 16384u));
+    tma_load_2d(bf, mx + 2 * (1 - cur), x, y, bar);
+    tma_load_2d(bf + 8192, mx + 2 * (1 - cur) + 1, x, y, bar);
+    if (do_rho) {
+        tma_load_2d(bf + 16384, mr, 2 * x, y, bar);
+        tma_load_2d(bf + 32768, mr, 2 * x + 32, y, bar);
+    }
+    if (do_mom) {
+        tma_load_2d(bf + 16384, mx + 2 * cur, x, y, bar);
+        tma_load_2d(bf + 24576, mx + 2 * cur + 1, x, y, bar);
+    }
+}
+
 __device__ __forceinline__ int ld_acquire(const int* p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -497,11 +523,6 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 const TcSys& S = sys[tl.sys];
                 const int l = cu.l, cur = cu.cur;
                 if (l >= S.lim) continue;
-                if (nfin > 0 && !mbar_wait(epi_done, (uint32_t)((nfin - 1) & 1))) {
-                    // the previous tile's epilogue still holds the ring
-                    *abort_flag = 1;
-                    break;
-                }
                 const CUtensorMap* mp = maps + TC_MAPS_PER_SYS * tl.sys + (BK == 64 ? 6 : 0);
                 // X operand maps: 256-row boxes beside the H maps, or the 128-row set
                 const CUtensorMap* mb = BN == 128 ? maps + TC_MAPS_PER_SYS * tl.sys + 12 : mp + 2;
@@ -509,9 +530,10 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 const int nk = (S.K + BK - 1) / BK;
                 const int nchunk = (nk + GK - 1) / GK;
                 const int kend = min(nk, cu.q1(nchunk) * GK);
-                // dataflow: one batch of relaxed reads of the block counters this
-                // tile needs (chunks below 64), then one acquire fence; only the
-                // chunks not complete yet are waited for one by one below
+                // dataflow: relaxed reads of the block counters this tile needs
+                // (chunks below 64), then one acquire fence; only the chunks not
+                // complete yet are waited for one by one below.  This runs while
+                // the previous tile's epilogue still holds the ring.
                 unsigned long long rmask = 0;
                 if (fl && cu.s > 0) {
                     const int nch = min(nchunk, 64);
@@ -530,6 +552,11 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                     }
                     asm volatile("fence.acq_rel.gpu;" ::: "memory");
                     asm volatile("fence.proxy.async.global;" ::: "memory");
+                }
+                if (nfin > 0 && !mbar_wait(epi_done, (uint32_t)((nfin - 1) & 1))) {
+                    // the previous tile's epilogue still holds the ring
+                    *abort_flag = 1;
+                    break;
                 }
                 for (int kb = cu.q0() * GK; kb < kend; ++kb, ++g) {
                     const int s = (int)(g % STAGES);
@@ -562,6 +589,24 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                     tma_load_2d(sAl(s), mp + 1, kb * BK, m0, &full[s]);
                     tma_load_2d(sBh(s), mb + 2 * cur, kb * BK, n0, &full[s]);
                     tma_load_2d(sBl(s), mb + 1 + 2 * cur, kb * BK, n0, &full[s]);
+                }
+                if (!sk && BN == 256 && (tl.i >> 1) != tl.j && !(do_rho && do_mom) && nchunk >= 2 && !*abort_flag) {
+                    // the first slab of every epilogue buffer, each as soon as the
+                    // MMAs have freed its stage
+                    constexpr int NBS = STAGE_BYTES >= SLAB_BYTES ? STAGE_BYTES / SLAB_BYTES : 1;
+                    const CUtensorMap* mxs = maps + TC_MAPS_PER_SYS * tl.sys + 12;
+                    const CUtensorMap* mrs = maps + TC_MAPS_PER_SYS * tl.sys + 16;
+                    for (int b = 0; b < 4; ++b) {
+                        if (b % NBS == 0) {
+                            const long long gv = g + b / NBS;
+                            if (!mbar_wait(&empty[gv % STAGES], (uint32_t)(((gv / STAGES) & 1) ^ 1))) {
+                                *abort_flag = 1;
+                                break;
+                            }
+                        }
+                        slab_load(slab_buf<STAGES, STAGE_BYTES>(smem, g, b), &ebar[b], mxs, mrs, cur, do_rho, do_mom,
+                                  n0 + 128 * (b >> 1) + 32 * (b & 1), m0);
+                    }
                 }
                 if (!sk || cu.q0() == 0) ++nfin;
             }
@@ -634,7 +679,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
         // ---- epilogue warps: quadrant = warp % 4 (tensor-memory lane group), half = 128-column group ----
         const int quad = warp & 3;
         const int half = (warp - 2) >> 2;
-        long long qg = 0;
+        long long qg = 0, gk = 0;
         bool ok = true;
         bool bad = false;
         const int et = threadIdx.x - 64;   // epilogue thread index
@@ -648,6 +693,8 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             const int nchunk = ((S.K + BK - 1) / BK + GK - 1) / GK;
             const int qa = cu.q0(), qb = cu.q1(nchunk);
             const int m0 = tl.i * BM, n0 = tl.j * BN;
+            gk += min((S.K + BK - 1) / BK, qb * GK) - qa * GK;   // ring position after this tile's k-blocks
+            const long long gend = gk;
             float R[CPT];
 #pragma unroll
             for (int i = 0; i < CPT; ++i) R[i] = 0.0f;
@@ -780,43 +827,26 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             const size_t Kp = (size_t)S.Kp;
             // Off-diagonal tiles (block row i / 2 < block column j) lie wholly above
             // the diagonal and inside the Kp x Kp buffers, so whole boxes move: the
-            // sums stay in registers (thread = tile row, 128 columns), and each
-            // half of the epilogue streams its four 32-column slabs (X_{l-1} pair,
-            // rho pairs or X_l pair; 48 KB) through two ring buffers with TMA
-            // loads, updates them in place and TMA-stores them back; the mirror
-            // goes out from registers, one contiguous 64-byte run per warp and
-            // column.  Diagonal tiles take the masked path below.
+            // sums go back to tensor memory, and each half of the epilogue streams
+            // its four 32-column slabs (X_{l-1} pair, rho pairs or X_l pair; 48 KB)
+            // through two ring buffers (the producer loads the first slab of each,
+            // see slab_buf), updates them in place and TMA-stores them back; the
+            // mirror of each slab is staged in shared memory for a TMA store.
+            // Diagonal tiles take the masked path below.
             if (fast) {
                 const int r_loc = 32 * quad + lane;
                 const bool th = (et & 127) == 0;   // issues this half's bulk copies
                 const CUtensorMap* mx = maps + TC_MAPS_PER_SYS * tl.sys + 12;   // X pairs, 32 x 128 boxes
                 const CUtensorMap* mr = maps + TC_MAPS_PER_SYS * tl.sys + 16;   // rho pairs
                 const CUtensorMap* mm = maps + TC_MAPS_PER_SYS * tl.sys + 18;   // X pairs, 64 x 32 boxes
-                constexpr int SLAB = 48 * 1024;
-                static_assert(BN != 256 || 4 * SLAB <= STAGES * STAGE_BYTES, "slab buffers exceed the ring");
-                const uint32_t slab_bytes = do_rho ? 49152u : (do_mom ? 32768u : 16384u);
+                static_assert(BN != 256 || 4 * SLAB_BYTES <= STAGES * STAGE_BYTES, "slab buffers exceed the ring");
+                // the producer loaded the first slab of both buffers of each half
+                // (see slab_buf); this half's issuing thread loads the other two
                 auto issue_load = [&](int sl) {
-                    uint8_t* bf = smem + (2 * half + (sl & 1)) * SLAB;
-                    uint64_t* bar = &ebar[2 * half + (sl & 1)];
-                    const int x = n0 + 128 * half + 32 * sl;
-                    mbar_expect_tx(bar, slab_bytes);
-                    tma_load_2d(bf, mx + 2 * (1 - cur), x, m0, bar);
-                    tma_load_2d(bf + 8192, mx + 2 * (1 - cur) + 1, x, m0, bar);
-                    if (do_rho) {
-                        tma_load_2d(bf + 16384, mr, 2 * x, m0, bar);
-                        tma_load_2d(bf + 32768, mr, 2 * x + 32, m0, bar);
-                    }
-                    if (do_mom) {
-                        tma_load_2d(bf + 16384, mx + 2 * cur, x, m0, bar);
-                        tma_load_2d(bf + 24576, mx + 2 * cur + 1, x, m0, bar);
-                    }
+                    const int b = 2 * half + (sl & 1);
+                    slab_load(slab_buf<STAGES, STAGE_BYTES>(smem, gend, b), &ebar[b], mx, mr, cur, do_rho, do_mom,
+                              n0 + 128 * half + 32 * sl, m0);
                 };
-                // the slab loads read only this tile's own positions: they go out
-                // before anything else, ahead of the wait for the block's readers
-                if (th) {
-                    issue_load(0);
-                    issue_load(1);
-                }
                 // the final sums go back to tensor memory (both chunk accumulators
                 // stay idle until this tile hands the ring back), freeing registers
                 const uint32_t tacc = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(half * CPT);
@@ -831,7 +861,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 bool got_all = true, war_ok = true;
 #pragma unroll 1
                 for (int sl = 0; sl < 4; ++sl) {
-                    uint8_t* bf = smem + (2 * half + (sl & 1)) * SLAB;
+                    uint8_t* bf = slab_buf<STAGES, STAGE_BYTES>(smem, gend, 2 * half + (sl & 1));
                     got_all &= mbar_wait(&ebar[2 * half + (sl & 1)], (uint32_t)((sl >> 1) & 1));
                     uint32_t av[32];
                     tmem_ld32(tacc + 32 * sl, av);
