@@ -49,7 +49,7 @@ struct TcTile {
 };
 constexpr int TC_MAX_SYS = 64;
 constexpr int TC_SK_MAX_CTAS = 256;   // stream-K grid bound (one 128 KB partial-sum slot per CTA)
-constexpr int TC_MAPS_PER_SYS = 22;   // H, X (k-block 32 / 64), X 128-row, rho, spare, X mirror boxes
+constexpr int TC_MAPS_PER_SYS = 26;   // H, X (k-block 32 / 64), X 128-row, rho, spare, X mirror and slab boxes
 constexpr int TC_LISTS = 3;           // tile lists: 256-wide, 128-wide, 256-wide in block order (dataflow)
 
 // Dataflow pass: steps l0 .. l0 + nsteps - 1 in one persistent launch; X_l is
@@ -137,7 +137,8 @@ struct Ctx {
     CUtensorMap tm_x[2][4];      // per k-block variant (32 or 64 wide)
     CUtensorMap tm_xn[4];        // X maps with 128-row boxes (128-wide tiles, 32-wide k-blocks; epilogue slabs)
     CUtensorMap tm_rho;          // rho pairs as FP32, 32 x 128 boxes (16 pairs per row), 128-byte swizzle
-    CUtensorMap tm_xm[4];        // X maps with 64 x 32 boxes, 128-byte swizzle (mirror of an epilogue slab)
+    CUtensorMap tm_xm[4];        // X maps with 64 x 16 boxes, 128-byte swizzle (mirror of an epilogue slab)
+    CUtensorMap tm_xs[4];        // X maps with 16 x 128 boxes, 32-byte swizzle (epilogue slabs)
     // batch area (device): system table, tensor maps (16 per system), tile
     // lists of both tile widths
     TcSys* d_systab = nullptr;

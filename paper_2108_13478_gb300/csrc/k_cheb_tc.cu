@@ -373,29 +373,27 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Epilogue slabs of off-diagonal 256-wide tiles: 32 columns x 128 rows of the
-// X_{l-1} pair (2 x 8 KB) and the rho pairs (2 x 16 KB) or the X_l pair
-// (2 x 8 KB), 48 KB per buffer.  Buffer b (half b / 2, slab parity b % 2)
-// lies in the ring stages that follow the tile's last k-block (gend), so the
-// producer can fill each as soon as the MMAs have freed its stage.
-constexpr int SLAB_BYTES = 48 * 1024;
+// Epilogue slabs of off-diagonal 256-wide tiles: 16 columns x 128 rows of the
+// X_{l-1} pair (2 x 4 KB, 32-byte swizzle) and the rho pairs (16 KB, 128-byte
+// swizzle) or the X_l pair (2 x 4 KB), 24 KB per buffer, four buffers per
+// 128-column half.  Buffer b (half b / 4, slot b % 4) lies in the ring stages
+// that follow the tile's last k-block (gend), so the producer can fill each as
+// soon as the MMAs have freed its stage.
+constexpr int SLAB_BYTES = 24 * 1024;
 template <int STAGES, int STAGE_BYTES>
 __device__ __forceinline__ uint8_t* slab_buf(uint8_t* smem, long long gend, int b) {
     constexpr int NBS = STAGE_BYTES >= SLAB_BYTES ? STAGE_BYTES / SLAB_BYTES : 1;   // slab buffers per stage
     return smem + (int)((gend + b / NBS) % STAGES) * STAGE_BYTES + (b % NBS) * SLAB_BYTES;
 }
-__device__ __forceinline__ void slab_load(uint8_t* bf, uint64_t* bar, const CUtensorMap* mx, const CUtensorMap* mr,
+__device__ __forceinline__ void slab_load(uint8_t* bf, uint64_t* bar, const CUtensorMap* mxs, const CUtensorMap* mr,
                                           int cur, bool do_rho, bool do_mom, int x, int y) {
-    mbar_expect_tx(bar, do_rho ? 49152u : (do_mom ? 32768u : 16384u));
-    tma_load_2d(bf, mx + 2 * (1 - cur), x, y, bar);
-    tma_load_2d(bf + 8192, mx + 2 * (1 - cur) + 1, x, y, bar);
-    if (do_rho) {
-        tma_load_2d(bf + 16384, mr, 2 * x, y, bar);
-        tma_load_2d(bf + 32768, mr, 2 * x + 32, y, bar);
-    }
+    mbar_expect_tx(bar, do_rho ? 24576u : (do_mom ? 16384u : 8192u));
+    tma_load_2d(bf, mxs + 2 * (1 - cur), x, y, bar);
+    tma_load_2d(bf + 4096, mxs + 2 * (1 - cur) + 1, x, y, bar);
+    if (do_rho) tma_load_2d(bf + 8192, mr, 2 * x, y, bar);
     if (do_mom) {
-        tma_load_2d(bf + 16384, mx + 2 * cur, x, y, bar);
-        tma_load_2d(bf + 24576, mx + 2 * cur + 1, x, y, bar);
+        tma_load_2d(bf + 8192, mxs + 2 * cur, x, y, bar);
+        tma_load_2d(bf + 12288, mxs + 2 * cur + 1, x, y, bar);
     }
 }
 
@@ -467,11 +465,11 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
     uint64_t* accempty = accfull + 2;
     uint64_t* drain = accempty + 2;
     uint64_t* epi_done = drain + 1;   // epilogue finished with the ring (staged sums)
-    uint64_t* ebar = epi_done + 1;    // [4] epilogue slab loads (off-diagonal tiles)
-    uint32_t* tmem_slot = (uint32_t*)(ebar + 4);
+    uint64_t* ebar = epi_done + 1;    // [8] epilogue slab loads (off-diagonal tiles)
+    uint32_t* tmem_slot = (uint32_t*)(ebar + 8);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     double* red = (double*)(mirbuf + C::MIR_BYTES + 256);   // 2 x 8 moment partials + 1 flag
-    static_assert((2 * STAGES + 10) * 8 + 8 <= 256, "barriers overlap the reduction slots");
+    static_assert((2 * STAGES + 14) * 8 + 8 <= 256, "barriers overlap the reduction slots");
     // staged FP32 sums of a finished tile, over the operand ring
     static_assert(BM * BN * 4 <= STAGES * STAGE_BYTES, "staged tile does not fit the ring");
     float* Rs = (float*)smem;
@@ -490,7 +488,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
         }
         mbar_init(drain, 1);
         mbar_init(epi_done, NEPI);
-        for (int b = 0; b < 4; ++b) mbar_init(&ebar[b], 1);
+        for (int b = 0; b < 8; ++b) mbar_init(&ebar[b], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -594,9 +592,9 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                     // the first slab of every epilogue buffer, each as soon as the
                     // MMAs have freed its stage
                     constexpr int NBS = STAGE_BYTES >= SLAB_BYTES ? STAGE_BYTES / SLAB_BYTES : 1;
-                    const CUtensorMap* mxs = maps + TC_MAPS_PER_SYS * tl.sys + 12;
+                    const CUtensorMap* mxs = maps + TC_MAPS_PER_SYS * tl.sys + 22;
                     const CUtensorMap* mrs = maps + TC_MAPS_PER_SYS * tl.sys + 16;
-                    for (int b = 0; b < 4; ++b) {
+                    for (int b = 0; b < 8; ++b) {
                         if (b % NBS == 0) {
                             const long long gv = g + b / NBS;
                             if (!mbar_wait(&empty[gv % STAGES], (uint32_t)(((gv / STAGES) & 1) ^ 1))) {
@@ -605,7 +603,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                             }
                         }
                         slab_load(slab_buf<STAGES, STAGE_BYTES>(smem, g, b), &ebar[b], mxs, mrs, cur, do_rho, do_mom,
-                                  n0 + 128 * (b >> 1) + 32 * (b & 1), m0);
+                                  n0 + 128 * (b >> 2) + 16 * (b & 3), m0);
                     }
                 }
                 if (!sk || cu.q0() == 0) ++nfin;
@@ -836,16 +834,16 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             if (fast) {
                 const int r_loc = 32 * quad + lane;
                 const bool th = (et & 127) == 0;   // issues this half's bulk copies
-                const CUtensorMap* mx = maps + TC_MAPS_PER_SYS * tl.sys + 12;   // X pairs, 32 x 128 boxes
-                const CUtensorMap* mr = maps + TC_MAPS_PER_SYS * tl.sys + 16;   // rho pairs
-                const CUtensorMap* mm = maps + TC_MAPS_PER_SYS * tl.sys + 18;   // X pairs, 64 x 32 boxes
-                static_assert(BN != 256 || 4 * SLAB_BYTES <= STAGES * STAGE_BYTES, "slab buffers exceed the ring");
-                // the producer loaded the first slab of both buffers of each half
-                // (see slab_buf); this half's issuing thread loads the other two
+                const CUtensorMap* mxs = maps + TC_MAPS_PER_SYS * tl.sys + 22;   // X pairs, 16 x 128 boxes
+                const CUtensorMap* mr = maps + TC_MAPS_PER_SYS * tl.sys + 16;    // rho pairs, 16 x 128 boxes
+                const CUtensorMap* mm = maps + TC_MAPS_PER_SYS * tl.sys + 18;    // X pairs, 64 x 16 boxes
+                static_assert(BN != 256 || 8 * SLAB_BYTES <= STAGES * STAGE_BYTES, "slab buffers exceed the ring");
+                // the producer loaded slabs 0 .. 3 of both halves (see slab_buf);
+                // this half's issuing thread loads slabs 4 .. 7 into the same slots
                 auto issue_load = [&](int sl) {
-                    const int b = 2 * half + (sl & 1);
-                    slab_load(slab_buf<STAGES, STAGE_BYTES>(smem, gend, b), &ebar[b], mx, mr, cur, do_rho, do_mom,
-                              n0 + 128 * half + 32 * sl, m0);
+                    const int b = 4 * half + (sl & 3);
+                    slab_load(slab_buf<STAGES, STAGE_BYTES>(smem, gend, b), &ebar[b], mxs, mr, cur, do_rho, do_mom,
+                              n0 + 128 * half + 16 * sl, m0);
                 };
                 // the final sums go back to tensor memory (both chunk accumulators
                 // stay idle until this tile hands the ring back), freeing registers
@@ -853,34 +851,37 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
 #pragma unroll
                 for (int cc = 0; cc < CPT / 16; ++cc) tmem_st16(tacc + 16 * cc, &R[16 * cc]);
                 tmem_wait_st();
-                const int xsw = (r_loc >> 1) & 3, rsw = r_loc & 7;   // 64- and 128-byte swizzle of this row
-                // mirror of this thread's row: column r_loc of the 32 x 128 mirror
-                // boxes (box r_loc / 64, 128-byte swizzle on the 16-byte chunk)
-                uint8_t* mb = mirbuf + half * 16384 + (r_loc >> 6) * 4096;
+                const int xsw = (r_loc >> 2) & 1, rsw = r_loc & 7;   // 32- and 128-byte swizzle of this row
+                // mirror of a slab: 16 rows (the slab's columns) x 128 columns (the
+                // tile's rows) per part, two 64-column boxes, double-buffered per half;
+                // this thread writes column r_loc (128-byte swizzle on the 16-byte chunk)
                 const int rb = (r_loc & 63) * 2;
                 bool got_all = true, war_ok = true;
 #pragma unroll 1
-                for (int sl = 0; sl < 4; ++sl) {
-                    uint8_t* bf = slab_buf<STAGES, STAGE_BYTES>(smem, gend, 2 * half + (sl & 1));
-                    got_all &= mbar_wait(&ebar[2 * half + (sl & 1)], (uint32_t)((sl >> 1) & 1));
-                    uint32_t av[32];
-                    tmem_ld32(tacc + 32 * sl, av);
+                for (int sl = 0; sl < 8; ++sl) {
+                    uint8_t* bf = slab_buf<STAGES, STAGE_BYTES>(smem, gend, 4 * half + (sl & 3));
+                    uint8_t* mb = mirbuf + (2 * half + (sl & 1)) * 8192;
+                    uint8_t* mbt = mb + (r_loc >> 6) * 2048;
+                    got_all &= mbar_wait(&ebar[4 * half + (sl & 3)], (uint32_t)((sl >> 2) & 1));
+                    uint32_t av[16];
+                    tmem_ld16(tacc + 16 * sl, av);
 #pragma unroll
-                    for (int c8 = 0; c8 < 4; ++c8) {
-                        uint4* hp = (uint4*)(bf + r_loc * 64 + ((c8 ^ xsw) << 4));
-                        uint4* lp = (uint4*)(bf + 8192 + r_loc * 64 + ((c8 ^ xsw) << 4));
+                    for (int c8 = 0; c8 < 2; ++c8) {
+                        const int xo = r_loc * 32 + ((c8 ^ xsw) << 4);
+                        uint4* hp = (uint4*)(bf + xo);
+                        uint4* lp = (uint4*)(bf + 4096 + xo);
                         const uint4 hv = *hp, lv = *lp;
                         uint4 chv = make_uint4(0, 0, 0, 0), clv = chv;
                         if (do_mom) {
-                            chv = *(const uint4*)(bf + 16384 + r_loc * 64 + ((c8 ^ xsw) << 4));
-                            clv = *(const uint4*)(bf + 24576 + r_loc * 64 + ((c8 ^ xsw) << 4));
+                            chv = *(const uint4*)(bf + 8192 + xo);
+                            clv = *(const uint4*)(bf + 12288 + xo);
                         }
-                        // rho pairs of these 8 columns: box c8 / 2, 16-byte chunks 4 (c8 & 1) .. + 3
-                        uint8_t* rrow = bf + 16384 + (c8 >> 1) * 16384 + r_loc * 128;
+                        // rho pairs of these 8 columns: 16-byte chunks 4 c8 .. 4 c8 + 3 of the row
+                        uint8_t* rrow = bf + 8192 + r_loc * 128;
                         float4 rv[4];
                         if (do_rho)
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) rv[k] = *(const float4*)(rrow + (((4 * (c8 & 1) + k) ^ rsw) << 4));
+                            for (int k = 0; k < 4; ++k) rv[k] = *(const float4*)(rrow + (((4 * c8 + k) ^ rsw) << 4));
                         const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
                         const uint32_t chw[4] = {chv.x, chv.y, chv.z, chv.w}, clw[4] = {clv.x, clv.y, clv.z, clv.w};
                         uint32_t ho[4], lo_[4];
@@ -911,20 +912,27 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                                 acc_prod(snc_h, snc_l, 2.0f * xn, xc);
                             }
                             bad |= !(fabsf(xn) <= 4.0f);
-                            // mirror row c = 8 c8 + e of the slab, column r_loc
                             const int cm = 8 * c8 + e;
                             const int mo = cm * 128 + ((((rb >> 4) ^ (cm & 7))) << 4) + (rb & 15);
-                            *(T*)(mb + mo) = h;
-                            *(T*)(mb + 8192 + mo) = lo;
+                            *(T*)(mbt + mo) = h;
+                            *(T*)(mbt + 4096 + mo) = lo;
                         }
                         *hp = make_uint4(ho[0], ho[1], ho[2], ho[3]);
                         *lp = make_uint4(lo_[0], lo_[1], lo_[2], lo_[3]);
                         if (do_rho)
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) *(float4*)(rrow + (((4 * (c8 & 1) + k) ^ rsw) << 4)) = rv[k];
+                            for (int k = 0; k < 4; ++k) *(float4*)(rrow + (((4 * c8 + k) ^ rsw) << 4)) = rv[k];
                     }
                     // the half's generic writes of this slab before its bulk stores
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    if (th && sl >= 1) {
+                        // the previous slab's stores have read their buffers: the
+                        // next slab may refill its mirror buffer, and its data slot
+                        // takes slab sl + 3
+                        bulk_wait_read0();
+                        if (sl == 1) asm volatile("fence.proxy.async.global;" ::: "memory");
+                        if (sl + 3 < 8) issue_load(sl + 3);
+                    }
                     asm volatile("bar.sync %0, 128;" ::"r"(2 + half) : "memory");
                     if (th) {
                         if (sl == 0 && fl && cu.s > 0) {
@@ -935,30 +943,19 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                             war_ok = wait_count(flow.cnt + S.cnt_off + (2 - cur) * S.npair + pair_idx(p, q, S.nb),
                                                 rd * ((cu.s + 1) / 2), flags);
                         }
-                        const int x = n0 + 128 * half + 32 * sl;
+                        const int x = n0 + 128 * half + 16 * sl;
                         if (war_ok) {
-                            // mirror: rows x .. x + 31, columns m0 .. m0 + 127 (two boxes per part)
-                            tma_store_2d(mm + 2 * (1 - cur), m0, x, mirbuf + half * 16384);
-                            tma_store_2d(mm + 2 * (1 - cur), m0 + 64, x, mirbuf + half * 16384 + 4096);
-                            tma_store_2d(mm + 2 * (1 - cur) + 1, m0, x, mirbuf + half * 16384 + 8192);
-                            tma_store_2d(mm + 2 * (1 - cur) + 1, m0 + 64, x, mirbuf + half * 16384 + 12288);
+                            // mirror: rows x .. x + 15, columns m0 .. m0 + 127 (two boxes per part)
+                            tma_store_2d(mm + 2 * (1 - cur), m0, x, mb);
+                            tma_store_2d(mm + 2 * (1 - cur), m0 + 64, x, mb + 2048);
+                            tma_store_2d(mm + 2 * (1 - cur) + 1, m0, x, mb + 4096);
+                            tma_store_2d(mm + 2 * (1 - cur) + 1, m0 + 64, x, mb + 6144);
+                            tma_store_2d(mxs + 2 * (1 - cur), x, m0, bf);
+                            tma_store_2d(mxs + 2 * (1 - cur) + 1, x, m0, bf + 4096);
+                            if (do_rho) tma_store_2d(mr, 2 * x, m0, bf + 8192);
                             bulk_commit();
-                            tma_store_2d(mx + 2 * (1 - cur), x, m0, bf);
-                            tma_store_2d(mx + 2 * (1 - cur) + 1, x, m0, bf + 8192);
-                            if (do_rho) {
-                                tma_store_2d(mr, 2 * x, m0, bf + 16384);
-                                tma_store_2d(mr, 2 * x + 32, m0, bf + 32768);
-                            }
-                            bulk_commit();
-                        }
-                        if (sl + 2 < 4) {
-                            bulk_wait_read0();   // slab and mirror buffers free again
-                            issue_load(sl + 2);
-                        } else {
-                            bulk_wait_read1();   // mirror buffer free again
                         }
                     }
-                    asm volatile("bar.sync %0, 128;" ::"r"(2 + half) : "memory");
                 }
                 if (th) {
                     bulk_wait0();
@@ -1311,7 +1308,8 @@ void make_map(CUtensorMap* m, const void* base, int Kp, int box_rows, int bk) {
     cuuint32_t es[2] = {1, 1};
     CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                             bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                      : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) throw Error(DFT_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
@@ -1329,12 +1327,12 @@ void make_map_rho(CUtensorMap* m, const void* base, int Kp) {
     if (r != CUDA_SUCCESS) throw Error(DFT_ECUDA, "cuTensorMapEncodeTiled (rho) failed (" + std::to_string((int)r) + ")");
 }
 
-// X pair part (Kp x Kp 16-bit) with boxes of 64 columns by 32 rows, 128-byte
-// swizzle: the transposed copy of a 32-column epilogue slab
+// X pair part (Kp x Kp 16-bit) with boxes of 64 columns by 16 rows, 128-byte
+// swizzle: half the transposed copy of a 16-column epilogue slab
 void make_map_mirror(CUtensorMap* m, const void* base, int Kp) {
     cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)Kp};
     cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-    cuuint32_t box[2] = {64, 32};
+    cuuint32_t box[2] = {64, 16};
     cuuint32_t es[2] = {1, 1};
     CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -1371,6 +1369,7 @@ void tc_setup(Ctx& c) {
     for (int q = 0; q < 4; ++q) tc::make_map(&c.tm_xn[q], c.d_x16[q], c.Kp, 128, 32);
     tc::make_map_rho(&c.tm_rho, c.d_rho_tc, c.Kp);
     for (int q = 0; q < 4; ++q) tc::make_map_mirror(&c.tm_xm[q], c.d_x16[q], c.Kp);
+    for (int q = 0; q < 4; ++q) tc::make_map(&c.tm_xs[q], c.d_x16[q], c.Kp, 128, 16);
     static bool attr_done = false;
     if (!attr_done) {
         auto attr = [](auto kern, int bytes) {
@@ -1459,6 +1458,7 @@ TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const i
         m[16] = c.tm_rho;
         m[17] = c.tm_rho;
         for (int k = 0; k < 4; ++k) m[18 + k] = c.tm_xm[k];
+        for (int k = 0; k < 4; ++k) m[22 + k] = c.tm_xs[k];
     }
     // one tile list per tile width; each interleaves the systems' tiles so
     // that consecutive CTAs mix large and small systems
