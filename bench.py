@@ -169,9 +169,9 @@ def cpu_baseline(sysm, budget_s):
 
 def run_batched(args, rank, world):
     """Ragged batch: every SCF step advances all systems with one
-    dft_scf_step_batched call (one tensor-core launch per recurrence step for
-    the whole batch, graph-captured loops).  Value = sum of K over systems x
-    steps / time."""
+    dft_scf_step_batched call (the tensor-core recurrence of the whole batch
+    as one launch per step in a CUDA graph, or one dataflow launch per pass,
+    whichever the tuner picks).  Value = sum of K over systems x steps / time."""
     import torch
     import torch.distributed as dist
     import paper_2108_13478_gb300 as dft
