@@ -22,8 +22,14 @@
 // the epilogue warps (four per 128 columns, one per tensor-memory lane
 // quadrant) add every finished chunk into FP32 registers with round-to-nearest
 // (so no accumulation chain in the tensor core is longer than one chunk) and
-// then run the fused update.  Every wait is bounded in time: on expiry the CTA
-// records FLAG_TIMEOUT, drains what it issued and returns.
+// then run the fused update: off-diagonal tiles stream 16-column slabs of
+// X_{l-1} and rho (or X_l) through the idle ring with TMA loads and stores and
+// TMA-store the mirror from shared memory; diagonal tiles use masked vector
+// loads and stores.  Launch shapes: one CTA per tile per step, a persistent
+// grid, stream-K chunk ranges, or the dataflow launch that runs a whole pass
+// in one cooperative launch with per-block counters between steps.  Every wait
+// is bounded in time: on expiry the CTA records FLAG_TIMEOUT, drains what it
+// issued and returns.
 #include "dft_internal.cuh"
 
 #include <cuda.h>
