@@ -363,6 +363,13 @@ def run_reference(args, sysm, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes per recurrence step of the weighted pass, from one ncu capture of
+# the dataflow launch on the 465-atom sphere (dram__bytes_read.sum +
+# dram__bytes_write.sum over its 2882 steps); quoted only for the workload and
+# launch shape it was taken on, and to be removed when the kernel changes
+MEASURED_TRAFFIC = {("sphere25", 1): (2527.7e9 + 573.3e9) / 2882}
+
+
 def tuned_shape():
     """Launch shape(s) the tuner picked in this process: {key: {bk, persist, bn, streamk, flow}}."""
     path = os.environ.get("DFT_AUTOTUNE_CACHE")
@@ -513,6 +520,13 @@ def main():
     shape = tuned_shape()
     if shape is not None and prec != dft.DFT_PREC_FP64:
         line["roofline"]["launch_shape"] = shape
+        flows = {v.get("flow", 0) for v in shape.values()}
+        if len(flows) == 1:
+            tr = MEASURED_TRAFFIC.get((sysm.name, flows.pop()))
+            if tr is not None:
+                line["roofline"]["traffic"] = tr
+                line["roofline"]["traffic_note"] = "DRAM bytes per recurrence step (ncu, dataflow launch)"
+
     if rank == 0 and not args.no_compare:
         line["mixed_vs_fp64"] = compare_precisions(dft, torch, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
