@@ -53,19 +53,27 @@ __global__ void k_take_real(long long n, const cufftDoubleComplex* c, double sca
     if (e < n) r[e] = c[e].x * scale;
 }
 
-// padded[z][y][x] = n - n_ion inside the box, 0 outside
-__global__ void k_pad(int nx, int ny, int nz, int Nx, int Ny, int Nz, const double* __restrict__ n,
-                      const double* __restrict__ nion, double* __restrict__ out) {
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long tot = (long long)Nx * Ny * Nz;
-    if (e >= tot) return;
-    int ix = (int)(e % Nx), iy = (int)((e / Nx) % Ny), iz = (int)(e / ((long long)Nx * Ny));
-    double v = 0.0;
-    if (ix < nx && iy < ny && iz < nz) {
-        long long g = ((long long)iz * ny + iy) * nx + ix;
-        v = n[g] - (nion ? nion[g] : 0.0);
+// padded[z][y][x] = n - n_ion inside the box, 0 outside.  Block (bx, y, zb)
+// covers x = 128 bx + thread on the line (y, z) for PAD_Z consecutive z, so
+// no index is divided and every block writes PAD_Z x 1 KB.
+constexpr int PAD_Z = 8;
+__global__ void __launch_bounds__(128) k_pad(int nx, int ny, int nz, int Nx, int Ny, int Nz,
+                                             const double* __restrict__ n, const double* __restrict__ nion,
+                                             double* __restrict__ out) {
+    const int ix = blockIdx.x * 128 + threadIdx.x, iy = blockIdx.y;
+    if (ix >= Nx) return;
+    const bool in_xy = ix < nx && iy < ny;
+#pragma unroll
+    for (int k = 0; k < PAD_Z; ++k) {
+        const int iz = blockIdx.z * PAD_Z + k;
+        if (iz >= Nz) break;
+        double v = 0.0;
+        if (in_xy && iz < nz) {
+            const long long g = ((long long)iz * ny + iy) * nx + ix;
+            v = n[g] - (nion ? nion[g] : 0.0);
+        }
+        out[((long long)iz * Ny + iy) * Nx + ix] = v;
     }
-    out[e] = v;
 }
 
 __global__ void k_mul_real(long long n, cufftDoubleComplex* c, const double* __restrict__ w) {
@@ -79,18 +87,32 @@ __global__ void k_mul_real(long long n, cufftDoubleComplex* c, const double* __r
 
 constexpr double CX = 0.98474502184269641;   // (3/pi)^(1/3)
 
+// d^(1/3) for d > 1e-30: an FP32 estimate, then one Newton step for
+// y^3 - d = 0 in FP64, y1 = y0 - (y0^3 - d) / (3 y0^2), with 1 / y0^2 taken in
+// FP32 (the correction is ~1e-7 y0, so its own relative error of ~1e-7 leaves
+// ~1e-14).  Four FP64 operations instead of a full FP64 cube root on GB300's
+// narrow FP64 pipe.
+__device__ __forceinline__ double cbrt_pos(double d) {
+    const float yf = cbrtf((float)d);
+    const double y0 = (double)yf;
+    const double r = (double)(1.0f / (yf * yf));
+    const double t = fma(y0 * y0, y0, -d);
+    return fma(-t * r, 1.0 / 3.0, y0);
+}
+
 // v_ks = v_loc + v_H + v_x; energy partials sum v_loc n, v_H rho, eps_x n
 __global__ void __launch_bounds__(256) k_vks(int nx, int ny, int nz, int Nx, int Ny, const double* __restrict__ pad,
                                              const double* __restrict__ n, const double* __restrict__ nion,
                                              const double* __restrict__ vloc, double* __restrict__ vks,
                                              double* __restrict__ part) {
-    long long ng = (long long)nx * ny * nz;
+    const int ng = nx * ny * nz;   // below 2^31 for every grid here (274^3 = 2.1e7)
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (long long g = (long long)blockIdx.x * 256 + threadIdx.x; g < ng; g += (long long)gridDim.x * 256) {
-        int ix = (int)(g % nx), iy = (int)((g / nx) % ny), iz = (int)(g / ((long long)nx * ny));
+    for (int g = blockIdx.x * 256 + threadIdx.x; g < ng; g += gridDim.x * 256) {
+        const int line = g / nx, ix = g - line * nx;
+        const int iz = line / ny, iy = line - iz * ny;
         double vh = pad[((long long)iz * Ny + iy) * Nx + ix];
         double d = n[g];
-        double c = d > 1e-30 ? CX * cbrt(d) : 0.0;
+        double c = d > 1e-30 ? CX * cbrt_pos(d) : 0.0;
         double vx = -c, ex = -0.75 * c;
         double vl = vloc[g];
         if (vks) vks[g] = vl + vh + vx;
@@ -183,11 +205,19 @@ __global__ void __launch_bounds__(256) k_ring_dots(long long ng, int m, const do
     double acc[PMAX];
 #pragma unroll
     for (int i = 0; i < PMAX; ++i) acc[i] = 0.0;
-    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < ng; e += (long long)gridDim.x * 256) {
-        double r = rn[e];
+    // two grid points per iteration, so each thread has 2 (m + 1) loads in flight
+    const long long stride = (long long)gridDim.x * 512;
+    for (long long e = (long long)blockIdx.x * 512 + threadIdx.x; e < ng; e += stride) {
+        const long long e2 = e + 256;
+        const bool two = e2 < ng;
+        const double r = rn[e], r2 = two ? rn[e2] : 0.0;
 #pragma unroll
         for (int i = 0; i < PMAX; ++i)
-            if (i < m) acc[i] = fma(ring[(long long)i * ng + e], r, acc[i]);
+            if (i < m) {
+                const double* ri = ring + (long long)i * ng;
+                const double a = ri[e], b = two ? ri[e2] : 0.0;
+                acc[i] = fma(b, r2, fma(a, r, acc[i]));
+            }
     }
 #pragma unroll
     for (int i = 0; i < PMAX; ++i) {
@@ -251,8 +281,8 @@ void hartree_xc(Ctx& c, const double* n, double* vks, bool energies, cudaStream_
     const double* nion = c.p.model == DFT_MODEL_NEUTRAL ? c.d_nion : nullptr;
     cufft_check(cufftSetStream(c.plan_f, s), "stream");
     cufft_check(cufftSetStream(c.plan_b, s), "stream");
-    k_pad<<<blocks_for(c.nfft_r, 256), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.Nfft[2], n,
-                                                     nion, c.d_fft_r);
+    k_pad<<<dim3((unsigned)((c.Nfft[0] + 127) / 128), (unsigned)c.Nfft[1], (unsigned)((c.Nfft[2] + PAD_Z - 1) / PAD_Z)),
+            128, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.Nfft[2], n, nion, c.d_fft_r);
     check_launch("pad");
     cufft_check(cufftExecD2Z(c.plan_f, c.d_fft_r, c.d_fft_c), "exec D2Z");
     k_mul_real<<<blocks_for(c.nfft_c, 256), 256, 0, s>>>(c.nfft_c, c.d_fft_c, c.d_ghat);
