@@ -211,13 +211,9 @@ def run_batched(args, rank, world):
         ms.append(e0.elapsed_time(e1))
     launches = (dft.dft_kernel_launches() - l0) / args.steps
     clocks = sampler.stop()
-    total_ms = sum(ms)
-    t = torch.tensor([total_ms], device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms), world, f"cuda:{local}")
     ksum = sum(c.K for c in ctxs)
-    value = world * ksum * args.steps / (total_ms / 1000.0)
+    value = job_throughput(world, ksum, args.steps, total_ms)
     n_c = [i.n_cheb for i in infos]
     line = {"metric": METRIC, "value": value, "unit": "P-columns/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -370,6 +366,23 @@ def run_reference(args, sysm, rank, world):
 MEASURED_TRAFFIC = {("sphere25", 1): (2527.7e9 + 573.3e9) / 2882}
 
 
+def max_over_ranks(value, world, device):
+    """The largest of the ranks' values: the job is as slow as its slowest rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, steps, max_ms):
+    """Units all ranks processed per second (weak scaling: every rank runs the
+    same workload), timed by the slowest rank."""
+    return world * units_per_rank * steps / (max_ms / 1000.0)
+
+
 def tuned_shape():
     """Launch shape(s) the tuner picked in this process: {key: {bk, persist, bn, streamk, flow}}."""
     path = os.environ.get("DFT_AUTOTUNE_CACHE")
@@ -446,13 +459,9 @@ def main():
     barrier()
     launches = (dft.dft_kernel_launches() - launches0) / args.steps
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, f"cuda:{local}")
     K = ctx.K
-    value = world * K * args.steps / (total_ms / 1000.0)
+    value = job_throughput(world, K, args.steps, total_ms)
     # end to end through the public API with host buffers: pinned n_in -> device,
     # step, next density and energies back to the host
     n_host = torch.empty(ctx.grid_shape, dtype=torch.float64, pin_memory=True)
@@ -472,10 +481,7 @@ def main():
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
         n_host.copy_(out_host)
-    t = torch.tensor([e2e_ms], device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * K * args.steps / (float(t.item()) / 1000.0)
+    e2e_value = job_throughput(world, K, args.steps, max_over_ranks(e2e_ms, world, f"cuda:{local}"))
     # roofline of the dominant kernel: the Chebyshev step (one launch per term of pass 2)
     pk = peaks()
     n_c = infos[-1].n_cheb

@@ -1,0 +1,70 @@
+"""The benchmark's multi-rank bookkeeping on CPU ranks (gloo, world size 2).
+
+With N GPUs the benchmark runs one replica of the workload per rank (the
+path needs no collective); the job is timed by its slowest rank and its
+throughput is the units of all ranks over that time.  The reference arm runs
+on rank 0 only.  These are the host-side parts of the N > 1 path, exercised
+here with two gloo ranks on 127.0.0.1.
+"""
+import os
+import socket
+import sys
+import types
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, local_ms, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        m = bench.max_over_ranks(local_ms[rank], world, "cpu")
+        q.put((rank, m, bench.job_throughput(world, 4650, 3, m)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_are_timed_by_the_slowest():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    local_ms = [1200.0, 955.5]
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, local_ms, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs)
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, m, v in res:
+        assert m == 1200.0
+        assert v == pytest.approx(2 * 4650 * 3 / 1.2)
+
+
+def test_one_rank_needs_no_process_group():
+    assert bench.max_over_ranks(7.5, 1, "cpu") == 7.5
+    assert bench.job_throughput(1, 640, 2, 500.0) == pytest.approx(2560.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys):
+    import workloads as w
+    args = types.SimpleNamespace(warmup=0, steps=1, cpu_budget=1.0, gpus=2)
+    bench.run_reference(args, w.config_system("tiny8"), rank=1, world=2)
+    assert capsys.readouterr().out == ""
