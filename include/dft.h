@@ -32,9 +32,14 @@
  *    tuned per (precision, size bucket, batch size); read at the first
  *    tuned launch, rewritten after each tuning.
  *  - DFT_AUTOTUNE_OFF: any value disables tuning (the default shape runs).
- *  - DFT_TC_SHAPE="bk,persist,bn": forces one launch shape (k-block 32 or
- *    64; 0 = one CTA per tile, 1 or 2 = that many persistent CTAs per SM;
- *    tile width 256, or 128 with bk = 32) and disables tuning.  Malformed
+ *  - DFT_TC_SHAPE="bk,persist,bn[,streamk[,pf[,epf[,flow]]]]": forces one
+ *    launch shape and disables tuning: k-block 32 or 64; 0 = one CTA per
+ *    tile, 1 or 2 = that many persistent CTAs per SM; tile width 256, or 128
+ *    with bk = 32; streamk 1 = equal chunk ranges per CTA on a cooperative
+ *    grid (256-wide tiles); pf = L2 prefetch distance of operand k-blocks
+ *    (0 .. 64); epf 1 = L2 prefetch of the epilogue's rows; flow 1 = one
+ *    cooperative launch per recurrence pass, tiles of consecutive steps
+ *    ordered by per-block counters (256-wide tiles, no stream-K).  Malformed
  *    values are ignored.
  */
 #ifndef DFT_H
