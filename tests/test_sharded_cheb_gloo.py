@@ -94,7 +94,9 @@ def _rank_main(rank, world, port, n_e, beta, n_c, q):
 
 
 @pytest.mark.parametrize("world", [2, 3, 5])
-def test_column_shards_reproduce_the_unsharded_density_matrix(world):
+def test_column_shards_reproduce_the_unsharded_density_matrix(world, monkeypatch):
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        monkeypatch.setenv(var, "1")                 # one BLAS thread per rank process
     F, S, lo, hi = _problem()
     K = F.shape[0]
     n_e, beta = 20.0, 8.0
@@ -109,10 +111,11 @@ def test_column_shards_reproduce_the_unsharded_density_matrix(world):
     procs = [ctx.Process(target=_rank_main, args=(r, world, port, n_e, beta, n_c, q)) for r in range(world)]
     for p in procs:
         p.start()
+    # drain the queue before joining: a child does not exit until what it put is read
+    res = [q.get(timeout=180) for _ in range(world)]
     for p in procs:
-        p.join(timeout=180)
+        p.join(timeout=60)
     assert all(p.exitcode == 0 for p in procs)
-    res = [q.get(timeout=10) for _ in range(world)]
     for rank, mu, P in res:
         assert abs(mu - ref["mu"]) < 1e-10
         assert np.max(np.abs(P - ref["P"])) < 1e-10 * max(1.0, np.max(np.abs(ref["P"])))
