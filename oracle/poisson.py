@@ -61,7 +61,7 @@ def hartree(sysm, rho, c0=None):
         G = np.where(r > 0, 1.0 / np.where(r > 0, r, 1.0), c0 / h)
     pad = np.zeros((Nz, Ny, Nx))
     pad[:nz, :ny, :nx] = rho
-    v = np.fft.irfftn(np.fft.rfftn(pad) * np.fft.rfftn(G), s=(Nz, Ny, Nx))
+    v = np.fft.irfftn(np.fft.rfftn(pad) * np.fft.rfftn(G), s=(Nz, Ny, Nx), axes=(0, 1, 2))
     return h ** 3 * v[:nz, :ny, :nx]
 
 

@@ -135,3 +135,30 @@ def test_cheb_dm_mu_and_count():
     # exact and truncated DMs agree once the expansion has converged
     ex = dm.dm_exact(F, S, 14.0, 6.0)
     assert np.max(np.abs(ex["P"] - r["P"])) < 1e-9
+
+
+def test_doubling_moments_equal_direct_traces():
+    """T_m T_n = (T_{m+n} + T_{|m-n|}) / 2 gives m_{2l} = 2 <X_l, X_l> - m_0 and
+    m_{2l+1} = 2 <X_{l+1}, X_l> - m_1 from the first half of the recurrence
+    (Supp. B's moments, the doubling the moments pass relies on); they must
+    equal the oracle's moments taken from the eigenvalues."""
+    K, n_half = 21, 30
+    F, S = random_pair(K, 11)
+    eps = dm.geneig(F, S)[0]
+    lo, hi = eps[0] - 0.2, eps[-1] + 0.3
+    L = np.linalg.cholesky(S)
+    Li = np.linalg.inv(L)
+    HN = (Li @ F @ Li.T - 0.5 * (hi + lo) * np.eye(K)) / (0.5 * (hi - lo))
+    X = [np.eye(K), HN.copy()]
+    for _ in range(2, n_half + 1):
+        X.append(2 * HN @ X[-1] - X[-2])
+    m0, m1 = float(K), float(np.trace(HN))
+    dbl = np.zeros(2 * n_half)
+    for l in range(n_half):
+        dbl[2 * l] = 2 * np.sum(X[l] * X[l]) - m0
+        dbl[2 * l + 1] = 2 * np.sum(X[l + 1] * X[l]) - m1
+    x = (eps - 0.5 * (hi + lo)) / (0.5 * (hi - lo))
+    ref = dm.moments_from_eigs(x, 2 * n_half)
+    assert np.max(np.abs(dbl - ref)) < 1e-10 * K
+    # and against the cosine form on [-1, 1]: T_l(cos t) = cos(l t)
+    assert np.max(np.abs(ref - np.cos(np.outer(np.arange(2 * n_half), np.arccos(x))).sum(1))) < 1e-10 * K

@@ -158,3 +158,51 @@ def test_band_energy_double_counting_identity():
     r = scf.step(st, n0)
     V = r["F"] - st.T
     assert abs(2 * np.sum(r["P"] * V) - s.grid_h ** 3 * np.sum(r["v"] * r["n_out"])) < 1e-9
+
+
+def test_poisson_far_field_and_linearity():
+    """Far from a compact charge Q the potential tends to Q/|r - r_c| (r_c its
+    centroid), with the quadrupole remainder falling like 1/r^3; the solve is
+    linear in the charge."""
+    s = w.make_system(np.array([[0.0, 0.0, 0.0]]), h=0.4, pad=6.0)
+    nx, ny, nz = (int(t) for t in s.grid_n)
+    rng = np.random.default_rng(7)
+    rho = np.zeros((nz, ny, nx))
+    c = [n // 2 for n in (nz, ny, nx)]
+    rho[c[0] - 2:c[0] + 3, c[1] - 2:c[1] + 3, c[2] - 2:c[2] + 3] = rng.uniform(0.0, 1.0, (5, 5, 5))
+    h3 = s.grid_h ** 3
+    Q = h3 * rho.sum()
+    xs, ys, zs = scf.grid_points(s)
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    rc = np.array([np.sum(rho * X), np.sum(rho * Y), np.sum(rho * Z)]) * h3 / Q
+    d = np.sqrt((X - rc[0]) ** 2 + (Y - rc[1]) ** 2 + (Z - rc[2]) ** 2)
+    v = poisson.hartree(s, rho)
+    rel = np.abs(v * d / Q - 1.0)
+    far, mid = d > 9.0, (d > 4.0) & (d < 5.0)
+    assert rel[far].max() < 2e-3
+    assert rel[far].max() < rel[mid].max()
+    rho2 = rng.normal(size=rho.shape)
+    v2 = poisson.hartree(s, rho2)
+    v3 = poisson.hartree(s, 1.5 * rho - 2.0 * rho2)
+    assert np.max(np.abs(v3 - (1.5 * v - 2.0 * v2))) < 1e-12 * np.max(np.abs(v3))
+
+
+def test_energy_invariant_under_quarter_turn():
+    """A 90-degree turn of the atoms about z, on a grid centred on the axis
+    with equal x and y sizes, maps the grid, the windows and the s/p shells
+    onto themselves: one SCF step's energy is unchanged and the density turns
+    with the atoms."""
+    h, n = 0.4, 43
+    xyz = np.array([[0.0, 0.0, 0.0], [2.3, 0.7, -0.4], [-1.1, 1.9, 0.8]])
+    c = 0.5 * (n - 1) * h
+    nz = int(math.ceil((1.2 + 12.0) / h)) + 1
+    org = np.array([-c, -c, -0.4 - 6.0])
+    s1 = w.make_system(xyz, h=h, grid_n=np.array([n, n, nz]), grid_origin=org)
+    rot = np.stack([-xyz[:, 1], xyz[:, 0], xyz[:, 2]], 1)
+    s2 = w.make_system(rot, h=h, grid_n=np.array([n, n, nz]), grid_origin=org)
+    r1 = scf.step(scf.setup(s1), scf.ion_density(s1))
+    r2 = scf.step(scf.setup(s2), scf.ion_density(s2))
+    assert abs(r1["E"]["total"] - r2["E"]["total"]) < 1e-9 * abs(r1["E"]["total"])
+    # point (x, y) of the first grid is point (-y, x) of the second
+    n1, n2 = r1["n_out"], r2["n_out"]
+    assert np.max(np.abs(n2 - n1[:, ::-1, :].transpose(0, 2, 1))) < 1e-10 * np.max(n1)
