@@ -206,3 +206,29 @@ def test_energy_invariant_under_quarter_turn():
     # point (x, y) of the first grid is point (-y, x) of the second
     n1, n2 = r1["n_out"], r2["n_out"]
     assert np.max(np.abs(n2 - n1[:, ::-1, :].transpose(0, 2, 1))) < 1e-10 * np.max(n1)
+
+
+@pytest.mark.parametrize("neutral", [False, True])
+def test_energy_gradient_is_the_fock_matrix(neutral):
+    """The Kohn-Sham potential is the functional derivative of the energy
+    (Eq. 2.6 from the energy terms): for n = n[P] the directional derivative
+    of E(P) along a symmetric D is 2 Tr[D F[n(P)]], F = T + V[v_KS].  A
+    wrong Hartree factor, an exchange potential that is not d(n eps_x)/dn or
+    a wrong sign on the ionic charge all break it."""
+    xyz = np.array([[0.0, 0.0, 0.0], [2.3, 0.7, -0.4], [-1.1, 1.9, 0.8]])
+    s = w.make_system(xyz, h=0.4)
+    st = scf.setup(s, scf.Model(neutral=neutral))
+    r = scf.step(st, scf.ion_density(s))
+    P = r["P"]
+    K = P.shape[0]
+    rng = np.random.default_rng(5)
+    A = rng.normal(size=(K, K)) * 0.02
+    for D in (P, A + A.T):
+        def E(eps):
+            Pe = P + eps * D
+            return scf.energy(st, Pe, grid_ops.density_on_grid(s, Pe, st.model.eta))["total"]
+        eps = 1e-4
+        fd = (E(eps) - E(-eps)) / (2 * eps)
+        v, _, _ = scf.potential(st, grid_ops.density_on_grid(s, P, st.model.eta))
+        an = 2.0 * float(np.sum(D * scf.fock(st, v)))
+        assert abs(fd - an) < 1e-6 * max(1.0, abs(an)), (fd, an)
