@@ -18,6 +18,8 @@ Modules
               expansion and recurrence (Supp. B), mu bisection (Eq. 2.8)
   poisson     free-space Hartree potential by zero-padded FFT, Slater exchange
   scf         local pseudopotential, initial density, energy, SCF cycle (A.3)
+  warmstart   atom-centred descriptor, MLP, start-potential assembly and
+              their gradients (the learned warm start; not in the paper)
 
 Parity status: every function is pinned by the `-m "not gpu"` tests in
 tests/test_oracle_*.py against closed forms, brute force or library routines;
