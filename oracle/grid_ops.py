@@ -44,6 +44,46 @@ def potential_matrix(sysm, v, eta=1e-10, windowed=True, planes=4):
     return V * sysm.grid_h ** 3
 
 
+def potential_matrix_separable(sysm, factors, eta=1e-10, windowed=True, absolute=False):
+    """V_ab of Eq. 2.5 / A.6 for a potential that is a sum of products of
+    one-dimensional factors, v(x, y, z) = sum_r fx_r(x) fy_r(y) fz_r(z).
+
+    Each function is a product of one-dimensional tabulated factors inside a
+    box window (Supp. A.1), so the grid sum factorises per axis:
+    V = h^3 sum_r Vx_r o Vy_r o Vz_r (elementwise product) with
+    Vd_r[a, b] = sum_i tab_d[i, a] fd_r[i] tab_d[i, b].  This reaches the
+    same V as potential_matrix on the full grid at a cost that stays small
+    for thousands of functions.  factors: list of (fx, fy, fz) arrays of
+    lengths (nx, ny, nz).  absolute=True sums the absolute values of the
+    terms instead, h^3 sum_g |phi_a| |v| |phi_b|: the scale of a rounding-error
+    bound on V_ab."""
+    fn = basis.functions(sysm)
+    tabs = basis.axis_tables(sysm, fn, eta if windowed else None)
+    if absolute:
+        tabs = [np.abs(t) for t in tabs]
+        factors = [tuple(np.abs(np.asarray(f, dtype=np.float64)) for f in fr) for fr in factors]
+    K = len(fn["zeta"])
+    V = np.zeros((K, K))
+    for fr in factors:
+        # grid lines where a factor vanishes and functions that vanish on
+        # every remaining line add exact zeros; leave them out
+        rows = [np.nonzero(np.asarray(fr[d]))[0] for d in range(3)]
+        live = np.ones(K, dtype=bool)
+        for d in range(3):
+            live &= np.any(tabs[d][rows[d]] != 0.0, axis=0)
+        idx = np.nonzero(live)[0]
+        if idx.size == 0:
+            continue
+        term = None
+        for d in range(3):
+            f = np.asarray(fr[d], dtype=np.float64)[rows[d]]
+            t = tabs[d][np.ix_(rows[d], idx)]
+            q = t.T @ (f[:, None] * t)
+            term = q if term is None else np.multiply(term, q, out=term)
+        V[np.ix_(idx, idx)] += term
+    return V * sysm.grid_h ** 3
+
+
 def density_on_grid(sysm, P, eta=1e-10, windowed=True, planes=4):
     """n(r_g) = 2 sum_ab P_ab phi_a(r_g) phi_b(r_g)  (Eq. 2.7), evaluated as
     the column sum of Eq. A.5: n = sum_a 2 phi_a sum_b phi_b P_ba.
@@ -68,11 +108,15 @@ def phi_points(sysm, fn, tabs, flat_idx):
     return tabs[0][ix] * tabs[1][iy] * tabs[2][iz]
 
 
-def density_at(sysm, P, flat_idx, eta=1e-10, windowed=True):
-    """n at selected flat grid indices (Eq. 2.7), for sampled checks."""
+def density_at(sysm, P, flat_idx, eta=1e-10, windowed=True, absolute=False):
+    """n at selected flat grid indices (Eq. 2.7), for sampled checks.
+    absolute=True sums the absolute values of the terms,
+    2 sum_ab |phi_a| |P_ab| |phi_b|: the scale of a rounding-error bound on n."""
     fn = basis.functions(sysm)
     tabs = basis.axis_tables(sysm, fn, eta if windowed else None)
     ph = phi_points(sysm, fn, tabs, flat_idx)
+    if absolute:
+        ph, P = np.abs(ph), np.abs(P)
     return 2.0 * np.einsum("ga,ga->g", ph @ P, ph)
 
 

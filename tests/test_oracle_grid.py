@@ -93,6 +93,13 @@ def test_density_count_and_pair_density(tiny):
     # sampled evaluation agrees with the full grid
     pick = rng.integers(0, n.size, 40)
     assert np.max(np.abs(grid_ops.density_at(s, P, pick) - n.ravel()[pick])) < 1e-12
+    # the absolute-term sum bounds |n|, and equals n for a nonnegative P on s functions
+    A = grid_ops.density_at(s, P, pick, absolute=True)
+    assert np.all(A >= np.abs(n.ravel()[pick]) - 1e-13)
+    sfun = np.nonzero(fn["l"] == 0)[0]
+    Ps = np.zeros((K, K))
+    Ps[np.ix_(sfun, sfun)] = np.abs(P[np.ix_(sfun, sfun)])
+    assert np.max(np.abs(grid_ops.density_at(s, Ps, pick, absolute=True) - grid_ops.density_at(s, Ps, pick))) < 1e-13
 
 
 def test_cube_constant_closed_form():
@@ -232,3 +239,31 @@ def test_energy_gradient_is_the_fock_matrix(neutral):
         v, _, _ = scf.potential(st, grid_ops.density_on_grid(s, P, st.model.eta))
         an = 2.0 * float(np.sum(D * scf.fock(st, v)))
         assert abs(fd - an) < 1e-6 * max(1.0, abs(an)), (fd, an)
+
+
+def test_separable_quadrature_equals_grid_sum(tiny):
+    """The factorised quadrature of a sum of separable potentials equals the
+    plain grid sum of Eq. 2.5 over the same windows (and without them)."""
+    s, fn, _, _ = tiny
+    nx, ny, nz = (int(t) for t in s.grid_n)
+    rng = np.random.default_rng(9)
+    factors = [tuple(rng.normal(size=n) for n in (nx, ny, nz)) for _ in range(2)]
+    # a factor that vanishes on most lines, so that whole functions drop out
+    band = [np.where(np.abs(np.arange(n) - n // 3) < 3, rng.normal(size=n), 0.0) for n in (nx, ny, nz)]
+    factors.append(tuple(band))
+    v = sum(np.einsum("z,y,x->zyx", fz, fy, fx) for fx, fy, fz in factors)
+    for windowed in (True, False):
+        ref = grid_ops.potential_matrix(s, v, windowed=windowed)
+        got = grid_ops.potential_matrix_separable(s, factors, windowed=windowed)
+        assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+    # the sum of absolute terms bounds |V| and equals it where no term is
+    # negative (s functions are positive; a positive one-term potential)
+    A = grid_ops.potential_matrix_separable(s, factors, absolute=True)
+    assert np.all(A >= np.abs(got) - 1e-13 * np.max(A))
+    pos = [tuple(np.abs(f) for f in factors[0])]
+    sfun = np.nonzero(fn["l"] == 0)[0]
+    Vp = grid_ops.potential_matrix_separable(s, pos)[np.ix_(sfun, sfun)]
+    Ap = grid_ops.potential_matrix_separable(s, pos, absolute=True)[np.ix_(sfun, sfun)]
+    assert np.max(np.abs(Ap - Vp)) < 1e-13 * np.max(Ap)
+    assert np.max(np.abs(grid_ops.potential_matrix_separable(s, pos, absolute=True) -
+                         grid_ops.potential_matrix_separable(s, pos))) > 1e-6   # p functions change sign
