@@ -818,11 +818,12 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             // Off-diagonal tiles (block row i / 2 < block column j) lie wholly above
             // the diagonal and inside the Kp x Kp buffers, so whole boxes move: the
             // sums go back to tensor memory, and each half of the epilogue streams
-            // its four 32-column slabs (X_{l-1} pair, rho pairs or X_l pair; 48 KB)
-            // through two ring buffers (the producer loads the first slab of each,
-            // see slab_buf), updates them in place and TMA-stores them back; the
-            // mirror of each slab is staged in shared memory for a TMA store.
-            // Diagonal tiles take the masked path below.
+            // its eight 16-column slabs (X_{l-1} pair with the rho pairs or the X_l
+            // pair; 24 KB each) through four ring buffers (the producer loads the
+            // first four, see slab_buf), updates them in place and TMA-stores them
+            // back; the mirror of each slab is staged in one of two shared-memory
+            // buffers per half for a TMA store.  Diagonal tiles take the masked
+            // path below.
             if (fast) {
                 const int r_loc = 32 * quad + lane;
                 const bool th = (et & 127) == 0;   // issues this half's bulk copies
