@@ -112,3 +112,39 @@ def test_product_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), f
                 assert "oracle/" not in txt, f
+
+
+def _desc(dft, s):
+    """Descriptors of a workload system; the arrays are kept alive on the returned tuple."""
+    arrs = (np.ascontiguousarray(s.xyz), np.ascontiguousarray(s.shell_atom, np.int32),
+            np.ascontiguousarray(s.shell_l, np.int32), np.ascontiguousarray(s.shell_exp))
+    b = dft.dft_basis_desc()
+    b.n_atoms, b.n_shells = s.n_atoms, len(arrs[1])
+    b.xyz = arrs[0].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    b.shell_atom = arrs[1].ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    b.shell_l = arrs[2].ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    b.shell_exp = arrs[3].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    g = dft.dft_grid_desc()
+    for d in range(3):
+        g.origin[d] = s.grid_origin[d]
+        g.n[d] = int(s.grid_n[d])
+    g.h = s.grid_h
+    return b, g, arrs
+
+
+@pytest.mark.parametrize("name,lo_gb,hi_gb", [("sphere25", 2.0, 3.5), ("sphere40", 25.0, 64.0)])
+def test_workspace_of_the_large_workloads_fits_one_gpu(built, name, lo_gb, hi_gb):
+    """The mixed-precision workspace (K x K FP64 matrices, 16-bit operand
+    pairs padded to 256, rho pairs, grids and the padded FFT grid) of the
+    465- and 1963-atom spheres: a few GB and a few tens of GB of the
+    GPU's 284 GB (host-side sizing, no device needed)."""
+    import paper_2108_13478_gb300 as dft
+    import workloads as w
+    s = w.config_system(name)
+    b, g, _keep = _desc(dft, s)
+    p = dft.make_params(kT=s.kT, n_electrons=s.n_electrons, precision=dft.DFT_PREC_FP16X3)
+    nb = dft.dft_workspace_bytes(b, g, p)
+    K = s.n_basis
+    Kp = -(-K // 256) * 256
+    assert nb >= 8 * K * K * 8 + 4 * Kp * Kp * 2      # at least the FP64 matrices and the operand pairs
+    assert lo_gb * 1e9 < nb < hi_gb * 1e9
