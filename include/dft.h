@@ -194,15 +194,20 @@ dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double
 
 /* One SCF cycle for each of n independent systems (at most 64), e.g.
  * clusters of uneven basis size.  Every context must use the same mixed
- * precision (DFT_PREC_FP16X3 or DFT_PREC_BF16X3).  The per-system stages run
- * one after another on `stream`; the two Chebyshev passes of all systems are
- * merged: one persistent tensor-core launch per recurrence step walks the
- * tiles of every system still inside its own N_C, so ragged K share the SMs.
- * The launch sequences of both passes are captured once in CUDA graphs and
- * replayed while the step counts stay the same.  ctxs[0] holds the batch
- * tables (system table, tensor maps, up to 131072 tiles) and the graphs.
- * n_in_out[q]: device density of system q, updated as by dft_scf_step;
- * infos (host, may be NULL) receives n results (stage times are shared). */
+ * precision (DFT_PREC_FP16X3 or DFT_PREC_BF16X3) and appear once.  The
+ * per-system stages (potential, Fock matrix, bounds and N_C before the
+ * recurrence; back-transform, collocation, energy and mixing after it) run
+ * concurrently on per-context streams driven by host threads and are joined
+ * to `stream`.  The two Chebyshev passes of all systems are merged into
+ * tensor-core launches over the tiles of every system still inside its own
+ * N_C, so ragged K share the SMs: one cooperative launch per pass with the
+ * dataflow launch shape; otherwise one launch per recurrence step, captured
+ * once in a CUDA graph and replayed while the step counts stay the same.
+ * ctxs[0] holds the batch tables (system table, tensor maps, tile lists)
+ * and the graphs.  n_in_out[q]: device density of system q, updated as by
+ * dft_scf_step; infos (host, may be NULL) receives n results (stage times
+ * are shared).  DFT_EINVAL for an FP64 context, mixed precisions or a
+ * context given twice. */
 dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in_out, dft_info* infos,
                                 void* stream);
 

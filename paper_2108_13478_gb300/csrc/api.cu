@@ -883,7 +883,8 @@ dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in
             dm_prepare(c, c.d_F, as, nullptr, 0);
         });
         tm.mark(1);
-        // one persistent launch per recurrence step for all systems: moments pass
+        // moments pass over all systems: one dataflow launch, or one launch per
+        // step replayed from a CUDA graph
         std::vector<int> lim(n), last(n);
         int Jmax = 0, Lmax = 0;
         for (int q = 0; q < n; ++q) {
