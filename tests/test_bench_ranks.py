@@ -68,3 +68,26 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     args = types.SimpleNamespace(warmup=0, steps=1, cpu_budget=1.0, gpus=2)
     bench.run_reference(args, w.config_system("tiny8"), rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_keeps_the_contract(capsys):
+    """Rank 0 prints one JSON line with the contract's keys: the oracle's
+    throughput, its time per step, a CPU-baseline record and an end-to-end
+    record without host-device copies."""
+    import json
+    import workloads as w
+    s = w.config_system("tiny8")
+    args = types.SimpleNamespace(warmup=1, steps=2, cpu_budget=1.0, gpus=1)
+    bench.run_reference(args, s, rank=0, world=1)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] == pytest.approx(1000.0 * s.n_basis / d["value"])
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "tiny8"
