@@ -54,3 +54,23 @@ def test_pulay_solves_affine_fixed_point_in_dim_plus_one_steps():
     for _ in range(dim + 2):
         n_lin = scf.linear_mix(0.5)(n_lin, M @ n_lin + c)
     assert np.max(np.abs(n_lin - n_star)) > 1e-3
+
+
+def test_gaussian_fields_of_one_atom():
+    """Ionic charge and local potential of a lone atom: the charge sums to 4 e
+    (a Gaussian of width 1.5 bohr sampled at h = 0.4 sums to its integral to
+    roundoff, by the Poisson summation formula), the potential is -4 Ha at the
+    nucleus and falls as exp(-r^2 / 1.5^2)."""
+    import workloads as w
+    s = w.make_system(np.array([[0.0, 0.0, 0.0]]), h=0.4, pad=8.0)
+    n = scf.ion_density(s)
+    assert abs(s.grid_h ** 3 * n.sum() - 4.0) < 1e-10
+    v = scf.vloc(s)
+    nx, ny, nz = (int(t) for t in s.grid_n)
+    c = (nz // 2, ny // 2, nx // 2)
+    xs, ys, zs = scf.grid_points(s)
+    assert abs(xs[c[2]]) < 1e-12 and abs(ys[c[1]]) < 1e-12 and abs(zs[c[0]]) < 1e-12
+    assert abs(v[c] + 4.0) < 1e-14
+    r = xs[c[2] + 5]                                    # 2 bohr along x
+    assert abs(v[c[0], c[1], c[2] + 5] + 4.0 * np.exp(-r * r / 2.25)) < 1e-14
+    assert abs(n[c] - 4.0 * (np.pi * 2.25) ** -1.5) < 1e-14

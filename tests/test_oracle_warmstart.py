@@ -63,3 +63,22 @@ def test_gradient_matches_central_differences():
         Lm, _ = ws.loss_and_grad(theta - e, s, v_start, v_target)
         fd = (Lp - Lm) / 2e-5
         assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(fd)), (idx, fd, g[idx])
+
+
+def test_assembly_of_one_radial_gaussian():
+    """One atom with a single nonzero coefficient c_k = 1 contributes
+    exp(-r^2 / w_k^2) inside the 12-bohr cut and nothing beyond it."""
+    import workloads as w
+    s = w.make_system(np.array([[0.0, 0.0, 0.0]]), h=0.5, pad=13.0)
+    k = 9
+    c = np.zeros((1, ws.N_OUT))
+    c[0, k] = 1.0
+    v = ws.assemble(s, c)
+    nx, ny, nz = (int(t) for t in s.grid_n)
+    o, h = s.grid_origin, s.grid_h
+    Z, Y, X = np.meshgrid(o[2] + h * np.arange(nz), o[1] + h * np.arange(ny), o[0] + h * np.arange(nx), indexing="ij")
+    r2 = X * X + Y * Y + Z * Z
+    wk = ws.widths()[k]
+    ref = np.where(r2 < 144.0, np.exp(-r2 / (wk * wk)), 0.0)
+    assert np.max(np.abs(v - ref)) < 1e-15
+    assert abs(wk - 0.5 * 6.0 ** (k / 15)) < 1e-15
