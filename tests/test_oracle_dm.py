@@ -162,3 +162,22 @@ def test_doubling_moments_equal_direct_traces():
     assert np.max(np.abs(dbl - ref)) < 1e-10 * K
     # and against the cosine form on [-1, 1]: T_l(cos t) = cos(l t)
     assert np.max(np.abs(ref - np.cos(np.outer(np.arange(2 * n_half), np.arccos(x))).sum(1))) < 1e-10 * K
+
+
+def test_empty_and_full_occupation():
+    """Degenerate fillings: N_e -> 0 leaves P -> 0, N_e -> 2K fills every
+    state so that P -> S^-1 (f(S^-1 F) -> I), for the exact and the Chebyshev
+    density matrix alike."""
+    K = 18
+    F, S = random_pair(K, 21)
+    eps = dm.geneig(F, S)[0]
+    lo, hi = eps[0] - 0.1, eps[-1] + 0.1
+    beta = 4.0
+    n_c = dm.cheb_order(0.5 * (lo + hi), beta, lo, hi, 1e-12)
+    Si = np.linalg.inv(S)
+    for n_e, ref in ((1e-9, np.zeros((K, K))), (2 * K - 1e-9, Si)):
+        ex = dm.dm_exact(F, S, n_e, beta)
+        ch = dm.dm_cheb(F, S, n_e, beta, lo, hi, n_c)
+        for r in (ex, ch):
+            assert abs(2 * np.trace(r["P"] @ S) - n_e) < 1e-8
+            assert np.max(np.abs(r["P"] - ref)) < 1e-8 * max(1.0, np.max(np.abs(Si)))
