@@ -43,6 +43,26 @@ def make_params(*, kT, n_electrons, eta=1e-10, cheb_tail_tol=1e-10, cheb_order=0
     return p
 
 
+def device_f64(t, numel, name, inout=False):
+    """Check that t has the layout the C ABI expects for a K x K matrix or a
+    grid: a float64 CUDA tensor of numel elements, contiguous (in-place
+    arguments must already be, so that the library writes into t itself).
+    A host or wrongly typed buffer handed to the kernels would be read as
+    device memory, so it is refused here.  Returns the contiguous tensor."""
+    import torch
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64, not {t.dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    if not t.is_contiguous():
+        if inout:
+            raise ValueError(f"{name} is written in place and must be contiguous")
+        t = t.contiguous()
+    return t
+
+
 class Context:
     """One system on one GPU: descriptors, workspace and the libdft context.
 
@@ -108,24 +128,30 @@ class Context:
         dft_overlap_kinetic(self.ctx, S, T, stream)
         return S, T
 
+    def _mat(self, t, name, inout=False):
+        return device_f64(t, self.K * self.K, name, inout)
+
+    def _grid(self, t, name, inout=False):
+        return device_f64(t, int(np.prod(self.grid_shape)), name, inout)
+
     def density_matrix(self, F, stream=None):
         P = self.matrix()
-        info = dft_density_matrix(self.ctx, F.contiguous(), P, stream)
+        info = dft_density_matrix(self.ctx, self._mat(F, "F"), P, stream)
         return P, info
 
     def density_on_grid(self, P, stream=None):
         n = self.grid_array()
-        dft_density_on_grid(self.ctx, P.contiguous(), n, stream)
+        dft_density_on_grid(self.ctx, self._mat(P, "P"), n, stream)
         return n
 
     def potential_matrix(self, v, stream=None):
         V = self.matrix()
-        dft_potential_matrix(self.ctx, v.contiguous(), V, stream)
+        dft_potential_matrix(self.ctx, self._grid(v, "v"), V, stream)
         return V
 
     def hartree_xc(self, n, stream=None):
         v = self.grid_array()
-        e = dft_hartree_xc(self.ctx, n.contiguous(), v, stream)
+        e = dft_hartree_xc(self.ctx, self._grid(n, "n"), v, stream)
         return v, e
 
     def initial_density(self, stream=None):
@@ -134,4 +160,9 @@ class Context:
         return n
 
     def scf_step(self, n_in_out, v_ks_out=None, P_out=None, stream=None):
+        n_in_out = self._grid(n_in_out, "n_in_out", inout=True)
+        if v_ks_out is not None:
+            v_ks_out = self._grid(v_ks_out, "v_ks_out", inout=True)
+        if P_out is not None:
+            P_out = self._mat(P_out, "P_out", inout=True)
         return dft_scf_step(self.ctx, n_in_out, v_ks_out, P_out, stream)

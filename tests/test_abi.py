@@ -148,3 +148,37 @@ def test_workspace_of_the_large_workloads_fits_one_gpu(built, name, lo_gb, hi_gb
     Kp = -(-K // 256) * 256
     assert nb >= 8 * K * K * 8 + 4 * Kp * Kp * 2      # at least the FP64 matrices and the operand pairs
     assert lo_gb * 1e9 < nb < hi_gb * 1e9
+
+
+def test_context_refuses_buffers_the_kernels_cannot_read(built):
+    """The Python side checks what the C ABI cannot: a host tensor, another
+    dtype or a wrong size would be read by the kernels as device memory."""
+    import torch
+    import paper_2108_13478_gb300 as dft
+
+    class Dev:                       # stands in for a CUDA tensor (no GPU here)
+        is_cuda = True
+
+        def __init__(self, n, dtype=torch.float64, contiguous=True):
+            self.n, self.dtype, self.c = n, dtype, contiguous
+
+        def numel(self):
+            return self.n
+
+        def is_contiguous(self):
+            return self.c
+
+        def contiguous(self):
+            return Dev(self.n, self.dtype, True)
+
+    with pytest.raises(ValueError, match="CUDA"):
+        dft.device_f64(torch.zeros(16, dtype=torch.float64), 16, "F")
+    with pytest.raises(ValueError, match="float64"):
+        dft.device_f64(Dev(16, torch.float32), 16, "F")
+    with pytest.raises(ValueError, match="elements"):
+        dft.device_f64(Dev(15), 16, "F")
+    with pytest.raises(ValueError, match="in place"):
+        dft.device_f64(Dev(16, contiguous=False), 16, "n_in_out", inout=True)
+    t = Dev(16)
+    assert dft.device_f64(t, 16, "F") is t
+    assert dft.device_f64(Dev(16, contiguous=False), 16, "F").is_contiguous()
