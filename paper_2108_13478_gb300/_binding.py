@@ -170,7 +170,13 @@ def dft_scf_step(ctx, n_in_out, v_ks_out=None, P_out=None, stream=None) -> dft_i
 
 def dft_scf_step_batched(ctxs, n_in_out, stream=None):
     """One SCF step for several contexts; returns their dft_info results."""
+    import torch
     n = len(ctxs)
+    if len(n_in_out) != n:
+        raise ValueError("one density per context")
+    for q, t in enumerate(n_in_out):
+        if not (getattr(t, "is_cuda", False) and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError(f"density {q} must be a contiguous float64 CUDA tensor (it is updated in place)")
     carr = (_P * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
     narr = (_P * n)(*[t.data_ptr() for t in n_in_out])
     infos = (dft_info * n)()

@@ -182,3 +182,12 @@ def test_context_refuses_buffers_the_kernels_cannot_read(built):
     t = Dev(16)
     assert dft.device_f64(t, 16, "F") is t
     assert dft.device_f64(Dev(16, contiguous=False), 16, "F").is_contiguous()
+
+
+def test_batched_step_refuses_host_densities(built):
+    import torch
+    import paper_2108_13478_gb300 as dft
+    with pytest.raises(ValueError, match="CUDA"):
+        dft.dft_scf_step_batched([None], [torch.zeros(8, dtype=torch.float64)])
+    with pytest.raises(ValueError, match="one density"):
+        dft.dft_scf_step_batched([None, None], [torch.zeros(8, dtype=torch.float64)])
