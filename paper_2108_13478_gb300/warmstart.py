@@ -50,12 +50,16 @@ class WarmStart:
         return out
 
     def potential(self, ctx, v_start):
+        """v0 = v_start (None: zero) + the network's correction, on ctx's grid."""
         v0 = ctx.grid_array()
+        if v_start is not None:
+            v_start = ctx._grid(v_start, "v_start")
         B.dft_warmstart_potential(ctx.ctx, self.state, v_start, v0)
         return v0
 
     def accumulate(self, ctx, v_start, v_target):
-        return B.dft_warmstart_accumulate(ctx.ctx, self.state, v_start, v_target)
+        return B.dft_warmstart_accumulate(ctx.ctx, self.state, ctx._grid(v_start, "v_start"),
+                                          ctx._grid(v_target, "v_target"))
 
     def adam(self, lr):
         self.step += 1
@@ -87,7 +91,7 @@ def run_scf(ctx, v_first, max_iter=80, tol_e=1e-8, tol_n=1e-5, e_ref=None, e_tol
     cycles.  Returns (cycles, final info, converged v_KS, cycles to reach
     |E - e_ref| / atom < e_tol if e_ref is given)."""
     n = ctx.grid_array()
-    B.dft_density_from_potential(ctx.ctx, v_first, n)
+    B.dft_density_from_potential(ctx.ctx, ctx._grid(v_first, "v_first"), n)
     v = ctx.grid_array()
     hit = None
     info = None
