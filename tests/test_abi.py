@@ -150,26 +150,29 @@ def test_workspace_of_the_large_workloads_fits_one_gpu(built, name, lo_gb, hi_gb
     assert lo_gb * 1e9 < nb < hi_gb * 1e9
 
 
+class Dev:
+    """Stands in for a CUDA tensor on a host without a GPU."""
+    is_cuda = True
+
+    def __init__(self, n, dtype=None, contiguous=True):
+        import torch
+        self.n, self.dtype, self.c = n, torch.float64 if dtype is None else dtype, contiguous
+
+    def numel(self):
+        return self.n
+
+    def is_contiguous(self):
+        return self.c
+
+    def contiguous(self):
+        return Dev(self.n, self.dtype, True)
+
+
 def test_context_refuses_buffers_the_kernels_cannot_read(built):
     """The Python side checks what the C ABI cannot: a host tensor, another
     dtype or a wrong size would be read by the kernels as device memory."""
     import torch
     import paper_2108_13478_gb300 as dft
-
-    class Dev:                       # stands in for a CUDA tensor (no GPU here)
-        is_cuda = True
-
-        def __init__(self, n, dtype=torch.float64, contiguous=True):
-            self.n, self.dtype, self.c = n, dtype, contiguous
-
-        def numel(self):
-            return self.n
-
-        def is_contiguous(self):
-            return self.c
-
-        def contiguous(self):
-            return Dev(self.n, self.dtype, True)
 
     with pytest.raises(ValueError, match="CUDA"):
         dft.device_f64(torch.zeros(16, dtype=torch.float64), 16, "F")
@@ -191,3 +194,32 @@ def test_batched_step_refuses_host_densities(built):
         dft.dft_scf_step_batched([None], [torch.zeros(8, dtype=torch.float64)])
     with pytest.raises(ValueError, match="one density"):
         dft.dft_scf_step_batched([None, None], [torch.zeros(8, dtype=torch.float64)])
+
+
+def test_context_methods_check_each_argument(built, monkeypatch):
+    """Every Context method sends matrices and grids through the check with
+    its own size (K x K or the grid), and in-place SCF arguments must be
+    contiguous; the library calls are replaced by recorders."""
+    import torch
+    import paper_2108_13478_gb300 as dft
+    c = object.__new__(dft.Context)
+    c.torch, c.device, c.K, c.grid_shape, c.ctx = torch, torch.device("cpu"), 4, (2, 3, 5), None
+    calls = []
+    for name in ("dft_density_matrix", "dft_density_on_grid", "dft_potential_matrix", "dft_hartree_xc",
+                 "dft_scf_step"):
+        monkeypatch.setattr(dft, name, lambda *a, _n=name: calls.append(_n))
+    mat, grid = Dev(16), Dev(30)
+    c.density_matrix(mat)
+    c.density_on_grid(mat)
+    c.potential_matrix(grid)
+    c.hartree_xc(grid)
+    c.scf_step(grid, grid, mat)
+    c.scf_step(grid)
+    assert calls == ["dft_density_matrix", "dft_density_on_grid", "dft_potential_matrix", "dft_hartree_xc",
+                     "dft_scf_step", "dft_scf_step"]
+    for bad in (lambda: c.density_matrix(grid), lambda: c.density_on_grid(torch.zeros(16, dtype=torch.float64)),
+                lambda: c.potential_matrix(mat), lambda: c.hartree_xc(Dev(30, torch.float32)),
+                lambda: c.scf_step(Dev(30, contiguous=False)), lambda: c.scf_step(grid, None, grid)):
+        with pytest.raises(ValueError):
+            bad()
+    assert len(calls) == 6
