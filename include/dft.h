@@ -25,7 +25,7 @@
  *    stream).  Work is enqueued on it; functions that need a result on the
  *    host (spectral bounds to fix the Chebyshev order, the info struct)
  *    synchronise that stream before returning.
- *  - Device pointers must be 16-byte aligned.
+ *  - Device pointers must be 16-byte aligned (DFT_EINVAL otherwise).
  *
  * Environment (mixed-precision paths)
  *  - DFT_AUTOTUNE_CACHE: JSON file that keeps the tensor-core launch shape

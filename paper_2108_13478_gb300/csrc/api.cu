@@ -782,6 +782,7 @@ dft_status dft_density_matrix(dft_ctx* ctx, const double* F, double* P, dft_info
     return guarded(ctx, [&] {
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !F || !P) throw Error(DFT_EINVAL, "null argument");
+        require_aligned16({F, P});
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         Timer tm(s);
         density_matrix_impl(c, F, P, info, s, &tm, 0);
@@ -797,6 +798,7 @@ dft_status dft_density_on_grid(dft_ctx* ctx, const double* P, double* n_grid, vo
     return guarded(ctx, [&] {
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !P || !n_grid) throw Error(DFT_EINVAL, "null argument");
+        require_aligned16({P, n_grid});
         launch_collocate(c, P, n_grid, static_cast<cudaStream_t>(stream));
     });
 }
@@ -806,6 +808,7 @@ dft_status dft_potential_matrix(dft_ctx* ctx, const double* v_grid, double* V, v
     return guarded(ctx, [&] {
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !v_grid || !V) throw Error(DFT_EINVAL, "null argument");
+        require_aligned16({v_grid, V});
         launch_quadrature(c, v_grid, V, static_cast<cudaStream_t>(stream));
     });
 }
@@ -815,6 +818,7 @@ dft_status dft_hartree_xc(dft_ctx* ctx, const double* n_grid, double* v_ks, doub
     return guarded(ctx, [&] {
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !n_grid) throw Error(DFT_EINVAL, "null argument");
+        require_aligned16({n_grid, v_ks});
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         hartree_xc(c, n_grid, v_ks, energies != nullptr, s);
         if (energies) {
@@ -829,6 +833,7 @@ dft_status dft_initial_density(dft_ctx* ctx, double* n_grid, void* stream) {
     return guarded(ctx, [&] {
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !n_grid) throw Error(DFT_EINVAL, "null argument");
+        require_aligned16({n_grid});
         double w = c.p.vloc_width;
         launch_gaussian_sum(c, c.p.ion_charge * std::pow(M_PI * w * w, -1.5), w, n_grid,
                             static_cast<cudaStream_t>(stream));
@@ -841,6 +846,7 @@ dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double
     return guarded(ctx, [&] {
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !n_in_out) throw Error(DFT_EINVAL, "null argument");
+        require_aligned16({n_in_out, v_ks_out, P_out});
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         Timer tm(s);
         dft_info loc{};
@@ -864,6 +870,7 @@ dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in
         std::vector<Ctx*> cs(n);
         for (int q = 0; q < n; ++q) {
             if (!ctxs[q] || !n_in_out[q]) throw Error(DFT_EINVAL, "null context or density in the batch");
+            require_aligned16({n_in_out[q]});
             cs[q] = reinterpret_cast<Ctx*>(ctxs[q]);
             if (cs[q]->K == 0 || cs[q]->Kp == 0) throw Error(DFT_EINVAL, "batched steps need mixed-precision contexts");
             if (cs[q]->p.precision != cs[0]->p.precision) throw Error(DFT_EINVAL, "batch mixes precisions");
@@ -967,6 +974,7 @@ dft_status dft_density_from_potential(dft_ctx* ctx, const double* v_grid, double
     return guarded(ctx, [&] {
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !v_grid || !n_out) throw Error(DFT_EINVAL, "null argument");
+        require_aligned16({v_grid, n_out});
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         launch_quadrature(c, v_grid, c.d_F, s);
         launch_axpby_mat(c.K, 1.0, c.d_T, 1.0, c.d_F, c.d_F, s);
@@ -997,6 +1005,7 @@ dft_status dft_warmstart_potential(dft_ctx* ctx, const void* state, const double
     return guarded(ctx, [&] {
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !state || !v0) throw Error(DFT_EINVAL, "null argument");
+        require_aligned16({state, v_start, v0});
         warm_forward(c, state, v_start, v0, false, static_cast<cudaStream_t>(stream));
     });
 }
@@ -1007,6 +1016,7 @@ dft_status dft_warmstart_accumulate(dft_ctx* ctx, void* state, const double* v_s
     return guarded(ctx, [&] {
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !state || !v_target) throw Error(DFT_EINVAL, "null argument");
+        require_aligned16({state, v_start, v_target});
         double L = warm_accumulate(c, state, v_start, v_target, static_cast<cudaStream_t>(stream));
         if (loss) *loss = L;
     });

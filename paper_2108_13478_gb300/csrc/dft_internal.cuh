@@ -7,6 +7,7 @@
 #include <cufft.h>
 #include <stdint.h>
 #include <atomic>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -323,6 +324,14 @@ struct Error {
     std::string msg;
     Error(dft_status c, std::string m) : code(c), msg(std::move(m)) {}
 };
+// The ABI requires device arguments to start on a 16-byte boundary (the
+// kernels' vector accesses rely on it); null pointers pass, each entry point
+// checks its required arguments for null itself.
+inline void require_aligned16(std::initializer_list<const void*> ptrs) {
+    for (const void* p : ptrs)
+        if (p && (reinterpret_cast<uintptr_t>(p) & 15) != 0)
+            throw Error(DFT_EINVAL, "device arguments must be 16-byte aligned");
+}
 // process-wide count of kernels this library has launched (diagnostics)
 extern std::atomic<unsigned long long> g_launches;
 inline void check_launch(const char* what, int kernels = 1) {

@@ -54,6 +54,7 @@ extern "C" dft_status dft_spectral_bounds_static(dft_ctx* ctx, const double* F, 
     Ctx& c = *reinterpret_cast<Ctx*>(ctx);
     try {
         if (c.K == 0 || !F || !bounds) throw Error(DFT_EINVAL, "null argument");
+        require_aligned16({F});
         if (c.K > MAX_K)
             throw Error(DFT_EINVAL, "K = " + std::to_string(c.K) + " exceeds the static scratch limit of " +
                                         std::to_string(MAX_K) + " basis functions");
