@@ -91,3 +91,12 @@ def test_reference_arm_line_keeps_the_contract(capsys):
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "tiny8"
+
+
+def test_chebyshev_tail_defaults():
+    """FP64 keeps the 1e-10 tail its 1e-9 parity needs; the mixed precisions
+    take 1e-6; an explicit --cheb-tail wins."""
+    ns = lambda p, t=None: types.SimpleNamespace(precision=p, cheb_tail=t)
+    assert bench.cheb_tail(ns("fp64")) == 1e-10
+    assert bench.cheb_tail(ns("fp16x3")) == 1e-6 and bench.cheb_tail(ns("bf16x3")) == 1e-6
+    assert bench.cheb_tail(ns("fp16x3", 1e-8)) == 1e-8
