@@ -94,3 +94,30 @@ def slater_exchange(n, floor=1e-30):
     pos = n > floor
     c = np.where(pos, np.cbrt(np.where(pos, n, 0.0)), 0.0) * CX
     return -c, -0.75 * c
+
+
+# Perdew-Wang 1992 parametrisation of the spin-unpolarised correlation energy
+# per electron of the uniform gas (the paper's LDA, Section 4),
+#   eps_c(r_s) = -2 A (1 + a1 r_s) ln(1 + 1 / (2 A (b1 r_s^1/2 + b2 r_s + b3 r_s^3/2 + b4 r_s^2))),
+# r_s = (3 / (4 pi n))^(1/3); the published constants for the unpolarised gas:
+PW92_A, PW92_A1 = 0.031091, 0.21370
+PW92_B = (7.5957, 3.5876, 1.6382, 0.49294)
+
+
+def pw92_correlation(n, floor=1e-30):
+    """PW92 LDA correlation: eps_c(n) and v_c = d(n eps_c)/dn =
+    eps_c - (r_s / 3) d eps_c / d r_s; points with n <= floor give 0.
+    Returns (v_c, eps_c) like slater_exchange."""
+    n = np.asarray(n, dtype=np.float64)
+    pos = n > floor
+    rs = np.where(pos, (3.0 / (4.0 * math.pi * np.where(pos, n, 1.0))) ** (1.0 / 3.0), 1.0)
+    b1, b2, b3, b4 = PW92_B
+    sr = np.sqrt(rs)
+    q0 = -2.0 * PW92_A * (1.0 + PW92_A1 * rs)
+    q1 = 2.0 * PW92_A * (b1 * sr + b2 * rs + b3 * rs * sr + b4 * rs * rs)
+    dq1 = PW92_A * (b1 / sr + 2.0 * b2 + 3.0 * b3 * sr + 4.0 * b4 * rs)
+    lg = np.log1p(1.0 / q1)
+    eps = q0 * lg
+    deps = -2.0 * PW92_A * PW92_A1 * lg - q0 * dq1 / (q1 * q1 + q1)
+    v = eps - rs / 3.0 * deps
+    return np.where(pos, v, 0.0), np.where(pos, eps, 0.0)

@@ -3,8 +3,11 @@
 Test infrastructure only; see the package docstring.
 
 SCF cycle (Supp. A.3, Fig. A.3): from an input density n_in,
-  v_KS = v_loc + v_H[n_in] + v_x[n_in]          (Eq. 2.6)
-  F    = T + V^KS[v_KS]                          (Eqs. 2.3, 2.5; V^NL = 0)
+  v_KS = v_loc + v_H[n_in] + v_xc[n_in]         (Eq. 2.6; v_xc = Slater
+                                                 exchange, plus PW92
+                                                 correlation when chosen)
+  F    = T + V^NL + V^KS[v_KS]                   (Eqs. 2.3-2.5; V^NL = 0
+                                                 unless KB projectors are set)
   P    = f_FD(S^-1 F) S^-1                       (Eq. 2.9)
   n_out(r_g) = 2 sum P phi phi                   (Eq. 2.7)
 then the energy of n_out and a mixing step give the next n_in.
@@ -15,7 +18,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import basis, dm, grid_ops, poisson
+from . import basis, dm, grid_ops, poisson, pseudo
 
 
 def grid_points(sysm):
@@ -56,6 +59,8 @@ class Model:
     vloc_width: float = 1.5
     neutral: bool = False              # add Gaussian ionic charges to the Poisson source
     ion_charge: float = 4.0
+    nl: object = None                  # pseudo.KB projectors of V^NL, or None (V^NL = 0)
+    pw92: bool = False                 # add PW92 correlation to the Slater exchange
 
 
 @dataclass
@@ -76,34 +81,51 @@ def setup(sysm, model=None):
     S, T = basis.overlap_kinetic(fn)
     vl = vloc(sysm, model.vloc_depth, model.vloc_width)
     ni = ion_density(sysm, model.ion_charge, model.vloc_width) if model.neutral else np.zeros_like(vl)
-    return Setup(sysm=sysm, model=model, S=S, T=T, vloc=vl, nion=ni, c0=poisson.cube_inv_r_constant())
+    st = Setup(sysm=sysm, model=model, S=S, T=T, vloc=vl, nion=ni, c0=poisson.cube_inv_r_constant())
+    st.extras["vnl"] = pseudo.vnl(sysm, model.nl, model.eta) if model.nl is not None else None
+    return st
+
+
+def xc(st, n):
+    """LDA v_xc and eps_xc: Slater exchange, plus PW92 correlation when the
+    model asks for it."""
+    vx, ex = poisson.slater_exchange(n)
+    if st.model.pw92:
+        vc, ec = poisson.pw92_correlation(n)
+        vx, ex = vx + vc, ex + ec
+    return vx, ex
 
 
 def potential(st, n):
     """v_KS[n] = v_loc + v_H[n - n_ion] + v_x[n]  (Eq. 2.6)."""
     vh = poisson.hartree(st.sysm, n - st.nion, st.c0)
-    vx, ex = poisson.slater_exchange(n)
+    vx, ex = xc(st, n)
     return st.vloc + vh + vx, vh, ex
 
 
 def energy(st, P, n):
-    """E = 2 Tr[P T] + h^3 sum v_loc n + 1/2 h^3 sum v_H[rho] rho
-           + h^3 sum eps_x(n) n,   rho = n - n_ion.
+    """E = 2 Tr[P T] + 2 Tr[P V^NL] + h^3 sum v_loc n + 1/2 h^3 sum v_H[rho] rho
+           + h^3 sum eps_xc(n) n,   rho = n - n_ion.
     (The paper names only the change Delta E between cycles, Supp. C; this
     internal energy is the reading taken.)"""
     h3 = st.sysm.grid_h ** 3
     rho = n - st.nion
     vh = poisson.hartree(st.sysm, rho, st.c0)
-    _, ex = poisson.slater_exchange(n)
+    _, ex = xc(st, n)
     e_kin = 2.0 * float(np.sum(P * st.T))
+    vnl = st.extras.get("vnl")
+    e_nl = 2.0 * float(np.sum(P * vnl)) if vnl is not None else 0.0
     e_loc = h3 * float(np.sum(st.vloc * n))
     e_h = 0.5 * h3 * float(np.sum(vh * rho))
     e_x = h3 * float(np.sum(ex * n))
-    return dict(total=e_kin + e_loc + e_h + e_x, kin=e_kin, loc=e_loc, hartree=e_h, xc=e_x)
+    return dict(total=e_kin + e_nl + e_loc + e_h + e_x, kin=e_kin, nl=e_nl, loc=e_loc, hartree=e_h, xc=e_x)
 
 
 def fock(st, v):
-    return st.T + grid_ops.potential_matrix(st.sysm, v, st.model.eta)
+    """F = T + V^NL + V^KS[v] (Eq. 2.3)."""
+    F = st.T + grid_ops.potential_matrix(st.sysm, v, st.model.eta)
+    vnl = st.extras.get("vnl")
+    return F if vnl is None else F + vnl
 
 
 def step(st, n_in, dm_fn=None):

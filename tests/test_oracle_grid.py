@@ -215,16 +215,19 @@ def test_energy_invariant_under_quarter_turn():
     assert np.max(np.abs(n2 - n1[:, ::-1, :].transpose(0, 2, 1))) < 1e-10 * np.max(n1)
 
 
-@pytest.mark.parametrize("neutral", [False, True])
-def test_energy_gradient_is_the_fock_matrix(neutral):
+@pytest.mark.parametrize("neutral,full", [(False, False), (True, False), (True, True)])
+def test_energy_gradient_is_the_fock_matrix(neutral, full):
     """The Kohn-Sham potential is the functional derivative of the energy
     (Eq. 2.6 from the energy terms): for n = n[P] the directional derivative
-    of E(P) along a symmetric D is 2 Tr[D F[n(P)]], F = T + V[v_KS].  A
-    wrong Hartree factor, an exchange potential that is not d(n eps_x)/dn or
-    a wrong sign on the ionic charge all break it."""
+    of E(P) along a symmetric D is 2 Tr[D F[n(P)]], F = T + V^NL + V[v_KS].
+    A wrong Hartree factor, an exchange or correlation potential that is not
+    d(n eps_xc)/dn, a wrong sign on the ionic charge, or a non-local energy
+    that is not 2 Tr[P V^NL] all break it.  full: with the KB projectors
+    (s and p) and PW92 correlation."""
+    from oracle import pseudo
     xyz = np.array([[0.0, 0.0, 0.0], [2.3, 0.7, -0.4], [-1.1, 1.9, 0.8]])
     s = w.make_system(xyz, h=0.4)
-    st = scf.setup(s, scf.Model(neutral=neutral))
+    st = scf.setup(s, scf.Model(neutral=neutral, nl=pseudo.KB() if full else None, pw92=full))
     r = scf.step(st, scf.ion_density(s))
     P = r["P"]
     K = P.shape[0]
