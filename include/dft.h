@@ -41,6 +41,10 @@
  *    cooperative launch per recurrence pass, tiles of consecutive steps
  *    ordered by per-block counters (256-wide tiles, no stream-K).  Malformed
  *    values are ignored.
+ *  - DFT_TEST_EXPIRE_WAITS: test hook of the bounded waits; any value makes
+ *    every block-counter wait of the dataflow launch ask for one write more
+ *    than any tile makes, so each runs out after its limit (1 s) and the call
+ *    returns DFT_ETIMEOUT with the context still usable.  Never set in use.
  */
 #ifndef DFT_H
 #define DFT_H
@@ -73,6 +77,10 @@ enum { DFT_MODEL_LITERAL = 0, DFT_MODEL_NEUTRAL = 1 };
  * Pulay (DIIS, the paper's accelerator, Section 2) on the density residual,
  * Kerker-preconditioned when kerker_q0 > 0. */
 enum { DFT_MIX_LINEAR = 0, DFT_MIX_KERKER = 1, DFT_MIX_PULAY = 2 };
+/* LDA exchange-correlation (Eq. 2.6): Slater exchange only, or exchange
+ * plus the PW92 parametrisation of the uniform-gas correlation (the LDA the
+ * paper uses, Section 4). */
+enum { DFT_XC_SLATER = 0, DFT_XC_PW92 = 1 };
 
 typedef struct dft_ctx dft_ctx;
 
@@ -118,6 +126,18 @@ typedef struct dft_params {
     double kerker_q0;       /* Kerker wave number (bohr^-1); 0 = no preconditioning for Pulay */
     int    mix_history;     /* Pulay history length (0 -> 8, at most 16) */
     unsigned long long seed;/* Lanczos start vector */
+    int    skip_correction; /* mixed precisions: 1 = leave out the FP64 electron-count
+                               correction that follows the recurrence (dft_density_matrix) */
+    int    reuse_mu;        /* mixed precisions, dft_scf_step: 1 = skip the moments pass while
+                               mu has settled (see dft_scf_step) */
+    /* Non-local Kleinman-Bylander pseudopotential (Eqs. 2.3-2.4, Supp.
+     * A.2.2): per atom nl_channels projectors (0 = none, 1 = s, 4 = s and
+     * x, y, z p), chi(r) = N (r - R)^(l) exp(-nl_zeta |r - R|^2) with unit
+     * norm and cube windows by the rule of Eq. A.4, and KB energies nl_e_s,
+     * nl_e_p (hartree): v_nl = sum_p e_p |chi_p><chi_p|. */
+    int    nl_channels;
+    double nl_zeta, nl_e_s, nl_e_p;
+    int    xc;              /* DFT_XC_SLATER or DFT_XC_PW92 */
 } dft_params;
 
 /* Results of dft_density_matrix / dft_scf_step.  ms_stage: CUDA-event
@@ -132,8 +152,13 @@ typedef struct dft_info {
     int n_cheb;                          /* N_C used */
     int iter;                            /* SCF steps taken by this context */
     int spectrum_ok;                     /* 1 if every iterate stayed bounded */
-    int reserved;
+    int mu_reused;                       /* 1 if the moments pass was skipped (dft_scf_step) */
     float ms_stage[8];
+    /* FP64 correction after the mixed-precision recurrence (0 on the FP64
+     * path or when skipped): the shift of mu it applied, 2 Tr[P S] before it,
+     * and the change it made to the band energy 2 Tr[P F] */
+    double mu_correction, n_e_uncorrected, e_band_correction;
+    double e_nl;                         /* 2 Tr[P V^NL] (part of e_total; 0 without projectors) */
 } dft_info;
 
 /* Bytes of device workspace dft_init_basis needs for this problem.
@@ -159,12 +184,34 @@ dft_status dft_init_basis(dft_ctx** ctx, const dft_basis_desc* basis, const dft_
  * positive definite. */
 dft_status dft_overlap_kinetic(dft_ctx* ctx, double* S, double* T, void* stream);
 
+/* The non-local pseudopotential matrix V^NL (device, K x K, written; zeros
+ * without projectors), formed by dft_overlap_kinetic once per geometry
+ * (Supp. A.2.2: "only once in the beginning").  For the separable KB
+ * operator the paper's two grid stages (psi_Cb = v_nl^C phi_b h^3 on the
+ * atom's window, V^C_ab = phi_a . psi_Cb h^3, V^NL = sum_C V^C, Eq. A.7)
+ * equal V^NL = B^T diag(e) B with the grid projections
+ * B_pb = h^3 sum_{g in W_p and W_b} chi_p(r_g) phi_b(r_g), which is what is
+ * computed (each projection as three one-dimensional sums over the
+ * intersection of the two cube windows, FP64).  dft_scf_step and
+ * dft_density_from_potential add it to the Fock matrix (Eq. 2.3) and
+ * 2 Tr[P V^NL] to the energy.  DFT_EINVAL before dft_overlap_kinetic. */
+dft_status dft_nonlocal_matrix(dft_ctx* ctx, double* VNL, void* stream);
+
 /* P = f_FD(S^-1 F) S^-1 (Eq. 2.9) for the Fock matrix F (device, K x K),
  * by the Chebyshev recurrence of Supp. B in the symmetric form
  * F~ = L^-1 F L^-T, X_0 = I, X_{l+1} = 2 H_N X_l - X_{l-1}, H_N = (F~ - Ebar)/dE,
- * P = L^-T (sum_l a_l(mu) X_l) L^-1, with mu fixed by 2 Tr[P S] = N_e
- * (Eq. 2.8) from the Chebyshev moments.  P (device, K x K) is written;
- * info (host, may be NULL) receives mu, the bounds and N_C. */
+ * P = L^-T rho L^-1 with rho = sum_l a_l(mu) X_l, and mu fixed by
+ * 2 Tr[P S] = N_e (Eq. 2.8) from the Chebyshev moments.  P (device, K x K)
+ * is written; info (host, may be NULL) receives mu, the bounds and N_C.
+ * Mixed precisions: the two congruences run as split-FP16 tensor-core
+ * products (about 22 bits; FP64 results), and unless params.skip_correction
+ * is set an FP64 correction step follows the recurrence: with
+ * d rho / d mu = beta (rho - rho^2) (the Fermi function's derivative),
+ * dmu = (N_e / 2 - Tr rho) / (beta (Tr rho - ||rho||_F^2)) and
+ * rho += dmu beta (rho - rho^2), which restores 2 Tr[P S] = N_e to FP64
+ * rounding; it is skipped where no states lie at the Fermi level or
+ * |beta dmu| > 0.5.  DFT_EINTERNAL if a split operand leaves the FP16
+ * range (|x| >= 32768). */
 dft_status dft_density_matrix(dft_ctx* ctx, const double* F, double* P, dft_info* info, void* stream);
 
 /* n(r_g) = 2 sum_ab P_ab phi_a(r_g) phi_b(r_g) over the windows (Eq. 2.7,
@@ -185,10 +232,18 @@ dft_status dft_hartree_xc(dft_ctx* ctx, const double* n_grid, double* v_ks, doub
 
 /* One SCF cycle (Supp. A.3): from the input density n_in (device grid),
  * v_KS[n_in] -> V^KS -> F = T + V^KS -> P -> n_out -> energy of n_out ->
- * mixing.  n_in_out is overwritten with the next input density; v_ks_out
+ * mixing, with F = T + V^NL + V^KS (Eq. 2.3) and v_KS's exchange-correlation
+ * as params.xc selects.  n_in_out is overwritten with the next input density; v_ks_out
  * (device grid, may be NULL) receives v_KS[n_in]; P_out (device K x K, may
  * be NULL) receives P; info (host, may be NULL) receives the energies,
- * mu, N_C and the density residual. */
+ * mu, N_C and the density residual.
+ * With params.reuse_mu (mixed precisions, correction on) the moments pass
+ * that fixes mu is skipped once mu has settled: when the chemical
+ * potentials of the context's last two cycles differ by less than 0.01 kT,
+ * the expansion is taken at the last mu and the FP64 correction step moves
+ * mu to first order (info->mu_reused = 1, ms_stage[3] ~ 0); if that Newton
+ * step exceeds 0.05 kT the cycle's density matrix is computed again with
+ * the moments pass.  dft_overlap_kinetic clears the history. */
 dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double* P_out,
                         dft_info* info, void* stream);
 
@@ -258,9 +313,12 @@ dft_status dft_initial_density(dft_ctx* ctx, double* n_grid, void* stream);
  * The paper has no counterpart: this is a deployment variant of the Lanczos
  * step inside dft_density_matrix for code that runs where cudaMalloc is not
  * allowed (a host framework's fixed memory pool, pre-planned execution with
- * every buffer fixed up front).  It computes F~ = L^-1 F L^-T and the padded
- * Lanczos bounds exactly as dft_density_matrix does, but its scratch is a
- * file-scope device array of 2 K^2 + 4 K + 300 doubles for K <= 768 (about
+ * every buffer fixed up front).  It computes F~ = L^-1 F L^-T in FP64 and the
+ * padded Lanczos bounds as dft_density_matrix does (identical for FP64
+ * contexts; a mixed-precision context forms F~ by split-FP16 products, so its
+ * bounds agree to that rounding, ~1e-6 relative), and returns the fixed
+ * bounds of the parameters unchanged when e_max > e_min; its scratch is a
+ * file-scope device array of 2 K^2 + 4 K + 304 doubles for K <= 768 (about
  * 9.5 MB, held by every GPU that loads the library until the process ends);
  * it calls no cudaMalloc, cudaFree or allocating library routine.
  *   F       device, K x K Fock matrix (as for dft_density_matrix)

@@ -15,6 +15,7 @@ from . import _binding as B
 from ._binding import (  # noqa: F401
     DftError, dft_basis_desc, dft_grid_desc, dft_info, dft_params,
     DFT_PREC_FP64, DFT_PREC_BF16X3, DFT_PREC_FP16X3, DFT_MODEL_LITERAL, DFT_MODEL_NEUTRAL, DFT_MIX_LINEAR, DFT_MIX_KERKER, DFT_MIX_PULAY,
+    DFT_XC_SLATER, DFT_XC_PW92, dft_nonlocal_matrix,
     dft_workspace_bytes, dft_init_basis, dft_overlap_kinetic, dft_density_matrix, dft_density_on_grid,
     dft_potential_matrix, dft_hartree_xc, dft_scf_step, dft_initial_density, dft_destroy, dft_last_error,
     dft_version, dft_kernel_launches, dft_spectral_bounds_static, dft_scf_step_batched,
@@ -26,7 +27,8 @@ from ._binding import (  # noqa: F401
 def make_params(*, kT, n_electrons, eta=1e-10, cheb_tail_tol=1e-10, cheb_order=0, precision=DFT_PREC_FP64,
                 e_min=0.0, e_max=0.0, lanczos_steps=64, model=DFT_MODEL_LITERAL, vloc_depth=4.0, vloc_width=1.5,
                 ion_charge=4.0, mixer=DFT_MIX_LINEAR, mix_alpha=0.3, kerker_q0=0.8, mix_history=8,
-                seed=1234) -> dft_params:
+                seed=1234, skip_correction=0, reuse_mu=0, nl_channels=0, nl_zeta=1.0, nl_e_s=0.0, nl_e_p=0.0,
+                xc=DFT_XC_SLATER) -> dft_params:
     p = dft_params()
     p.beta = 1.0 / kT
     p.n_electrons = n_electrons
@@ -40,6 +42,10 @@ def make_params(*, kT, n_electrons, eta=1e-10, cheb_tail_tol=1e-10, cheb_order=0
     p.vloc_depth, p.vloc_width, p.ion_charge = vloc_depth, vloc_width, ion_charge
     p.mixer, p.mix_alpha, p.kerker_q0, p.mix_history = mixer, mix_alpha, kerker_q0, mix_history
     p.seed = seed
+    p.skip_correction = int(skip_correction)
+    p.reuse_mu = int(reuse_mu)
+    p.nl_channels, p.nl_zeta, p.nl_e_s, p.nl_e_p = int(nl_channels), nl_zeta, nl_e_s, nl_e_p
+    p.xc = int(xc)
     return p
 
 
@@ -138,6 +144,16 @@ class Context:
         P = self.matrix()
         info = dft_density_matrix(self.ctx, self._mat(F, "F"), P, stream)
         return P, info
+
+    def nonlocal_matrix(self, stream=None):
+        """V^NL (K x K), formed by overlap_kinetic (zeros without projectors)."""
+        V = self.matrix()
+        dft_nonlocal_matrix(self.ctx, V, stream)
+        return V
+
+    def spectral_bounds_static(self, F, stream=None):
+        """(E_min, E_max) of S^-1 F from the allocation-free entry point."""
+        return dft_spectral_bounds_static(self.ctx, self._mat(F, "F"), stream)
 
     def density_on_grid(self, P, stream=None):
         n = self.grid_array()

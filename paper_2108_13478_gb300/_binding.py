@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "DFT_OK", 1: "DFT_EINVAL", 2: "DFT_ENOMEM", 3: "DFT_ECUDA", 4
 DFT_PREC_FP64, DFT_PREC_BF16X3, DFT_PREC_FP16X3 = 0, 1, 2
 DFT_MODEL_LITERAL, DFT_MODEL_NEUTRAL = 0, 1
 DFT_MIX_LINEAR, DFT_MIX_KERKER, DFT_MIX_PULAY = 0, 1, 2
+DFT_XC_SLATER, DFT_XC_PW92 = 0, 1
 
 
 class dft_basis_desc(C.Structure):
@@ -37,18 +38,21 @@ class dft_params(C.Structure):
                 ("e_min", C.c_double), ("e_max", C.c_double), ("lanczos_steps", C.c_int), ("model", C.c_int),
                 ("vloc_depth", C.c_double), ("vloc_width", C.c_double), ("ion_charge", C.c_double),
                 ("mixer", C.c_int), ("mix_alpha", C.c_double), ("kerker_q0", C.c_double),
-                ("mix_history", C.c_int), ("seed", C.c_ulonglong)]
+                ("mix_history", C.c_int), ("seed", C.c_ulonglong), ("skip_correction", C.c_int),
+                ("reuse_mu", C.c_int), ("nl_channels", C.c_int), ("nl_zeta", C.c_double),
+                ("nl_e_s", C.c_double), ("nl_e_p", C.c_double), ("xc", C.c_int)]
 
 
 class dft_info(C.Structure):
     _fields_ = [("mu", C.c_double), ("e_min", C.c_double), ("e_max", C.c_double), ("n_e_trace", C.c_double),
                 ("e_total", C.c_double), ("e_kin", C.c_double), ("e_loc", C.c_double), ("e_hartree", C.c_double),
                 ("e_xc", C.c_double), ("de_per_atom", C.c_double), ("residual", C.c_double),
-                ("n_cheb", C.c_int), ("iter", C.c_int), ("spectrum_ok", C.c_int), ("reserved", C.c_int),
-                ("ms_stage", C.c_float * 8)]
+                ("n_cheb", C.c_int), ("iter", C.c_int), ("spectrum_ok", C.c_int), ("mu_reused", C.c_int),
+                ("ms_stage", C.c_float * 8), ("mu_correction", C.c_double), ("n_e_uncorrected", C.c_double),
+                ("e_band_correction", C.c_double), ("e_nl", C.c_double)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("ms_stage", "reserved")}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms_stage"}
         d["ms_stage"] = list(self.ms_stage)
         return d
 
@@ -61,6 +65,7 @@ SIGNATURES = [
                                  C.POINTER(dft_params), _P, C.c_size_t, _P]),
     ("dft_overlap_kinetic", C.c_int, [_P, _P, _P, _P]),
     ("dft_density_matrix", C.c_int, [_P, _P, _P, C.POINTER(dft_info), _P]),
+    ("dft_nonlocal_matrix", C.c_int, [_P, _P, _P]),
     ("dft_density_on_grid", C.c_int, [_P, _P, _P, _P]),
     ("dft_potential_matrix", C.c_int, [_P, _P, _P, _P]),
     ("dft_hartree_xc", C.c_int, [_P, _P, _P, C.POINTER(C.c_double), _P]),
@@ -140,6 +145,10 @@ def dft_init_basis(basis, grid, params, workspace, stream=None):
 
 def dft_overlap_kinetic(ctx, S=None, T=None, stream=None):
     _check(ctx, lib.dft_overlap_kinetic(ctx, _ptr(S), _ptr(T), _stream(stream)))
+
+
+def dft_nonlocal_matrix(ctx, VNL, stream=None):
+    _check(ctx, lib.dft_nonlocal_matrix(ctx, _ptr(VNL), _stream(stream)))
 
 
 def dft_density_matrix(ctx, F, P, stream=None) -> dft_info:
@@ -249,7 +258,18 @@ def dft_version() -> str:
 
 def dft_spectral_bounds_static(ctx, F, stream=None):
     """Lanczos bounds of S^-1 F through the allocation-free entry point
-    (K <= 768); returns (E_min, E_max)."""
+    (K <= 768); returns (E_min, E_max).  F must be a contiguous square
+    float64 CUDA matrix (Context.spectral_bounds_static also checks that it
+    is K x K): the kernels read K x K doubles from its pointer."""
+    import torch
+    if not getattr(F, "is_cuda", False):
+        raise ValueError("F must be a CUDA tensor")
+    if F.dtype != torch.float64:
+        raise ValueError(f"F must be float64, not {F.dtype}")
+    if F.dim() != 2 or F.shape[0] != F.shape[1]:
+        raise ValueError("F must be a square matrix")
+    if not F.is_contiguous():
+        raise ValueError("F must be contiguous")
     b = (C.c_double * 2)()
     _check(ctx, lib.dft_spectral_bounds_static(ctx, _ptr(F), b, _stream(stream)))
     return b[0], b[1]

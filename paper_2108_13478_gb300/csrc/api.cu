@@ -17,7 +17,9 @@ std::atomic<unsigned long long> dft::g_launches{0};
 
 namespace {
 
-const char* kVersion = "libdft 0.1 (sm_103a)";
+const char* kVersion = "libdft 0.2 (sm_103a)";
+// reuse of mu between SCF cycles, in units of kT (see dft_scf_step)
+constexpr double MU_SETTLED = 0.01, MU_REDO = 0.05;
 
 // Window half-length L solving c(L sqrt(zeta), l) = 1 - eta (Eq. A.4).
 // c(d, 0) = erf(d), c(d, 1) = 1 - exp(-d^2).
@@ -65,6 +67,10 @@ void validate(const dft_basis_desc* b, const dft_grid_desc* g, const dft_params*
     if (p->cheb_order <= 0 && !(p->cheb_tail_tol > 0.0)) throw Error(DFT_EINVAL, "cheb_tail_tol must be positive");
     if (p->mixer < DFT_MIX_LINEAR || p->mixer > DFT_MIX_PULAY) throw Error(DFT_EINVAL, "unknown mixer");
     if (p->mix_history < 0 || p->mix_history > 16) throw Error(DFT_EINVAL, "mix_history must be in [0, 16]");
+    if (p->nl_channels != 0 && p->nl_channels != 1 && p->nl_channels != 4)
+        throw Error(DFT_EINVAL, "nl_channels must be 0, 1 (s) or 4 (s and p)");
+    if (p->nl_channels && !(p->nl_zeta > 0.0)) throw Error(DFT_EINVAL, "nl_zeta must be positive");
+    if (p->xc != DFT_XC_SLATER && p->xc != DFT_XC_PW92) throw Error(DFT_EINVAL, "unknown xc");
 }
 
 // functions, windows, tables and tile lists (host part of the set-up)
@@ -127,6 +133,37 @@ void build_basis(Ctx& c, const dft_basis_desc* b, const dft_grid_desc* g, const 
         std::vector<int> pos(cnt.begin(), cnt.end() - 1);
         for (int f = 0; f < c.K; ++f) each_tile(c.fn_host[f], [&](long long t) { (*tile_fn)[pos[t]++] = f; });
     }
+    // KB projectors (Supp. A.2.2): per atom an s Gaussian (and x, y, z p
+    // Gaussians) of exponent nl_zeta, unit continuum norm, cube windows by
+    // the basis functions' rule (Eq. A.4)
+    c.pj_host.clear();
+    c.pje_host.clear();
+    c.pj_w = 0;
+    if (p->nl_channels > 0) {
+        const double z = p->nl_zeta, base = std::pow(2.0 * z / M_PI, 0.75);
+        for (int a = 0; a < b->n_atoms; ++a)
+            for (int q = 0; q < p->nl_channels; ++q) {
+                const int l = q == 0 ? 0 : 1;
+                Fn f{};
+                f.cx = b->xyz[3 * a]; f.cy = b->xyz[3 * a + 1]; f.cz = b->xyz[3 * a + 2];
+                f.zeta = z;
+                f.norm = l == 0 ? base : base * 2.0 * std::sqrt(z);
+                f.px = q == 1; f.py = q == 2; f.pz = q == 3;
+                const double L = window_halfwidth(z, l, p->eta);
+                const double cc[3] = {f.cx, f.cy, f.cz};
+                for (int d = 0; d < 3; ++d) {
+                    long long lo = (long long)std::ceil((cc[d] - L - c.origin[d]) / c.h);
+                    long long hi = (long long)std::floor((cc[d] + L - c.origin[d]) / c.h);
+                    lo = std::max<long long>(lo, 0);
+                    hi = std::min<long long>(hi, c.n[d] - 1);
+                    f.lo[d] = (int)std::min<long long>(lo, c.n[d]);
+                    f.hi[d] = (int)std::max<long long>(hi, -1);
+                    c.pj_w = std::max(c.pj_w, f.hi[d] - f.lo[d] + 1);
+                }
+                c.pj_host.push_back(f);
+                c.pje_host.push_back(l == 0 ? p->nl_e_s : p->nl_e_p);
+            }
+    }
     for (int d = 0; d < 3; ++d) c.Nfft[d] = fft_size(2 * c.n[d]);
     c.nfft_r = (long long)c.Nfft[0] * c.Nfft[1] * c.Nfft[2];
     c.nfft_c = (long long)(c.Nfft[0] / 2 + 1) * c.Nfft[1] * c.Nfft[2];
@@ -173,12 +210,24 @@ size_t carve(Ctx& c, char* base) {
     size_t o_wcoef = L.off(sizeof(double) * 16 * (size_t)c.n_atoms);
     size_t o_wz = L.off(sizeof(float) * 3 * 128 * (size_t)c.n_atoms);
     size_t o_wdc = L.off(sizeof(double) * 16 * (size_t)c.n_atoms);
+    const size_t np = c.pj_host.size();
+    size_t o_pj = 0, o_pje = 0, o_pjt = 0, o_nlb = 0, o_nleb = 0, o_vnl = 0;
+    if (np > 0) {
+        o_pj = L.off(sizeof(Fn) * np);
+        o_pje = L.off(sizeof(double) * np);
+        o_pjt = L.off(sizeof(double) * np * 3 * (size_t)c.pj_w);
+        o_nlb = L.off(sizeof(double) * np * (size_t)c.K);
+        o_nleb = L.off(sizeof(double) * np * (size_t)c.K);
+        o_vnl = L.off(K2);
+    }
     size_t o_h16[2] = {0, 0}, o_x16[4] = {0, 0, 0, 0}, o_rtc = 0, o_tiles = 0, o_systab = 0, o_maps = 0;
-    size_t o_cst = 0, o_skf = 0, o_skb = 0, o_cnt = 0, o_macc = 0;
+    size_t o_cst = 0, o_skf = 0, o_skb = 0, o_cnt = 0, o_macc = 0, o_li16[2] = {0, 0}, o_lt16[2] = {0, 0};
     if (c.Kp > 0) {
         size_t P16 = (size_t)c.Kp * c.Kp * 2;
         for (auto& o : o_h16) o = L.off(P16);
         for (auto& o : o_x16) o = L.off(P16);
+        for (auto& o : o_li16) o = L.off(P16);
+        for (auto& o : o_lt16) o = L.off(P16);
         o_rtc = L.off((size_t)c.Kp * c.Kp * sizeof(double));
         o_systab = L.off(sizeof(TcSys) * TC_MAX_SYS);
         o_maps = L.off(sizeof(CUtensorMap) * TC_MAPS_PER_SYS * TC_MAX_SYS);
@@ -219,9 +268,21 @@ size_t carve(Ctx& c, char* base) {
         c.d_wcoef = (double*)(base + o_wcoef);
         c.d_wz = (float*)(base + o_wz);
         c.d_wdc = (double*)(base + o_wdc);
+        if (np > 0) {
+            c.d_pj = (Fn*)(base + o_pj);
+            c.d_pje = (double*)(base + o_pje);
+            c.d_pjtab = (double*)(base + o_pjt);
+            c.d_nlB = (double*)(base + o_nlb);
+            c.d_nlEB = (double*)(base + o_nleb);
+            c.d_VNL = (double*)(base + o_vnl);
+        }
         if (c.Kp > 0) {
             for (int q = 0; q < 2; ++q) c.d_h16[q] = base + o_h16[q];
             for (int q = 0; q < 4; ++q) c.d_x16[q] = base + o_x16[q];
+            for (int q = 0; q < 2; ++q) {
+                c.d_li16[q] = base + o_li16[q];
+                c.d_lt16[q] = base + o_lt16[q];
+            }
             c.d_rho_tc = (float2*)(base + o_rtc);
             c.d_systab = (TcSys*)(base + o_systab);
             c.d_maps = (CUtensorMap*)(base + o_maps);
@@ -383,8 +444,12 @@ void dm_prepare(Ctx& c, const double* F, cudaStream_t s, Timer* tm, int t0) {
     if (!c.have_chol) throw Error(DFT_EINVAL, "call dft_overlap_kinetic first");
     const int K = c.K;
     DFT_CUDA_CHECK(cudaMemsetAsync(c.d_flags, 0, sizeof(int) * FLAG_COUNT, s));
+    DFT_CUDA_CHECK(cudaMemsetAsync(c.d_scal + SCAL_DMU, 0, sizeof(double) * (SCAL_COUNT - SCAL_DMU), s));
     if (tm) tm->mark(t0);
-    congruence_lower(K, c.d_Linv, F, c.d_B, c.d_A, s);
+    // F~ = L^-1 F L^-T: split-FP16 tensor-core products on the mixed path,
+    // FP64 on the FP64 path
+    if (c.p.precision != DFT_PREC_FP64) cg_transform_f(c, F, c.d_A, s);
+    else congruence_lower(K, c.d_Linv, F, c.d_B, c.d_A, s);
     if (tm) tm->mark(t0 + 1);
     if (c.p.e_max > c.p.e_min) {
         double b[2] = {c.p.e_min, c.p.e_max};
@@ -510,6 +575,13 @@ void dm_mu(Ctx& c, cudaStream_t s) {
     launch_cheb_coeffs(n_c, M, c.d_cos, c.d_scal, c.p.beta, 0.0, false, c.d_coef, s);
 }
 
+// coefficients a_l(mu) at a given mu (the moments pass skipped), mu on the device
+void dm_mu_fixed(Ctx& c, double mu, cudaStream_t s) {
+    const int n_c = c.n_c_cur, M = 4 * n_c;
+    DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_scal + SCAL_MU, &mu, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_cheb_coeffs(n_c, M, c.d_cos, c.d_scal, c.p.beta, mu, true, c.d_coef, s);
+}
+
 // weighted pass of one system: rho = sum_l a_l X_l
 void dm_pass2(Ctx& c, cudaStream_t s) {
     const int K = c.K, n_c = c.n_c_cur;
@@ -536,15 +608,27 @@ void dm_pass2(Ctx& c, cudaStream_t s) {
 }
 
 // P = L^-T rho L^-1, electron count, status flags
+// (mixed path: first the FP64 electron-count correction of rho, unless
+// switched off; then the split-FP16 tensor-core back-transform)
 void dm_finish(Ctx& c, double* P, dft_info* info, cudaStream_t s) {
     const int K = c.K;
-    congruence_lower_t(K, c.d_Linv, c.d_rho, c.d_B, P, s);
+    if (c.p.precision != DFT_PREC_FP64) {
+        cg_split_rho(c, s);
+        if (!c.p.skip_correction) {
+            cg_correct_rho(c, s);
+            cg_split_rho(c, s);
+        }
+        cg_back_transform(c, P, s);
+    } else {
+        congruence_lower_t(K, c.d_Linv, c.d_rho, c.d_B, P, s);
+    }
     launch_frob_dot((long long)K * K, P, c.d_S, c.d_part, c.d_scal + SCAL_NE, s);
     int flags[FLAG_COUNT];
     read_flags(c, s, flags);
-    double sc[2];
+    double sc[2], corr[4];
     DFT_CUDA_CHECK(cudaMemcpyAsync(sc, c.d_scal + SCAL_MU, sizeof(double), cudaMemcpyDeviceToHost, s));
     DFT_CUDA_CHECK(cudaMemcpyAsync(sc + 1, c.d_scal + SCAL_NE, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DFT_CUDA_CHECK(cudaMemcpyAsync(corr, c.d_scal + SCAL_DMU, sizeof(corr), cudaMemcpyDeviceToHost, s));
     DFT_CUDA_CHECK(cudaStreamSynchronize(s));
     if (info) {
         info->mu = sc[0];
@@ -553,18 +637,30 @@ void dm_finish(Ctx& c, double* P, dft_info* info, cudaStream_t s) {
         info->n_e_trace = 2.0 * sc[1];
         info->n_cheb = c.n_c_cur;
         info->spectrum_ok = flags[FLAG_SPECTRUM] ? 0 : 1;
+        info->mu_correction = corr[0];
+        info->n_e_uncorrected = corr[1];
+        info->e_band_correction = 2.0 * corr[0] * c.p.beta * corr[2];
     }
+    c.mu_step_raw = corr[3];
+    c.mu_last = sc[0];
     if (flags[FLAG_TIMEOUT]) throw Error(DFT_ETIMEOUT, "a tensor-core pipeline wait expired");
+    if (flags[FLAG_RANGE]) throw Error(DFT_EINTERNAL, "a split-precision congruence left the range of the FP16 pair");
     if (flags[FLAG_SPECTRUM]) throw Error(DFT_ESPECTRUM, "Chebyshev iterates left [-1, 1]: spectral bounds too tight");
     if (flags[FLAG_MU]) throw Error(DFT_ENOTCONV, "mu bisection: the bracket does not contain N_e");
 }
 
-// P = f(S^-1 F) S^-1 through the symmetric Chebyshev recurrence (Supp. B)
+// P = f(S^-1 F) S^-1 through the symmetric Chebyshev recurrence (Supp. B);
+// with mu_fixed the moments pass is skipped and the expansion is taken at
+// that mu (the FP64 correction in dm_finish then moves mu to first order)
 void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cudaStream_t s, Timer* tm,
-                         int t0) {
+                         int t0, const double* mu_fixed = nullptr) {
     dm_prepare(c, F, s, tm, t0);
-    dm_pass1(c, s);
-    dm_mu(c, s);
+    if (mu_fixed) {
+        dm_mu_fixed(c, *mu_fixed, s);
+    } else {
+        dm_pass1(c, s);
+        dm_mu(c, s);
+    }
     if (tm) tm->mark(t0 + 3);
     dm_pass2(c, s);
     if (tm) tm->mark(t0 + 4);
@@ -572,11 +668,17 @@ void density_matrix_impl(Ctx& c, const double* F, double* P, dft_info* info, cud
     if (tm) tm->mark(t0 + 5);
 }
 
-// v_KS[n_in] -> V^KS -> F = T + V^KS (into c.d_F)
+// F += T + V^NL (Eq. 2.3; V^NL only with KB projectors)
+void add_one_electron(Ctx& c, double* F, cudaStream_t s) {
+    launch_axpby_mat(c.K, 1.0, c.d_T, 1.0, F, F, s);
+    if (c.d_VNL) launch_axpby_mat(c.K, 1.0, c.d_VNL, 1.0, F, F, s);
+}
+
+// v_KS[n_in] -> V^KS -> F = T + V^NL + V^KS (into c.d_F)
 void scf_head(Ctx& c, const double* n_in, cudaStream_t s) {
     hartree_xc(c, n_in, c.d_vks, false, s);
     launch_quadrature(c, c.d_vks, c.d_F, s);
-    launch_axpby_mat(c.K, 1.0, c.d_T, 1.0, c.d_F, c.d_F, s);
+    add_one_electron(c, c.d_F, s);
 }
 
 // n_out from c.d_P, energy of n_out, residual, mixing; fills loc
@@ -587,6 +689,7 @@ void scf_tail(Ctx& c, double* n_in_out, double* v_ks_out, double* P_out, dft_inf
     if (tm) tm->mark(8);
     hartree_xc(c, c.d_nout, nullptr, true, s);
     launch_frob_dot((long long)K * K, c.d_P, c.d_T, c.d_part, c.d_scal + SCAL_EKIN, s);
+    if (c.d_VNL) launch_frob_dot((long long)K * K, c.d_P, c.d_VNL, c.d_part, c.d_scal + SCAL_ENL, s);
     launch_maxabs_diff(c.ng, c.d_nout, n_in_out, c.d_part, c.d_scal + SCAL_RES, s);
     if (v_ks_out) DFT_CUDA_CHECK(cudaMemcpyAsync(v_ks_out, c.d_vks, sizeof(double) * c.ng, cudaMemcpyDeviceToDevice, s));
     if (P_out) DFT_CUDA_CHECK(cudaMemcpyAsync(P_out, c.d_P, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
@@ -597,7 +700,8 @@ void scf_tail(Ctx& c, double* n_in_out, double* v_ks_out, double* P_out, dft_inf
     loc->e_loc = sc[SCAL_E0];
     loc->e_hartree = sc[SCAL_E1];
     loc->e_xc = sc[SCAL_E2];
-    loc->e_total = loc->e_kin + loc->e_loc + loc->e_hartree + loc->e_xc;
+    loc->e_nl = c.d_VNL ? 2.0 * sc[SCAL_ENL] : 0.0;
+    loc->e_total = loc->e_kin + loc->e_nl + loc->e_loc + loc->e_hartree + loc->e_xc;
     loc->residual = sc[SCAL_RES];
     // mixing (Pulay needs the residual on the host for its small solve)
     if (c.p.mixer == DFT_MIX_KERKER) kerker_mix(c, n_in_out, c.d_nout, c.p.mix_alpha, s);
@@ -730,11 +834,18 @@ dft_status dft_init_basis(dft_ctx** ctx, const dft_basis_desc* basis, const dft_
             DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_tile_fn, tf.data(), sizeof(int) * tf.size(), cudaMemcpyHostToDevice, s));
         DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_xyz, c->xyz_host.data(), sizeof(double) * c->xyz_host.size(),
                                        cudaMemcpyHostToDevice, s));
+        if (!c->pj_host.empty()) {
+            DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_pj, c->pj_host.data(), sizeof(Fn) * c->pj_host.size(),
+                                           cudaMemcpyHostToDevice, s));
+            DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_pje, c->pje_host.data(), sizeof(double) * c->pje_host.size(),
+                                           cudaMemcpyHostToDevice, s));
+        }
         DFT_CUDA_CHECK(cudaMemsetAsync(c->d_scal, 0, sizeof(double) * SCAL_COUNT, s));
         DFT_CUDA_CHECK(cudaMemsetAsync(c->d_flags, 0, sizeof(int) * FLAG_COUNT, s));
         if (c->Kp > 0) {
             DFT_CUDA_CHECK(cudaMemsetAsync(c->d_x16[0], 0, (size_t)c->Kp * c->Kp * 2 * 4, s));
             tc_setup(*c);
+            cg_setup(*c);
         }
         launch_build_tables(*c, s);
         launch_gaussian_sum(*c, -c->p.vloc_depth, c->p.vloc_width, c->d_vloc, s);
@@ -769,11 +880,29 @@ dft_status dft_overlap_kinetic(dft_ctx* ctx, double* S, double* T, void* stream)
         DFT_CUDA_CHECK(cudaMemcpyAsync(c.d_A, c.d_S, K2, cudaMemcpyDeviceToDevice, s));
         DFT_CUDA_CHECK(cudaMemsetAsync(c.d_flags, 0, sizeof(int) * FLAG_COUNT, s));
         cholesky_inplace(c.d_A, c.K, c.d_flags + FLAG_CHOL, s);
+        c.mu_count = 0;   // a new geometry: no settled chemical potential yet
         tri_inverse_lower(c.d_A, c.d_Linv, c.K, c.d_B, s);
+        if (c.Kp > 0) cg_split_linv(c, s);   // L^-1, L^-T as FP16 pairs for the mixed congruences
+        if (c.d_VNL) launch_nonlocal(c, s);  // V^NL, once per geometry (Supp. A.2.2)
         int flags[FLAG_COUNT];
         read_flags(c, s, flags);
         if (flags[FLAG_CHOL]) throw Error(DFT_ENOTCONV, "overlap matrix is not positive definite");
+        if (flags[FLAG_RANGE]) throw Error(DFT_EINTERNAL, "L^-1 is outside the range of the FP16 pair");
         c.have_chol = true;
+    });
+}
+
+dft_status dft_nonlocal_matrix(dft_ctx* ctx, double* VNL, void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0 || !VNL) throw Error(DFT_EINVAL, "null argument");
+        require_aligned16({VNL});
+        if (!c.have_chol) throw Error(DFT_EINVAL, "call dft_overlap_kinetic first");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t K2 = sizeof(double) * (size_t)c.K * c.K;
+        if (c.d_VNL) DFT_CUDA_CHECK(cudaMemcpyAsync(VNL, c.d_VNL, K2, cudaMemcpyDeviceToDevice, s));
+        else DFT_CUDA_CHECK(cudaMemsetAsync(VNL, 0, K2, s));
     });
 }
 
@@ -853,7 +982,28 @@ dft_status dft_scf_step(dft_ctx* ctx, double* n_in_out, double* v_ks_out, double
         tm.mark(0);
         scf_head(c, n_in_out, s);
         tm.mark(1);
-        density_matrix_impl(c, c.d_F, c.d_P, &loc, s, &tm, 1);
+        // Skip the moments pass while mu has settled: the last two cycles'
+        // chemical potentials within MU_SETTLED kT.  The expansion is then taken
+        // at the last mu and the FP64 correction moves mu to first order; a
+        // Newton step beyond MU_REDO kT (first-order error no longer small, or
+        // no states at the Fermi level) runs the cycle's density matrix again
+        // with the moments pass.
+        const bool reuse = c.p.reuse_mu && c.p.precision != DFT_PREC_FP64 && !c.p.skip_correction &&
+                           c.mu_count >= 2 && std::fabs(c.p.beta * (c.mu_hist[0] - c.mu_hist[1])) < MU_SETTLED;
+        if (reuse) {
+            const double mu0 = c.mu_hist[0];
+            density_matrix_impl(c, c.d_F, c.d_P, &loc, s, &tm, 1, &mu0);
+            loc.mu_reused = 1;
+            if (!(std::fabs(c.p.beta * c.mu_step_raw) <= MU_REDO)) {
+                density_matrix_impl(c, c.d_F, c.d_P, &loc, s, &tm, 1);
+                loc.mu_reused = 0;
+            }
+        } else {
+            density_matrix_impl(c, c.d_F, c.d_P, &loc, s, &tm, 1);
+        }
+        c.mu_hist[1] = c.mu_hist[0];
+        c.mu_hist[0] = c.mu_last;
+        c.mu_count++;
         scf_tail(c, n_in_out, v_ks_out, P_out, &loc, s, &tm);
         loc.ms_stage[0] = tm.ms(0, 1);
         for (int i = 1; i < 6; ++i) loc.ms_stage[i] = tm.ms(i, i + 1);
@@ -940,6 +1090,9 @@ dft_status dft_scf_step_batched(dft_ctx* const* ctxs, int n, double* const* n_in
         fork_systems(cs, s, [&](Ctx& c, int q, cudaStream_t as) {
             tc_rho_finish(c, as);
             dm_finish(c, c.d_P, &loc[q], as);
+            c.mu_hist[1] = c.mu_hist[0];
+            c.mu_hist[0] = c.mu_last;
+            c.mu_count++;
             scf_tail(c, n_in_out[q], nullptr, nullptr, &loc[q], as, nullptr);
         });
         tm.mark(5);
@@ -977,7 +1130,7 @@ dft_status dft_density_from_potential(dft_ctx* ctx, const double* v_grid, double
         require_aligned16({v_grid, n_out});
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         launch_quadrature(c, v_grid, c.d_F, s);
-        launch_axpby_mat(c.K, 1.0, c.d_T, 1.0, c.d_F, c.d_F, s);
+        add_one_electron(c, c.d_F, s);
         dft_info loc{};
         density_matrix_impl(c, c.d_F, c.d_P, &loc, s, nullptr, 0);
         launch_collocate(c, c.d_P, n_out, s);

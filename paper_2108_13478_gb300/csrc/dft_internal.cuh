@@ -61,6 +61,7 @@ constexpr int TC_LISTS = 3;           // tile lists: 256-wide, 128-wide, 256-wid
 struct TcFlow {
     int l0 = 0, nsteps = 0, cshift = 0;
     int* cnt = nullptr;
+    int bias = 0;   // added to the producer's counter targets (0; 1 only to test the waits' expiry)
 };
 
 // launch configuration of the tensor-core step (chosen by the autotuner)
@@ -82,6 +83,11 @@ struct Ctx {
     dft_params p{};
     std::vector<Fn> fn_host;
     std::vector<double> xyz_host;
+    // non-local KB projectors (Supp. A.2.2): one Fn record per projector,
+    // their energies, and the width of their 1D tables
+    std::vector<Fn> pj_host;
+    std::vector<double> pje_host;
+    int pj_w = 0;
     int tab_w = 0;               // table width per function and axis
     int ntile[3] = {0, 0, 0};
     long long n_tiles = 0, tile_nnz = 0;
@@ -123,6 +129,12 @@ struct Ctx {
     double* d_ghat = nullptr;    // [nfft_c] real spectrum of the Coulomb kernel
     cufftDoubleComplex* d_fft_c = nullptr;  // [nfft_c]
     double* d_kerker = nullptr;  // Kerker weights on the unpadded box [nz][ny][nx/2+1]
+    Fn* d_pj = nullptr;          // KB projectors [np]
+    double* d_pje = nullptr;     // their energies [np]
+    double* d_pjtab = nullptr;   // their 1D tables [np][3][pj_w]
+    double* d_nlB = nullptr;     // projections B [np x K], and diag(e) B
+    double* d_nlEB = nullptr;
+    double* d_VNL = nullptr;     // V^NL, K x K (null without projectors)
     cufftDoubleComplex* d_kc = nullptr;
 
     int cheb_cap = 0;            // capacity of coefficient arrays
@@ -140,6 +152,14 @@ struct Ctx {
     CUtensorMap tm_rho;          // rho pairs as FP32, 32 x 128 boxes (16 pairs per row), 128-byte swizzle
     CUtensorMap tm_xm[4];        // X maps with 64 x 16 boxes, 128-byte swizzle (mirror of an epilogue slab)
     CUtensorMap tm_xs[4];        // X maps with 16 x 128 boxes, 32-byte swizzle (epilogue slabs)
+    // split-precision congruences (mixed path): L^-1 and L^-T as FP16 pairs
+    // [Kp x Kp], their maps with 128-row [0] and 256-row [1] boxes (32-wide
+    // k-blocks), and the H pair seen with 256-row boxes (holds F's pair then)
+    void* d_li16[2] = {nullptr, nullptr};
+    void* d_lt16[2] = {nullptr, nullptr};
+    CUtensorMap tm_li[2][2];
+    CUtensorMap tm_lt[2][2];
+    CUtensorMap tm_h256[2];
     // batch area (device): system table, tensor maps (16 per system), tile
     // lists of both tile widths
     TcSys* d_systab = nullptr;
@@ -174,6 +194,11 @@ struct Ctx {
     cufftHandle plan_f = 0, plan_b = 0;
     cufftHandle kplan_f = 0, kplan_b = 0;
     bool have_chol = false;
+    // chemical potential of the last two SCF cycles (after the FP64
+    // correction), for skipping the moments pass once it has settled
+    double mu_hist[2] = {0, 0};
+    int mu_count = 0;
+    double mu_last = 0, mu_step_raw = 0;   // of the last density matrix: final mu, Newton step
     double e_prev = 0;
     bool have_prev = false;
     int iter = 0;
@@ -192,13 +217,23 @@ enum {
     SCAL_EKIN = 262,
     SCAL_RES = 263,
     SCAL_E0 = 264, SCAL_E1 = 265, SCAL_E2 = 266,   // grid energy terms
+    SCAL_ENL = 267,      // Tr[P V^NL]
     SCAL_PULAY = 268,    // 16 Pulay dots, then 16 coefficients
-    SCAL_COUNT = 300
+    SCAL_DMU = 300,      // FP64 correction after the mixed recurrence: mu shift,
+    SCAL_NE_UNC = 301,   // 2 Tr[rho] before it,
+    SCAL_CORR_BAND = 302,   // Tr[(rho - rho^2) F~]
+    SCAL_DMU_RAW = 303,  // its Newton step before the trust check
+    SCAL_COUNT = 304
 };
-enum { FLAG_SPECTRUM = 0, FLAG_CHOL = 1, FLAG_MU = 2, FLAG_TIMEOUT = 3, FLAG_COUNT = 8 };
+// FLAG_RANGE: a split-precision operand or product left the FP16 pair's range
+enum { FLAG_SPECTRUM = 0, FLAG_CHOL = 1, FLAG_MU = 2, FLAG_TIMEOUT = 3, FLAG_RANGE = 4, FLAG_COUNT = 8 };
 
 // ---- grid kernels (k_grid.cu) ----
 void launch_build_tables(const Ctx& c, cudaStream_t s);
+// the same tables for any set of Fn records (the KB projectors)
+void launch_build_tables_for(const Ctx& c, const Fn* fn, int count, int W, double* tab, cudaStream_t s);
+// V^NL = B^T diag(e) B from the grid projections of the basis on the KB projectors (k_nonlocal.cu)
+void launch_nonlocal(const Ctx& c, cudaStream_t s);
 // FP64 kernels on the FP64 path, FP32 arithmetic (FP64 in and out) on the mixed path
 void launch_collocate(const Ctx& c, const double* P, double* n, cudaStream_t s);
 void launch_quadrature(const Ctx& c, const double* v, double* V, cudaStream_t s);
@@ -283,6 +318,16 @@ void tc_moments_from_fixed_range(const TcBatch& b, int j0, int j1, cudaStream_t 
 void tc_moment_reduce_batch(const TcBatch& b, int j, cudaStream_t s);
 void tc_set_limits(const TcBatch& b, Ctx* const* sys, const int* lim, const int* mom_last, cudaStream_t s);
 void tc_rho_finish(const Ctx& c, cudaStream_t s);
+
+// ---- split-precision congruences and the FP64 correction (k_congr_tc.cu) ----
+void cg_setup(Ctx& c);                                   // tensor maps of the pairs below
+void cg_split_linv(const Ctx& c, cudaStream_t s);        // L^-1, L^-T -> FP16 pairs (once per geometry)
+void cg_transform_f(const Ctx& c, const double* F, double* Ft, cudaStream_t s);   // Ft = L^-1 F L^-T (FP64 out)
+void cg_split_rho(const Ctx& c, cudaStream_t s);         // c.d_rho (FP64) -> X pair 0
+// electron-count correction: dmu from 2 Tr[rho] = N_e with d rho/d mu =
+// beta (rho - rho^2); rho += dmu beta (rho - rho^2) (needs the rho pair)
+void cg_correct_rho(const Ctx& c, cudaStream_t s);
+void cg_back_transform(const Ctx& c, double* P, cudaStream_t s);   // P = L^-T rho L^-1 from the rho pair
 
 // ---- Poisson + LDA (k_poisson.cu) ----
 void poisson_setup(Ctx& c, cudaStream_t s);

@@ -227,13 +227,16 @@ __global__ void k_gaussian_sum(const double* __restrict__ xyz, int n_atoms, int 
 
 }  // namespace
 
-void launch_build_tables(const Ctx& c, cudaStream_t s) {
-    long long total = (long long)c.K * 3 * c.tab_w;
+void launch_build_tables_for(const Ctx& c, const Fn* fn, int count, int W, double* tab, cudaStream_t s) {
+    long long total = (long long)count * 3 * W;
+    if (total == 0) return;
     int bs = 256;
-    k_build_tables<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(c.d_fn, c.K, c.tab_w, c.origin[0],
-                                                                    c.origin[1], c.origin[2], c.h, c.d_tab);
+    k_build_tables<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(fn, count, W, c.origin[0], c.origin[1],
+                                                                    c.origin[2], c.h, tab);
     check_launch("build_tables");
 }
+
+void launch_build_tables(const Ctx& c, cudaStream_t s) { launch_build_tables_for(c, c.d_fn, c.K, c.tab_w, c.d_tab, s); }
 
 void launch_collocate(const Ctx& c, const double* P, double* n, cudaStream_t s) {
     if (c.p.precision == DFT_PREC_FP64)

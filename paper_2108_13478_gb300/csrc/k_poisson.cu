@@ -100,7 +100,27 @@ __device__ __forceinline__ double cbrt_pos(double d) {
     return fma(-t * r, 1.0 / 3.0, y0);
 }
 
-// v_ks = v_loc + v_H + v_x; energy partials sum v_loc n, v_H rho, eps_x n
+// PW92 LDA correlation of the spin-unpolarised gas (the paper's LDA,
+// Section 4): eps_c(r_s) = -2 A (1 + a1 r_s) ln(1 + 1 / (2 A (b1 r_s^1/2 +
+// b2 r_s + b3 r_s^3/2 + b4 r_s^2))) and v_c = eps_c - (r_s / 3) d eps_c/d r_s,
+// with Perdew and Wang's published constants for the unpolarised gas
+__device__ __forceinline__ void pw92(double rs, double& v, double& e) {
+    const double A = 0.031091, a1 = 0.21370, b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
+    const double sr = sqrt(rs);
+    const double q0 = -2.0 * A * (1.0 + a1 * rs);
+    const double q1 = 2.0 * A * (sr * (b1 + b3 * rs) + rs * (b2 + b4 * rs));
+    const double dq1 = A * (b1 / sr + 2.0 * b2 + 3.0 * b3 * sr + 4.0 * b4 * rs);
+    const double lg = log1p(1.0 / q1);
+    e = q0 * lg;
+    const double de = -2.0 * A * a1 * lg - q0 * dq1 / (q1 * (q1 + 1.0));
+    v = e - rs * de * (1.0 / 3.0);
+}
+
+constexpr double RS0 = 0.62035049089940001;   // (3 / (4 pi))^(1/3): r_s = RS0 n^(-1/3)
+
+// v_ks = v_loc + v_H + v_xc; energy partials sum v_loc n, v_H rho, eps_xc n
+// (v_xc: Slater exchange, plus PW92 correlation with C)
+template <bool C>
 __global__ void __launch_bounds__(256) k_vks(int nx, int ny, int nz, int Nx, int Ny, const double* __restrict__ pad,
                                              const double* __restrict__ n, const double* __restrict__ nion,
                                              const double* __restrict__ vloc, double* __restrict__ vks,
@@ -112,8 +132,15 @@ __global__ void __launch_bounds__(256) k_vks(int nx, int ny, int nz, int Nx, int
         const int iz = line / ny, iy = line - iz * ny;
         double vh = pad[((long long)iz * Ny + iy) * Nx + ix];
         double d = n[g];
-        double c = d > 1e-30 ? CX * cbrt_pos(d) : 0.0;
+        const double cb = d > 1e-30 ? cbrt_pos(d) : 0.0;
+        double c = CX * cb;
         double vx = -c, ex = -0.75 * c;
+        if (C && d > 1e-30) {
+            double vc, ec;
+            pw92(RS0 / cb, vc, ec);
+            vx += vc;
+            ex += ec;
+        }
         double vl = vloc[g];
         if (vks) vks[g] = vl + vh + vx;
         double rho = d - (nion ? nion[g] : 0.0);
@@ -289,8 +316,12 @@ void hartree_xc(Ctx& c, const double* n, double* vks, bool energies, cudaStream_
     check_launch("mul_real");
     cufft_check(cufftExecZ2D(c.plan_b, c.d_fft_c, c.d_fft_r), "exec Z2D");
     int np = (int)std::min<long long>(1184, (c.ng + 255) / 256);
-    k_vks<<<np, 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.d_fft_r, n, nion, c.d_vloc, vks,
-                             c.d_part);
+    if (c.p.xc == DFT_XC_PW92)
+        k_vks<true><<<np, 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.d_fft_r, n, nion, c.d_vloc,
+                                       vks, c.d_part);
+    else
+        k_vks<false><<<np, 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.d_fft_r, n, nion, c.d_vloc,
+                                        vks, c.d_part);
     check_launch("vks");
     if (energies) {
         k_energy_reduce<<<1, 256, 0, s>>>(np, c.d_part, c.h * c.h * c.h, c.d_scal);

@@ -66,6 +66,14 @@ extern "C" dft_status dft_spectral_bounds_static(dft_ctx* ctx, const double* F, 
         double* Ft = base + (size_t)MAX_K * MAX_K;
         double* vec = base + 2ull * MAX_K * MAX_K;
         double* scal = vec + 4ull * MAX_K;
+        if (c.p.e_max > c.p.e_min) {
+            // fixed bounds in the parameters: dft_density_matrix takes them as
+            // they are, without Lanczos
+            bounds[0] = c.p.e_min;
+            bounds[1] = c.p.e_max;
+            c.err.clear();
+            return DFT_OK;
+        }
         // the scalar block starts from zero on every call (the array keeps the
         // previous call's contents)
         DFT_CUDA_CHECK(cudaMemsetAsync(scal, 0, sizeof(double) * SCAL_COUNT, s));

@@ -86,19 +86,38 @@ def start_potential(ctx):
     return v
 
 
-def run_scf(ctx, v_first, max_iter=80, tol_e=1e-8, tol_n=1e-5, e_ref=None, e_tol=1e-5):
+def run_scf(ctx, v_first, max_iter=80, tol_e=1e-8, tol_n=1e-5, e_ref=None, e_tol=1e-5, timings=None):
     """SCF cycle that starts from a potential: n_1 = n[v_first], then Pulay
     cycles.  Returns (cycles, final info, converged v_KS, cycles to reach
-    |E - e_ref| / atom < e_tol if e_ref is given)."""
+    |E - e_ref| / atom < e_tol if e_ref is given).  timings (a dict, if
+    given) receives the GPU seconds (CUDA events) of the start and of every
+    cycle, and the seconds until e_tol was reached."""
+    torch = ctx.torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
     n = ctx.grid_array()
     B.dft_density_from_potential(ctx.ctx, ctx._grid(v_first, "v_first"), n)
+    ev[1].record()
+    ev[1].synchronize()
+    t = ev[0].elapsed_time(ev[1]) / 1000.0
+    if timings is not None:
+        timings.update(start_s=t, cycle_s=[], hit_s=None)
     v = ctx.grid_array()
     hit = None
     info = None
     for it in range(max_iter):
+        ev[0].record()
         info = ctx.scf_step(n, v_ks_out=v)
+        ev[1].record()
+        ev[1].synchronize()
+        dt = ev[0].elapsed_time(ev[1]) / 1000.0
+        t += dt
+        if timings is not None:
+            timings["cycle_s"].append(dt)
         if e_ref is not None and hit is None and abs(info.e_total / ctx.n_atoms - e_ref) < e_tol:
             hit = it + 1
+            if timings is not None:
+                timings["hit_s"] = t
         if it > 0 and abs(info.de_per_atom) < tol_e and info.residual < tol_n:
             return it + 1, info, v, hit
     return max_iter, info, v, hit
@@ -127,3 +146,68 @@ def train(ws, data, epochs=60, lr=3e-3, log=None):
         if log:
             log(ep, loss)
     return hist
+
+
+def compare_starts(ws, system, max_iter=80, **kw):
+    """SCF from the superposition-of-atoms potential and from the network's
+    potential on one system: cycles and GPU seconds to 1e-5 Ha/atom of the
+    converged energy (from a tight run of the atomic start) and to full
+    convergence."""
+    ref = scf_context(system, **kw)
+    _, info, _, _ = run_scf(ref, start_potential(ref), max_iter=max_iter + 40, tol_e=1e-9, tol_n=1e-6)
+    e_ref = info.e_total / system.n_atoms
+    ref.close()
+    out = {"n_atoms": system.n_atoms, "n_basis": int(system.n_basis), "e_ref_per_atom": e_ref}
+    for key, warm in (("atoms", False), ("warm", True)):
+        ctx = scf_context(system, **kw)
+        v0 = start_potential(ctx)
+        if warm:
+            v0 = ws.potential(ctx, v0)
+        tm = {}
+        n_conv, _, _, hit = run_scf(ctx, v0, max_iter=max_iter, e_ref=e_ref, timings=tm)
+        out[key] = {"cycles_to_1e-5": hit, "seconds_to_1e-5": tm["hit_s"], "cycles_to_convergence": n_conv,
+                    "seconds_to_convergence": tm["start_s"] + sum(tm["cycle_s"])}
+        ctx.close()
+    return out
+
+
+def main(argv=None):
+    """Train on seeded spheres with the library's own converged potentials and
+    compare the two starts on a larger sphere; prints one JSON record."""
+    import argparse
+    import json
+    import os
+    import sys
+    import time
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import workloads as w
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=20, help="training spheres")
+    ap.add_argument("--rmin", type=float, default=10.0)
+    ap.add_argument("--rmax", type=float, default=20.0)
+    ap.add_argument("--test-radius", type=float, default=25.0)
+    ap.add_argument("--epochs", type=int, default=120)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--seed", type=int, default=1000)
+    a = ap.parse_args(argv)
+    t0 = time.time()
+    radii = np.random.default_rng(a.seed).uniform(a.rmin, a.rmax, a.train)
+    systems = [w.config_system(f"sphereR{r:.3f}", seed=a.seed + i) for i, r in enumerate(radii)]
+    data = training_set(systems)
+    t_data = time.time() - t0
+    ws = WarmStart(init_params(seed=1))
+    hist = train(ws, data, epochs=a.epochs, lr=a.lr)
+    for c, _, _ in data:
+        c.close()
+    test = w.config_system(f"sphereR{a.test_radius:g}", seed=99)
+    res = compare_starts(ws, test)
+    rec = {"train_spheres": a.train, "train_radii": [round(float(r), 3) for r in radii],
+           "train_atoms": [s.n_atoms for s in systems], "epochs": a.epochs, "loss_first": hist[0],
+           "loss_last": hist[-1], "test_radius": a.test_radius, "test": res, "targets_s": t_data,
+           "wall_s": time.time() - t0}
+    print(json.dumps(rec), flush=True)
+    return rec
+
+
+if __name__ == "__main__":
+    main()

@@ -3,6 +3,7 @@ point declared in include/dft.h, and sizes workspaces without a GPU."""
 import ctypes
 import os
 import re
+import types
 
 import numpy as np
 import pytest
@@ -223,3 +224,42 @@ def test_context_methods_check_each_argument(built, monkeypatch):
         with pytest.raises(ValueError):
             bad()
     assert len(calls) == 6
+
+
+def test_static_bounds_refuse_buffers_the_kernels_cannot_read(built, monkeypatch):
+    """The allocation-free bounds call reads K x K doubles from F's pointer:
+    the binding refuses host, non-float64, non-square or non-contiguous
+    tensors, and the Context method also a size other than K x K, before the
+    library is called."""
+    import torch
+    import paper_2108_13478_gb300 as dft
+    from paper_2108_13478_gb300 import _binding as B
+
+    class Mat(Dev):
+        def __init__(self, shape, dtype=None, contiguous=True):
+            super().__init__(int(np.prod(shape)), dtype, contiguous)
+            self.shape = shape
+
+        def dim(self):
+            return len(self.shape)
+
+    called = []
+    monkeypatch.setattr(B, "lib", types.SimpleNamespace(
+        dft_spectral_bounds_static=lambda *a: called.append(a) or 0, dft_last_error=lambda c: b""))
+    monkeypatch.setattr(B, "_stream", lambda s=None: None)
+    monkeypatch.setattr(B, "_ptr", lambda t: None)
+    with pytest.raises(ValueError, match="CUDA"):
+        dft.dft_spectral_bounds_static(None, torch.zeros((4, 4), dtype=torch.float64))
+    with pytest.raises(ValueError, match="float64"):
+        dft.dft_spectral_bounds_static(None, Mat((4, 4), torch.float32))
+    with pytest.raises(ValueError, match="square"):
+        dft.dft_spectral_bounds_static(None, Mat((4, 5)))
+    with pytest.raises(ValueError, match="contiguous"):
+        dft.dft_spectral_bounds_static(None, Mat((4, 4), contiguous=False))
+    c = object.__new__(dft.Context)
+    c.torch, c.device, c.K, c.grid_shape, c.ctx = torch, torch.device("cpu"), 4, (2, 3, 5), None
+    with pytest.raises(ValueError, match="elements"):
+        c.spectral_bounds_static(Mat((3, 3)))
+    assert called == []
+    c.spectral_bounds_static(Mat((4, 4)))
+    assert len(called) == 1

@@ -86,7 +86,11 @@ def test_reference_arm_line_keeps_the_contract(capsys):
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
-    assert d["value"] > 0 and d["ms_per_step"] == pytest.approx(1000.0 * s.n_basis / d["value"])
+    # a step is one bounded sample: its wall time, with the projected time of a
+    # whole oracle SCF step (the basis of value) beside it
+    assert d["value"] > 0 and d["projected_ms_per_scf_step"] == pytest.approx(1000.0 * s.n_basis / d["value"])
+    assert 0 < d["ms_per_step"] < 60000.0 and d["value_kind"].startswith("projected")
+    assert len(d["cpu_baseline"]["sample"]) <= 120
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

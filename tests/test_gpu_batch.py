@@ -1,8 +1,12 @@
 """Batched SCF steps of ragged systems (one persistent tensor-core launch per
-recurrence step for all systems) against the same steps run one system at a
-time.  Each tile's arithmetic is the same in both; the quadrature's FP64
-atomics leave differences at the 1e-16 level, which two SCF cycles carry to
-about 1e-11 in the density."""
+recurrence step for all systems) against the FP64 oracle's converged
+energies, and against the same steps run one system at a time.  Each tile's
+arithmetic is the same in both; the quadrature's FP64 atomics leave
+differences at the 1e-16 level, which two SCF cycles carry to about 1e-11 in
+the density."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -45,6 +49,54 @@ def test_batched_equals_one_by_one(shape, monkeypatch):
             assert abs(a.mu - b.mu) <= 1e-9, name
             assert float((ds - db).abs().max()) <= 1e-9 * float(ds.abs().max()), name
     for c in solo + batch:
+        c.close()
+
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+# K = 80, 370 (a ragged row and column tile) and 640 (a padded one)
+ORACLE_NAMES = ["tiny8", "tiny37", "cluster64"]
+
+
+@pytest.mark.parametrize("shape", [None, "32,0,256,0,0,0,1"])
+def test_batched_scf_converges_to_the_oracle(shape, monkeypatch):
+    """A ragged batch run to convergence with dft_scf_step_batched only (the
+    mixer, model and Chebyshev tail of the benchmark), each system's energy
+    against the oracle's converged energy (tests/golden/scf_<name>.json, from
+    the exact density matrix): every system must meet the stop criterion of
+    the one-system test (|dE|/atom < 1e-7 between cycles and max|n_out - n_in|
+    < 1e-5) and land within 1e-5 Ha/atom.  shape None: the tuned launch
+    shape; the other: one dataflow launch per pass over all systems' tiles."""
+    gold = {}
+    for n in ORACLE_NAMES:
+        p = os.path.join(GOLD, f"scf_{n}.json")
+        if not os.path.exists(p):
+            pytest.skip(f"no oracle golden energy for {n}")
+        gold[n] = json.load(open(p))
+        assert gold[n]["converged"]
+    if shape:
+        monkeypatch.setenv("DFT_TC_SHAPE", shape)
+    ctxs = []
+    for n in ORACLE_NAMES:
+        c = dft.Context(w.config_system(n), precision=dft.DFT_PREC_FP16X3, model=dft.DFT_MODEL_NEUTRAL,
+                        mixer=dft.DFT_MIX_PULAY, mix_alpha=0.3, kerker_q0=0.8, mix_history=8, cheb_tail_tol=1e-6)
+        c.overlap_kinetic()
+        ctxs.append(c)
+    dens = [c.initial_density() for c in ctxs]
+    done = {n: None for n in ORACLE_NAMES}
+    for it in range(120):
+        infos = dft.dft_scf_step_batched([c.ctx for c in ctxs], dens)
+        for n, info in zip(ORACLE_NAMES, infos):
+            if done[n] is None and it > 0 and abs(info.de_per_atom) < 1e-7 and info.residual < 1e-5:
+                done[n] = (it + 1, info.e_total / w.config_system(n).n_atoms)
+        if all(v is not None for v in done.values()):
+            break
+    for n in ORACLE_NAMES:
+        assert done[n] is not None, f"{n} did not converge in the batch"
+        cycles, e = done[n]
+        print(f"batched {shape or 'tuned'} {n}: {cycles} cycles, E/atom {e:.10f} vs oracle "
+              f"{gold[n]['E_per_atom']:.10f}, |dE| {abs(e - gold[n]['E_per_atom']):.2e}")
+        assert abs(e - gold[n]["E_per_atom"]) < 1e-5
+    for c in ctxs:
         c.close()
 
 

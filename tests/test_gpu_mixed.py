@@ -124,3 +124,33 @@ def test_mixed_launch_shapes(name, monkeypatch):
         d = float(np.max(np.abs(P - Ps[0])))
         print(f"{name} shape {shape} vs {SHAPES[0]}: max|dP| {d:.3e}")
         assert d < 1e-5
+
+
+def test_expired_waits_return_timeout_and_leave_the_context_usable(monkeypatch):
+    """The dataflow launch's block-counter waits are bounded (1 s of the
+    GPU's global timer).  With DFT_TEST_EXPIRE_WAITS set, every producer wait
+    asks for one write more than any tile makes, so the waits run out: the
+    CTAs record FLAG_TIMEOUT, drain their copies and MMAs, free tensor memory
+    and return, and the call reports DFT_ETIMEOUT within seconds.  The same
+    context then computes the oracle's density matrix."""
+    import time
+    s, st, F, lo, hi, n_c, ref = case("tiny37")
+    monkeypatch.setenv("DFT_TC_SHAPE", "32,0,256,0,0,0,1")
+    ctx = dft.Context(s, precision=dft.DFT_PREC_FP16X3, e_min=lo, e_max=hi, cheb_order=n_c,
+                      model=dft.DFT_MODEL_NEUTRAL)
+    ctx.overlap_kinetic()
+    monkeypatch.setenv("DFT_TEST_EXPIRE_WAITS", "1")
+    t0 = time.time()
+    with pytest.raises(dft.DftError) as e:
+        ctx.density_matrix(dev(F))
+    took = time.time() - t0
+    print(f"expired waits: {e.value} after {took:.1f} s")
+    assert e.value.status == dft._binding.DFT_ETIMEOUT
+    assert took < 60.0
+    monkeypatch.delenv("DFT_TEST_EXPIRE_WAITS")
+    P, info = ctx.density_matrix(dev(F))
+    dP = P.cpu().numpy() - ref["P"]
+    e_kin = abs(2 * np.sum(dP * st.T)) / s.n_atoms
+    assert info.spectrum_ok == 1
+    assert float(np.max(np.abs(dP))) < 1e-4 and e_kin < 1e-5
+    ctx.close()

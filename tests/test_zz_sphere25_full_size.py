@@ -112,14 +112,17 @@ def test_density_matrix(sphere, ctx):
     assert e_kin < 1e-5 and e_band < 1e-5
 
 
-def test_density_matrix_at_the_benchmark_order(sphere):
+@pytest.mark.parametrize("skip", [0, 1])
+def test_density_matrix_at_the_benchmark_order(sphere, skip):
     """The benchmark runs the mixed path with the Chebyshev tail 1e-6 (about
     40% fewer steps than 1e-10; the oracle puts its truncation error near
-    1e-10 Ha/atom here): the same gates hold."""
+    1e-10 Ha/atom here): the same gates hold, with the FP64 electron-count
+    correction after the recurrence (skip = 0, the default) and without it."""
     s, ex, F, T = sphere["s"], sphere["ex"], sphere["F"], sphere["T"]
     mp = pytest.MonkeyPatch()
     mp.setenv("DFT_TC_SHAPE", FLOW)
-    c = dft.Context(s, precision=dft.DFT_PREC_FP16X3, model=dft.DFT_MODEL_NEUTRAL, cheb_tail_tol=1e-6)
+    c = dft.Context(s, precision=dft.DFT_PREC_FP16X3, model=dft.DFT_MODEL_NEUTRAL, cheb_tail_tol=1e-6,
+                    skip_correction=skip)
     try:
         c.overlap_kinetic()
         P, info = c.density_matrix(dev(F))
@@ -132,8 +135,9 @@ def test_density_matrix_at_the_benchmark_order(sphere):
     e_kin = abs(2 * np.sum(dP * T)) / s.n_atoms
     e_band = abs(2 * np.sum(dP * F)) / s.n_atoms
     n_e = 2 * np.sum(P * sphere["S"])
-    print(f"sphere25 fp16x3 tail 1e-6: N_C {info.n_cheb}  max|dP| {err:.3e}  dEkin/atom {e_kin:.3e}  "
-          f"dEband/atom {e_band:.3e}  2Tr[PS] {n_e:.6f}")
+    print(f"sphere25 fp16x3 tail 1e-6 {'without' if skip else 'with'} correction: N_C {info.n_cheb}  "
+          f"max|dP| {err:.3e}  dEkin/atom {e_kin:.3e}  dEband/atom {e_band:.3e}  2Tr[PS] {n_e:.6f}  "
+          f"dmu {info.mu_correction:+.3e}  stages {[round(x, 1) for x in info.ms_stage]}")
     assert info.spectrum_ok == 1
     assert abs(n_e - s.n_electrons) < 1e-5 * s.n_electrons
     assert err < 1e-4
