@@ -10,6 +10,93 @@ import numpy as np
 from scipy import special
 
 
+# Table A.1: the real solid harmonics of degree l <= 2 as weights of the
+# Cartesian monomials x^i y^j z^k (i + j + k = l), in the table's order of m;
+# p keeps the Cartesian order x, y, z (all its weights are 1)
+SOLID = {
+    0: [[((0, 0, 0), 1.0)]],
+    1: [[((1, 0, 0), 1.0)], [((0, 1, 0), 1.0)], [((0, 0, 1), 1.0)]],
+    2: [[((2, 0, 0), math.sqrt(3.0) / 2.0), ((0, 2, 0), -math.sqrt(3.0) / 2.0)],   # m = 2
+        [((1, 1, 0), math.sqrt(3.0))],                                             # m = 1
+        [((2, 0, 0), -0.5), ((0, 2, 0), -0.5), ((0, 0, 2), 1.0)],                  # m = 0
+        [((0, 1, 1), math.sqrt(3.0))],                                             # m = -1
+        [((1, 0, 1), math.sqrt(3.0))]],                                            # m = -2
+}
+CART_D = [(2, 0, 0), (0, 2, 0), (0, 0, 2), (1, 1, 0), (1, 0, 1), (0, 1, 1)]
+
+
+def monomial_norm(zeta, l):
+    """Normalisation of x^l exp(-zeta r^2): (2 zeta/pi)^(3/4) (4 zeta)^(l/2) / sqrt((2l-1)!!)."""
+    dfact = {0: 1.0, 1: 1.0, 2: 3.0}[l]
+    return (2.0 * zeta / math.pi) ** 0.75 * (4.0 * zeta) ** (0.5 * l) / math.sqrt(dfact)
+
+
+def is_contracted(sysm):
+    return getattr(sysm, "shell_nprim", None) is not None or bool(np.any(np.asarray(sysm.shell_l) > 1))
+
+
+def expansion(sysm):
+    """Basis functions as sums of Cartesian Gaussian terms (Eqs. A.1-A.3):
+    phi_a = N_a sum_{t in a} c_t x^i y^j z^k exp(-zeta_t |r - R|^2), with
+    c_t = d_p w^{ijk}_{lm} (contraction coefficient times Table A.1 weight)
+    times the monomial's normalisation, and N_a making phi_a of unit norm.
+    Returns (terms, C): terms in the layout of functions() (norm = c_t) plus,
+    for the window of each term, its function's most diffuse exponent
+    ('wzeta') and l ('wl') (Supp. A.1.1); C (K x Kt) with C[a, t] = N_a for
+    t in a.  For uncontracted s/p shells C is None and terms are functions()."""
+    if not is_contracted(sysm):
+        return functions(sysm), None
+    nprim = getattr(sysm, "shell_nprim", None)
+    off = 0
+    cen, zet, ls, pw, nrm, atm, wz, wl, par = [], [], [], [], [], [], [], [], []
+    K = 0
+    for s in range(len(sysm.shell_l)):
+        a = int(sysm.shell_atom[s])
+        l = int(sysm.shell_l[s])
+        if nprim is None:
+            prims = [(float(sysm.shell_exp[s]), 1.0)]
+        else:
+            n = int(nprim[s])
+            prims = list(zip(sysm.prim_exp[off:off + n], sysm.prim_coef[off:off + n]))
+            off += n
+        zmin = min(z for z, _ in prims)
+        comps = SOLID[l] if (l < 2 or sysm.spherical) else [[(c, 1.0)] for c in CART_D]
+        for comp in comps:
+            for z, d in prims:
+                for ijk, wgt in comp:
+                    cen.append(sysm.xyz[a])
+                    zet.append(z)
+                    ls.append(l)
+                    pw.append(ijk)
+                    nrm.append(d * wgt * monomial_norm(z, l))
+                    atm.append(a)
+                    wz.append(zmin)
+                    wl.append(l)
+                    par.append(K)
+            K += 1
+    terms = dict(center=np.array(cen), zeta=np.array(zet), l=np.array(ls, dtype=np.int64),
+                 pw=np.array(pw, dtype=np.int64), norm=np.array(nrm), atom=np.array(atm, dtype=np.int64),
+                 wzeta=np.array(wz), wl=np.array(wl, dtype=np.int64), parent=np.array(par, dtype=np.int64))
+    M = np.zeros((K, len(par)))
+    M[terms["parent"], np.arange(len(par))] = 1.0
+    S_t, _ = overlap_kinetic(terms)
+    Nrm = 1.0 / np.sqrt(np.einsum("at,ts,as->a", M, S_t, M))
+    return terms, Nrm[:, None] * M
+
+
+def contract(C, A):
+    """C A C^T for a term-level matrix A (A itself when C is None)."""
+    return A if C is None else C @ A @ C.T
+
+
+def overlap_kinetic_system(sysm):
+    """S and T of the system's basis functions (contracted when it has
+    contracted or d shells)."""
+    terms, C = expansion(sysm)
+    S, T = overlap_kinetic(terms)
+    return contract(C, S), contract(C, T)
+
+
 def functions(sysm):
     """Expand shells into basis functions (Eqs. A.1-A.3 with one primitive).
 
@@ -52,13 +139,21 @@ def window_halfwidth(zeta, l, eta):
     return np.sqrt(d2) / np.sqrt(zeta)
 
 
+def _window_params(fn):
+    """(zeta, l) that set the window: the function's own, or for the terms of
+    a contracted function those of the function (its most diffuse primitive)."""
+    if "wzeta" in fn:
+        return fn["wzeta"], fn["wl"]
+    return fn["zeta"], fn["l"]
+
+
 def window_ranges(sysm, fn, eta):
     """Grid-index range [lo, hi] per function and axis of the cubic window
     W_alpha (Supp. A.1.1): points with |x_g - R_x| <= L on every axis,
     clipped to the box.  Returns (lo, hi) int arrays of shape (K, 3); an empty
     range has lo > hi.
     """
-    L = window_halfwidth(fn["zeta"], fn["l"], eta)
+    L = window_halfwidth(*_window_params(fn), eta)
     o = sysm.grid_origin
     h = sysm.grid_h
     n = sysm.grid_n
@@ -150,13 +245,13 @@ def overlap_kinetic(fn, rows=None):
     for d in range(3):
         A = fn["center"][ri, d][:, None]
         B = fn["center"][None, :, d]
-        tab = _os_1d(a, b, A, B, 1, 3)
+        tab = _os_1d(a, b, A, B, 2, 4)
         i = fn["pw"][ri, d][:, None] + np.zeros((1, K), dtype=np.int64)
         j = fn["pw"][None, :, d] + np.zeros((len(ri), 1), dtype=np.int64)
         s_d = np.zeros((len(ri), K))
         t_d = np.zeros((len(ri), K))
-        for ii in range(2):
-            for jj in range(2):
+        for ii in range(3):
+            for jj in range(3):
                 m = (i == ii) & (j == jj)
                 s_ij = tab[ii][jj]
                 t_ij = -2.0 * b * b * tab[ii][jj + 2] + b * (2 * jj + 1) * tab[ii][jj]

@@ -30,9 +30,10 @@ def potential_matrix(sysm, v, eta=1e-10, windowed=True, planes=4):
     windowed=True restricts every function to its cubic window W_a (A.1.1),
     so the sum runs over W_a intersect W_b; windowed=False is the plain
     all-points definition.  v has shape (nz, ny, nx).  The overlap on the
-    grid (Eq. 2.1) is potential_matrix(v = 1).
+    grid (Eq. 2.1) is potential_matrix(v = 1).  Contracted functions (Eq.
+    A.1) are sums of Cartesian terms: V = C V_terms C^T (basis.expansion).
     """
-    fn = basis.functions(sysm)
+    fn, C = basis.expansion(sysm)
     tabs = basis.axis_tables(sysm, fn, eta if windowed else None)
     K = len(fn["zeta"])
     V = np.zeros((K, K))
@@ -41,7 +42,7 @@ def potential_matrix(sysm, v, eta=1e-10, windowed=True, planes=4):
         ph = _phi_slab(tabs, z0, z1)
         w = vf[z0:z1].reshape(-1)
         V += ph.T @ (w[:, None] * ph)
-    return V * sysm.grid_h ** 3
+    return basis.contract(C, V * sysm.grid_h ** 3)
 
 
 def potential_matrix_separable(sysm, factors, eta=1e-10, windowed=True, absolute=False):
@@ -57,10 +58,11 @@ def potential_matrix_separable(sysm, factors, eta=1e-10, windowed=True, absolute
     lengths (nx, ny, nz).  absolute=True sums the absolute values of the
     terms instead, h^3 sum_g |phi_a| |v| |phi_b|: the scale of a rounding-error
     bound on V_ab."""
-    fn = basis.functions(sysm)
+    fn, C = basis.expansion(sysm)
     tabs = basis.axis_tables(sysm, fn, eta if windowed else None)
     if absolute:
         tabs = [np.abs(t) for t in tabs]
+        C = None if C is None else np.abs(C)
         factors = [tuple(np.abs(np.asarray(f, dtype=np.float64)) for f in fr) for fr in factors]
     K = len(fn["zeta"])
     V = np.zeros((K, K))
@@ -81,14 +83,16 @@ def potential_matrix_separable(sysm, factors, eta=1e-10, windowed=True, absolute
             q = t.T @ (f[:, None] * t)
             term = q if term is None else np.multiply(term, q, out=term)
         V[np.ix_(idx, idx)] += term
-    return V * sysm.grid_h ** 3
+    return basis.contract(C, V * sysm.grid_h ** 3)
 
 
 def density_on_grid(sysm, P, eta=1e-10, windowed=True, planes=4):
     """n(r_g) = 2 sum_ab P_ab phi_a(r_g) phi_b(r_g)  (Eq. 2.7), evaluated as
     the column sum of Eq. A.5: n = sum_a 2 phi_a sum_b phi_b P_ba.
-    Returns an (nz, ny, nx) array."""
-    fn = basis.functions(sysm)
+    Returns an (nz, ny, nx) array.  Contracted functions: the same sum over
+    their Cartesian terms with P_terms = C^T P C."""
+    fn, C = basis.expansion(sysm)
+    P = P if C is None else C.T @ P @ C
     tabs = basis.axis_tables(sysm, fn, eta if windowed else None)
     nx, ny, nz = (int(t) for t in sysm.grid_n)
     n = np.zeros(nz * ny * nx)
@@ -112,7 +116,9 @@ def density_at(sysm, P, flat_idx, eta=1e-10, windowed=True, absolute=False):
     """n at selected flat grid indices (Eq. 2.7), for sampled checks.
     absolute=True sums the absolute values of the terms,
     2 sum_ab |phi_a| |P_ab| |phi_b|: the scale of a rounding-error bound on n."""
-    fn = basis.functions(sysm)
+    fn, C = basis.expansion(sysm)
+    if C is not None:
+        P = (np.abs(C).T @ np.abs(P) @ np.abs(C)) if absolute else C.T @ P @ C
     tabs = basis.axis_tables(sysm, fn, eta if windowed else None)
     ph = phi_points(sysm, fn, tabs, flat_idx)
     if absolute:
@@ -123,6 +129,8 @@ def density_at(sysm, P, flat_idx, eta=1e-10, windowed=True, absolute=False):
 def potential_entries(sysm, v, pairs, eta=1e-10, windowed=True):
     """Selected V_ab (Eq. A.6) summed over the intersection box of the two
     windows only, for sampled checks on large systems."""
+    if basis.is_contracted(sysm):
+        raise NotImplementedError("sampled pair sums are written for one-primitive functions")
     fn = basis.functions(sysm)
     lo, hi = basis.window_ranges(sysm, fn, eta)
     h3 = sysm.grid_h ** 3

@@ -71,8 +71,9 @@ def projectors(sysm, kb):
 def projections(sysm, kb, eta=1e-10, windowed=True):
     """B_pb = h^3 sum_{g in W_p and W_b} chi_p(r_g) phi_b(r_g): the grid
     projection of every basis function on every projector, summed point by
-    point over each projector's window box."""
-    fn = basis.functions(sysm)
+    point over each projector's window box.  Contracted functions: the
+    projections of their Cartesian terms, times C^T."""
+    fn, C = basis.expansion(sysm)
     pj = projectors(sysm, kb)
     tabs = basis.axis_tables(sysm, fn, eta if windowed else None)
     if windowed:
@@ -94,7 +95,7 @@ def projections(sysm, kb, eta=1e-10, windowed=True):
         chi = basis.phi_at({k: pj[k][[p]] for k in ("center", "zeta", "pw", "norm")}, pts)[:, 0]
         ph = grid_phi(sysm, tabs, flat.ravel())
         B[p] = h3 * (chi @ ph)
-    return B, pj
+    return (B if C is None else B @ C.T), pj
 
 
 def grid_phi(sysm, tabs, flat_idx):
@@ -117,6 +118,8 @@ def vnl_two_stage(sysm, kb, eta=1e-10):
     v_nl^C(r_g, r_g') = sum_p e_p chi_p(r_g) chi_p(r_g') on W^C x W^C (each
     projector restricted to its window), psi_Cb = v_nl^C phi_b h^3 on W^C,
     V^C_ab = phi_a . psi_Cb h^3, and V^NL = sum_C V^C."""
+    if basis.is_contracted(sysm):
+        raise NotImplementedError("written for one-primitive functions")
     fn = basis.functions(sysm)
     pj = projectors(sysm, kb)
     tabs = basis.axis_tables(sysm, fn, eta)
@@ -151,6 +154,8 @@ def vnl_two_stage(sysm, kb, eta=1e-10):
 def projections_closed_form(sysm, kb):
     """<chi_p | phi_b> in the continuum (no grid, no windows), from the
     closed-form overlaps of Cartesian Gaussians: the h -> 0 limit of B."""
+    if basis.is_contracted(sysm):
+        raise NotImplementedError("written for one-primitive functions")
     fn = basis.functions(sysm)
     pj = projectors(sysm, kb)
     both = {k: np.concatenate([pj[k], fn[k]]) for k in ("center", "zeta", "pw", "norm", "l")}

@@ -77,8 +77,7 @@ class Setup:
 
 def setup(sysm, model=None):
     model = model or Model()
-    fn = basis.functions(sysm)
-    S, T = basis.overlap_kinetic(fn)
+    S, T = basis.overlap_kinetic_system(sysm)
     vl = vloc(sysm, model.vloc_depth, model.vloc_width)
     ni = ion_density(sysm, model.ion_charge, model.vloc_width) if model.neutral else np.zeros_like(vl)
     st = Setup(sysm=sysm, model=model, S=S, T=T, vloc=vl, nion=ni, c0=poisson.cube_inv_r_constant())

@@ -133,7 +133,7 @@ def _desc(dft, s):
     return b, g, arrs
 
 
-@pytest.mark.parametrize("name,lo_gb,hi_gb", [("sphere25", 2.0, 3.5), ("sphere40", 25.0, 64.0)])
+@pytest.mark.parametrize("name,lo_gb,hi_gb", [("sphere25", 2.0, 4.0), ("sphere40", 25.0, 64.0)])
 def test_workspace_of_the_large_workloads_fits_one_gpu(built, name, lo_gb, hi_gb):
     """The mixed-precision workspace (K x K FP64 matrices, 16-bit operand
     pairs padded to 256, rho pairs, grids and the padded FFT grid) of the

@@ -29,6 +29,13 @@ DIAMOND_BASIS = np.array([
 # (l, exponent) per shell, in function order on every atom; p shells expand to x, y, z
 SHELL_SPEC = ((0, 0.1), (0, 0.3), (0, 1.0), (0, 3.0), (1, 0.2), (1, 0.8))
 
+# A contracted basis with a d shell, in the style of a split-valence set with
+# polarisation: (l, exponents, contraction coefficients) per shell.  Synthetic
+# numbers (no basis-set tables are available here); 10 functions per atom
+# with spherical d (5), 11 with Cartesian d (6).
+SHELL_SPEC_D = ((0, (3.0, 1.0, 0.3), (0.15, 0.55, 0.45)), (0, (0.1,), (1.0,)),
+                (1, (0.8, 0.2), (0.4, 0.7)), (2, (0.5,), (1.0,)))
+
 
 def diamond_supercell(nrep: int = 2, a: float = SI_A0) -> np.ndarray:
     """All atoms of an nrep^3 supercell of the conventional diamond cell."""
@@ -67,8 +74,8 @@ class System:
     """
     xyz: np.ndarray                      # (n_atoms, 3) bohr
     shell_atom: np.ndarray               # (n_shells,) int32
-    shell_l: np.ndarray                  # (n_shells,) int32, 0 or 1
-    shell_exp: np.ndarray                # (n_shells,) float64
+    shell_l: np.ndarray                  # (n_shells,) int32, 0, 1 or 2
+    shell_exp: np.ndarray                # (n_shells,) float64: the exponent of one-primitive shells
     grid_origin: np.ndarray              # (3,) bohr
     grid_h: float
     grid_n: np.ndarray                   # (3,) int: nx, ny, nz
@@ -76,6 +83,13 @@ class System:
     kT: float
     name: str = ""
     meta: dict = field(default_factory=dict)
+    # contracted shells (None: one primitive per shell, exponent shell_exp,
+    # coefficient 1): primitives per shell, then all exponents and contraction
+    # coefficients shell by shell
+    shell_nprim: np.ndarray = None
+    prim_exp: np.ndarray = None
+    prim_coef: np.ndarray = None
+    spherical: bool = False              # d shells: 5 real solid harmonics (else 6 Cartesian)
 
     @property
     def n_atoms(self) -> int:
@@ -83,7 +97,8 @@ class System:
 
     @property
     def n_basis(self) -> int:
-        return int(np.sum(np.where(self.shell_l == 0, 1, 3)))
+        per_l = {0: 1, 1: 3, 2: 5 if self.spherical else 6}
+        return int(sum(per_l[int(l)] for l in self.shell_l))
 
     @property
     def n_grid(self) -> int:
@@ -92,14 +107,26 @@ class System:
 
 def make_system(xyz: np.ndarray, *, h: float = 0.4, pad: float = 6.0, kT: float = 0.01,
                 electrons_per_atom: float = 4.0, shells=SHELL_SPEC, name: str = "",
-                grid_n=None, grid_origin=None) -> System:
+                grid_n=None, grid_origin=None, spherical: bool = False) -> System:
+    """shells: (l, exponent) per shell, or (l, exponents, coefficients) for
+    contracted shells (then every shell carries its primitive list)."""
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     sa, sl, se = [], [], []
+    contracted = any(isinstance(sh[1], tuple) for sh in shells)
+    npr, pe, pc = [], [], []
     for a in range(xyz.shape[0]):
-        for (l, z) in shells:
+        for sh in shells:
+            l = sh[0]
             sa.append(a)
             sl.append(l)
-            se.append(z)
+            if contracted:
+                exps, coefs = (sh[1], sh[2]) if isinstance(sh[1], tuple) else ((sh[1],), (1.0,))
+                npr.append(len(exps))
+                pe.extend(exps)
+                pc.extend(coefs)
+                se.append(min(exps))
+            else:
+                se.append(sh[1])
     lo = xyz.min(axis=0) - pad
     hi = xyz.max(axis=0) + pad
     if grid_origin is None:
@@ -109,7 +136,10 @@ def make_system(xyz: np.ndarray, *, h: float = 0.4, pad: float = 6.0, kT: float 
     return System(xyz=xyz, shell_atom=np.array(sa, np.int32), shell_l=np.array(sl, np.int32),
                   shell_exp=np.array(se, np.float64), grid_origin=np.asarray(grid_origin, np.float64),
                   grid_h=float(h), grid_n=np.asarray(grid_n, np.int64),
-                  n_electrons=float(electrons_per_atom * xyz.shape[0]), kT=float(kT), name=name)
+                  n_electrons=float(electrons_per_atom * xyz.shape[0]), kT=float(kT), name=name,
+                  shell_nprim=np.array(npr, np.int32) if contracted else None,
+                  prim_exp=np.array(pe, np.float64) if contracted else None,
+                  prim_coef=np.array(pc, np.float64) if contracted else None, spherical=bool(spherical))
 
 
 def jitter(xyz: np.ndarray, sigma: float, seed: int) -> np.ndarray:
@@ -148,6 +178,8 @@ def config_system(name: str, seed: int = 0, **kw) -> System:
     sphere40    sphere R = 40 bohr, sigma 0.1, kT 0.005          (K ~ 19.6k)
     sphereR<r>  sphere of radius r, sigma 0.1, kT 0.01
     tiny<n>     the first n atoms of the 64-atom cluster, coarse grid (tests)
+    dtiny<n>    the same atoms with the contracted basis with spherical d
+                shells (SHELL_SPEC_D); ctiny<n> with Cartesian d shells
     """
     if name == "cluster64":
         xyz = jitter(diamond_supercell(2), 0.05, seed)
@@ -162,6 +194,10 @@ def config_system(name: str, seed: int = 0, **kw) -> System:
         r = float(name[len("sphereR"):])
         xyz = jitter(diamond_sphere(r), 0.1, seed)
         return make_system(xyz, kT=kw.pop("kT", 0.01), name=name, **kw)
+    if name.startswith(("dtiny", "ctiny")):
+        t = config_system("tiny" + name[5:], seed=seed)
+        return make_system(t.xyz, h=t.grid_h, kT=t.kT, shells=SHELL_SPEC_D, name=name, grid_n=t.grid_n,
+                           grid_origin=t.grid_origin, spherical=name.startswith("d"))
     if name.startswith("tiny"):
         n = int(name[4:])
         xyz = jitter(diamond_supercell(2), 0.05, seed)
