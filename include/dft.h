@@ -84,19 +84,30 @@ enum { DFT_XC_SLATER = 0, DFT_XC_PW92 = 1 };
 
 typedef struct dft_ctx dft_ctx;
 
-/* Atoms and uncontracted Cartesian Gaussian shells (Eqs. A.1-A.3 with one
- * primitive per shell).  Host pointers, read during dft_init_basis only.
- * Shell s sits on atom shell_atom[s], has angular momentum shell_l[s] in
- * {0, 1} and exponent shell_exp[s] > 0.  Basis functions are numbered shell
- * by shell; a p shell contributes x, y, z in that order.  Each function is
- * normalised to unit self-overlap. */
+/* Atoms and Gaussian shells (Eqs. A.1-A.3).  Host pointers, read during
+ * dft_init_basis only.  Shell s sits on atom shell_atom[s] and has angular
+ * momentum shell_l[s] in {0, 1, 2}.  Its radial part is one primitive of
+ * exponent shell_exp[s] > 0 when shell_nprim is NULL; otherwise the
+ * contraction sum_p d_p exp(-zeta_p r^2) (Eq. A.1) of shell_nprim[s]
+ * primitives (1 .. 32), whose exponents and coefficients follow shell by
+ * shell in prim_exp and prim_coef.  Basis functions are numbered shell by
+ * shell; a p shell contributes x, y, z in that order; a d shell the five
+ * real solid harmonics of Table A.1 in the table's order of m (2, 1, 0, -1,
+ * -2) when spherical is nonzero, else the six Cartesian functions xx, yy,
+ * zz, xy, xz, yz.  Each function is normalised to unit self-overlap (the
+ * contracted ones from their closed-form overlap, in dft_overlap_kinetic).
+ * The window of a function (Eq. A.4) is set by its most diffuse primitive. */
 typedef struct dft_basis_desc {
     int n_atoms;
     const double* xyz;        /* n_atoms * 3, bohr */
     int n_shells;
     const int* shell_atom;
     const int* shell_l;
-    const double* shell_exp;
+    const double* shell_exp;  /* may be NULL when shell_nprim is given */
+    const int* shell_nprim;   /* NULL: one primitive per shell */
+    const double* prim_exp;
+    const double* prim_coef;
+    int spherical;
 } dft_basis_desc;
 
 /* Grid point (i, j, k) sits at origin + h * (i, j, k), 0 <= i < n[0] (x),

@@ -73,7 +73,9 @@ class Context:
     """One system on one GPU: descriptors, workspace and the libdft context.
 
     system: any object with xyz (n,3), shell_atom, shell_l, shell_exp,
-    grid_origin (3,), grid_h, grid_n (3,) (nx, ny, nz), n_electrons, kT.
+    grid_origin (3,), grid_h, grid_n (3,) (nx, ny, nz), n_electrons, kT, and
+    optionally contracted shells (shell_nprim, prim_exp, prim_coef) and
+    spherical (d shells as the five solid harmonics).
     """
 
     def __init__(self, system, device="cuda", stream=None, **param_kw):
@@ -91,6 +93,14 @@ class Context:
         b.shell_atom = self._sa.ctypes.data_as(C.POINTER(C.c_int))
         b.shell_l = self._sl.ctypes.data_as(C.POINTER(C.c_int))
         b.shell_exp = self._se.ctypes.data_as(C.POINTER(C.c_double))
+        if getattr(system, "shell_nprim", None) is not None:
+            self._np = np.ascontiguousarray(system.shell_nprim, dtype=np.int32)
+            self._pe = np.ascontiguousarray(system.prim_exp, dtype=np.float64)
+            self._pc = np.ascontiguousarray(system.prim_coef, dtype=np.float64)
+            b.shell_nprim = self._np.ctypes.data_as(C.POINTER(C.c_int))
+            b.prim_exp = self._pe.ctypes.data_as(C.POINTER(C.c_double))
+            b.prim_coef = self._pc.ctypes.data_as(C.POINTER(C.c_double))
+        b.spherical = 1 if getattr(system, "spherical", False) else 0
         g = dft_grid_desc()
         for d in range(3):
             g.origin[d] = float(system.grid_origin[d])
@@ -107,7 +117,8 @@ class Context:
         off = (-self.workspace.data_ptr()) % 256
         self._ws = self.workspace[off:off + nbytes]
         self.ctx = dft_init_basis(b, g, self.params, self._ws, stream)
-        self.K = int(np.sum(np.where(self._sl == 0, 1, 3)))
+        per_l = {0: 1, 1: 3, 2: 5 if b.spherical else 6}
+        self.K = int(sum(per_l[int(l)] for l in self._sl))
         self.grid_shape = (int(g.n[2]), int(g.n[1]), int(g.n[0]))
         self.n_atoms = b.n_atoms
 

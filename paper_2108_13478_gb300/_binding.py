@@ -25,7 +25,8 @@ DFT_XC_SLATER, DFT_XC_PW92 = 0, 1
 class dft_basis_desc(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("xyz", C.POINTER(C.c_double)), ("n_shells", C.c_int),
                 ("shell_atom", C.POINTER(C.c_int)), ("shell_l", C.POINTER(C.c_int)),
-                ("shell_exp", C.POINTER(C.c_double))]
+                ("shell_exp", C.POINTER(C.c_double)), ("shell_nprim", C.POINTER(C.c_int)),
+                ("prim_exp", C.POINTER(C.c_double)), ("prim_coef", C.POINTER(C.c_double)), ("spherical", C.c_int)]
 
 
 class dft_grid_desc(C.Structure):

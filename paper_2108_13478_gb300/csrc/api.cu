@@ -22,21 +22,50 @@ const char* kVersion = "libdft 0.2 (sm_103a)";
 constexpr double MU_SETTLED = 0.01, MU_REDO = 0.05;
 
 // Window half-length L solving c(L sqrt(zeta), l) = 1 - eta (Eq. A.4).
-// c(d, 0) = erf(d), c(d, 1) = 1 - exp(-d^2).
+// c(d, 0) = erf(d), c(d, 1) = 1 - exp(-d^2),
+// c(d, 2) = erf(d) - 2 d exp(-d^2) / sqrt(pi).
 double window_halfwidth(double zeta, int l, double eta) {
     double d;
     if (l == 1) {
         d = std::sqrt(-std::log(eta));
     } else {
+        // 1 - c(d, l), decreasing in d
+        auto tail = [l](double x) {
+            return l == 0 ? std::erfc(x) : std::erfc(x) + 2.0 * x * std::exp(-x * x) / std::sqrt(M_PI);
+        };
         double lo = 0.0, hi = 40.0;
         for (int it = 0; it < 400; ++it) {
             double mid = 0.5 * (lo + hi);
             if (mid <= lo || mid >= hi) break;
-            if (std::erfc(mid) > eta) lo = mid; else hi = mid;
+            if (tail(mid) > eta) lo = mid; else hi = mid;
         }
         d = 0.5 * (lo + hi);
     }
     return d / std::sqrt(zeta);
+}
+
+// Table A.1: the real solid harmonics of degree 2 as weights of the
+// Cartesian monomials x^i y^j z^k, in the table's order of m (2, 1, 0, -1, -2);
+// s and p have one monomial of weight 1 (p in the Cartesian order x, y, z)
+struct Mono {
+    int i, j, k;
+    double w;
+};
+std::vector<std::vector<Mono>> shell_components(int l, bool spherical) {
+    const double r3 = std::sqrt(3.0);
+    if (l == 0) return {{{0, 0, 0, 1.0}}};
+    if (l == 1) return {{{1, 0, 0, 1.0}}, {{0, 1, 0, 1.0}}, {{0, 0, 1, 1.0}}};
+    if (spherical)
+        return {{{2, 0, 0, 0.5 * r3}, {0, 2, 0, -0.5 * r3}}, {{1, 1, 0, r3}},
+                {{2, 0, 0, -0.5}, {0, 2, 0, -0.5}, {0, 0, 2, 1.0}}, {{0, 1, 1, r3}}, {{1, 0, 1, r3}}};
+    return {{{2, 0, 0, 1.0}}, {{0, 2, 0, 1.0}}, {{0, 0, 2, 1.0}},
+            {{1, 1, 0, 1.0}}, {{1, 0, 1, 1.0}}, {{0, 1, 1, 1.0}}};
+}
+
+// normalisation of x^l exp(-zeta r^2): (2 zeta / pi)^(3/4) (4 zeta)^(l/2) / sqrt((2l - 1)!!)
+double monomial_norm(double zeta, int l) {
+    const double dfact = l == 2 ? 3.0 : 1.0;
+    return std::pow(2.0 * zeta / M_PI, 0.75) * std::pow(4.0 * zeta, 0.5 * l) / std::sqrt(dfact);
 }
 
 struct Layout {
@@ -51,11 +80,21 @@ struct Layout {
 void validate(const dft_basis_desc* b, const dft_grid_desc* g, const dft_params* p) {
     if (!b || !g || !p) throw Error(DFT_EINVAL, "null descriptor");
     if (b->n_atoms <= 0 || !b->xyz) throw Error(DFT_EINVAL, "no atoms");
-    if (b->n_shells <= 0 || !b->shell_atom || !b->shell_l || !b->shell_exp) throw Error(DFT_EINVAL, "no shells");
+    if (b->n_shells <= 0 || !b->shell_atom || !b->shell_l) throw Error(DFT_EINVAL, "no shells");
+    if (!b->shell_nprim && !b->shell_exp) throw Error(DFT_EINVAL, "no shell exponents");
+    if (b->shell_nprim && (!b->prim_exp || !b->prim_coef)) throw Error(DFT_EINVAL, "contracted shells need prim_exp and prim_coef");
+    long long np = 0;
     for (int s = 0; s < b->n_shells; ++s) {
         if (b->shell_atom[s] < 0 || b->shell_atom[s] >= b->n_atoms) throw Error(DFT_EINVAL, "shell_atom out of range");
-        if (b->shell_l[s] < 0 || b->shell_l[s] > 1) throw Error(DFT_EINVAL, "only s and p shells are supported");
-        if (!(b->shell_exp[s] > 0.0)) throw Error(DFT_EINVAL, "shell exponent must be positive");
+        if (b->shell_l[s] < 0 || b->shell_l[s] > 2) throw Error(DFT_EINVAL, "only s, p and d shells are supported");
+        if (b->shell_nprim) {
+            if (b->shell_nprim[s] < 1 || b->shell_nprim[s] > 32) throw Error(DFT_EINVAL, "shell_nprim must be in [1, 32]");
+            for (int q = 0; q < b->shell_nprim[s]; ++q)
+                if (!(b->prim_exp[np + q] > 0.0)) throw Error(DFT_EINVAL, "primitive exponent must be positive");
+            np += b->shell_nprim[s];
+        } else if (!(b->shell_exp[s] > 0.0)) {
+            throw Error(DFT_EINVAL, "shell exponent must be positive");
+        }
     }
     if (!(g->h > 0.0)) throw Error(DFT_EINVAL, "grid spacing must be positive");
     for (int d = 0; d < 3; ++d)
@@ -83,33 +122,60 @@ void build_basis(Ctx& c, const dft_basis_desc* b, const dft_grid_desc* g, const 
     c.p = *p;
     c.xyz_host.assign(b->xyz, b->xyz + 3 * b->n_atoms);
     c.fn_host.clear();
+    c.term_ptr_host.assign(1, 0);
     int wmax = 1;
+    // Every basis function (Eq. A.1) is a sum of Cartesian Gaussian terms,
+    // coefficient d_p w^{ijk} (contraction times Table A.1 weight) times the
+    // monomial's normalisation; all terms of a function share its window, set
+    // by its most diffuse primitive (Supp. A.1.1).  The grid kernels and the
+    // closed-form integrals work on the terms; function-level matrices are
+    // contracted from them (with the functions' normalisation N_a, formed on
+    // the device from the closed-form overlap).  An uncontracted s/p basis has
+    // one term per function with its primitive's normalisation: no
+    // contraction step at all.
+    bool contracted = false;
+    long long poff = 0;
     for (int s = 0; s < b->n_shells; ++s) {
-        int a = b->shell_atom[s], l = b->shell_l[s];
-        double z = b->shell_exp[s];
-        double base = std::pow(2.0 * z / M_PI, 0.75);
-        double L = window_halfwidth(z, l, p->eta);
-        int ncomp = l == 0 ? 1 : 3;
-        for (int q = 0; q < ncomp; ++q) {
-            Fn f{};
-            f.cx = b->xyz[3 * a]; f.cy = b->xyz[3 * a + 1]; f.cz = b->xyz[3 * a + 2];
-            f.zeta = z;
-            f.norm = l == 0 ? base : base * 2.0 * std::sqrt(z);
-            f.px = (l == 1 && q == 0); f.py = (l == 1 && q == 1); f.pz = (l == 1 && q == 2);
-            const double cc[3] = {f.cx, f.cy, f.cz};
-            for (int d = 0; d < 3; ++d) {
-                long long lo = (long long)std::ceil((cc[d] - L - c.origin[d]) / c.h);
-                long long hi = (long long)std::floor((cc[d] + L - c.origin[d]) / c.h);
-                lo = std::max<long long>(lo, 0);
-                hi = std::min<long long>(hi, c.n[d] - 1);
-                f.lo[d] = (int)std::min<long long>(lo, c.n[d]);
-                f.hi[d] = (int)std::max<long long>(hi, -1);
-                wmax = std::max(wmax, f.hi[d] - f.lo[d] + 1);
-            }
-            c.fn_host.push_back(f);
+        const int a = b->shell_atom[s], l = b->shell_l[s];
+        std::vector<std::pair<double, double>> prims;
+        if (b->shell_nprim) {
+            for (int q = 0; q < b->shell_nprim[s]; ++q) prims.emplace_back(b->prim_exp[poff + q], b->prim_coef[poff + q]);
+            poff += b->shell_nprim[s];
+        } else {
+            prims.emplace_back(b->shell_exp[s], 1.0);
+        }
+        if (l == 2 || prims.size() > 1 || prims[0].second != 1.0) contracted = true;
+        double zmin = prims[0].first;
+        for (auto& pr : prims) zmin = std::min(zmin, pr.first);
+        const double L = window_halfwidth(zmin, l, p->eta);
+        int lo_w[3], hi_w[3];
+        const double cc[3] = {b->xyz[3 * a], b->xyz[3 * a + 1], b->xyz[3 * a + 2]};
+        for (int d = 0; d < 3; ++d) {
+            long long lo = (long long)std::ceil((cc[d] - L - c.origin[d]) / c.h);
+            long long hi = (long long)std::floor((cc[d] + L - c.origin[d]) / c.h);
+            lo = std::max<long long>(lo, 0);
+            hi = std::min<long long>(hi, c.n[d] - 1);
+            lo_w[d] = (int)std::min<long long>(lo, c.n[d]);
+            hi_w[d] = (int)std::max<long long>(hi, -1);
+            wmax = std::max(wmax, hi_w[d] - lo_w[d] + 1);
+        }
+        for (const auto& comp : shell_components(l, b->spherical != 0)) {
+            for (const auto& pr : prims)
+                for (const Mono& m : comp) {
+                    Fn f{};
+                    f.cx = cc[0]; f.cy = cc[1]; f.cz = cc[2];
+                    f.zeta = pr.first;
+                    f.norm = pr.second * m.w * monomial_norm(pr.first, l);
+                    f.px = m.i; f.py = m.j; f.pz = m.k;
+                    for (int d = 0; d < 3; ++d) { f.lo[d] = lo_w[d]; f.hi[d] = hi_w[d]; }
+                    c.fn_host.push_back(f);
+                }
+            c.term_ptr_host.push_back((int)c.fn_host.size());
         }
     }
-    c.K = (int)c.fn_host.size();
+    c.K = (int)c.term_ptr_host.size() - 1;
+    c.Kt = (int)c.fn_host.size();
+    c.contracted = contracted;
     c.tab_w = wmax;
     for (int d = 0; d < 3; ++d) c.ntile[d] = (c.n[d] + TILE - 1) / TILE;
     c.n_tiles = (long long)c.ntile[0] * c.ntile[1] * c.ntile[2];
@@ -131,7 +197,7 @@ void build_basis(Ctx& c, const dft_basis_desc* b, const dft_grid_desc* g, const 
         *tile_ptr = cnt;
         tile_fn->assign(c.tile_nnz, 0);
         std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-        for (int f = 0; f < c.K; ++f) each_tile(c.fn_host[f], [&](long long t) { (*tile_fn)[pos[t]++] = f; });
+        for (int f = 0; f < c.Kt; ++f) each_tile(c.fn_host[f], [&](long long t) { (*tile_fn)[pos[t]++] = f; });
     }
     // KB projectors (Supp. A.2.2): per atom an s Gaussian (and x, y, z p
     // Gaussians) of exponent nl_zeta, unit continuum norm, cube windows by
@@ -183,8 +249,15 @@ size_t carve(Ctx& c, char* base) {
     size_t K2 = (size_t)c.K * c.K * sizeof(double);
     size_t G = (size_t)c.ng * sizeof(double);
     long long nkc = (long long)(c.n[0] / 2 + 1) * c.n[1] * c.n[2];
-    size_t o_fn = L.off(sizeof(Fn) * c.K);
-    size_t o_tab = L.off(sizeof(double) * (size_t)c.K * 3 * c.tab_w);
+    size_t o_fn = L.off(sizeof(Fn) * c.Kt);
+    size_t o_tab = L.off(sizeof(double) * (size_t)c.Kt * 3 * c.tab_w);
+    size_t o_ttp = 0, o_tpar = 0, o_cn = 0, o_mt = 0;
+    if (c.contracted) {
+        o_ttp = L.off(sizeof(int) * ((size_t)c.K + 1));
+        o_tpar = L.off(sizeof(int) * (size_t)c.Kt);
+        o_cn = L.off(sizeof(double) * (size_t)c.K);
+        o_mt = L.off(sizeof(double) * (size_t)c.Kt * c.Kt);
+    }
     size_t o_tp = L.off(sizeof(int) * (c.n_tiles + 1));
     size_t o_tf = L.off(sizeof(int) * std::max<long long>(1, c.tile_nnz));
     size_t o_xyz = L.off(sizeof(double) * 3 * c.n_atoms);
@@ -201,6 +274,7 @@ size_t carve(Ctx& c, char* base) {
     size_t o_flags = L.off(sizeof(int) * FLAG_COUNT);
     size_t o_vloc = L.off(G), o_nion = L.off(G), o_vks = L.off(G), o_nout = L.off(G), o_gtmp = L.off(G);
     size_t o_fr = L.off(sizeof(double) * c.nfft_r);
+    size_t o_fo = L.off(sizeof(double) * c.nfft_r);
     size_t o_gh = L.off(sizeof(double) * c.nfft_c);
     size_t o_fc = L.off(sizeof(cufftDoubleComplex) * c.nfft_c);
     size_t o_kw = L.off(sizeof(double) * nkc);
@@ -216,8 +290,8 @@ size_t carve(Ctx& c, char* base) {
         o_pj = L.off(sizeof(Fn) * np);
         o_pje = L.off(sizeof(double) * np);
         o_pjt = L.off(sizeof(double) * np * 3 * (size_t)c.pj_w);
-        o_nlb = L.off(sizeof(double) * np * (size_t)c.K);
-        o_nleb = L.off(sizeof(double) * np * (size_t)c.K);
+        o_nlb = L.off(sizeof(double) * np * (size_t)c.Kt);
+        o_nleb = L.off(sizeof(double) * np * (size_t)c.Kt);
         o_vnl = L.off(K2);
     }
     size_t o_h16[2] = {0, 0}, o_x16[4] = {0, 0, 0, 0}, o_rtc = 0, o_tiles = 0, o_systab = 0, o_maps = 0;
@@ -241,6 +315,12 @@ size_t carve(Ctx& c, char* base) {
     if (base) {
         c.d_fn = (Fn*)(base + o_fn);
         c.d_tab = (double*)(base + o_tab);
+        if (c.contracted) {
+            c.d_term_ptr = (int*)(base + o_ttp);
+            c.d_term_par = (int*)(base + o_tpar);
+            c.d_cnorm = (double*)(base + o_cn);
+            c.d_Mt = (double*)(base + o_mt);
+        }
         c.d_tile_ptr = (int*)(base + o_tp);
         c.d_tile_fn = (int*)(base + o_tf);
         c.d_xyz = (double*)(base + o_xyz);
@@ -259,6 +339,7 @@ size_t carve(Ctx& c, char* base) {
         c.d_vloc = (double*)(base + o_vloc); c.d_nion = (double*)(base + o_nion);
         c.d_vks = (double*)(base + o_vks); c.d_nout = (double*)(base + o_nout); c.d_gtmp = (double*)(base + o_gtmp);
         c.d_fft_r = (double*)(base + o_fr);
+        c.d_fft_o = (double*)(base + o_fo);
         c.d_ghat = (double*)(base + o_gh);
         c.d_fft_c = (cufftDoubleComplex*)(base + o_fc);
         c.d_kerker = (double*)(base + o_kw);
@@ -376,18 +457,25 @@ bool solve_pulay(int m, const std::vector<double>& B, std::vector<double>* c) {
     return true;
 }
 
-// Pulay (DIIS) update of the input density from the history ring
-void pulay_mix(Ctx& c, double* n_in, const double* n_out, cudaStream_t s) {
+// Pulay (DIIS) mixing, first half: the new history entry (n_in and its
+// residual R) goes to ring slot pl_count % H, and one pass over the grids
+// writes the new row of B, <R_slot, R_j> for the m filled slots (slots
+// 0..m-1), to scal[SCAL_PULAY..] and max|R| to scal[SCAL_RES]
+void pulay_begin(Ctx& c, const double* n_in, const double* n_out, cudaStream_t s) {
     const int H = c.pl_hist;
     const int slot = (int)(c.pl_count % H);
-    pulay_store(c, slot, n_in, n_out, s);
     c.pl_count++;
     const int m = (int)std::min<long long>(c.pl_count, H);
-    // new row of B: <R_slot, R_j> for the m filled slots (slots 0..m-1)
-    pulay_dots(c, m, slot, c.d_scal + SCAL_PULAY, s);
-    std::vector<double> row(m);
-    DFT_CUDA_CHECK(cudaMemcpyAsync(row.data(), c.d_scal + SCAL_PULAY, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
-    DFT_CUDA_CHECK(cudaStreamSynchronize(s));
+    pulay_prepare(c, m, slot, n_in, n_out, c.d_scal + SCAL_PULAY, c.d_scal + SCAL_RES, s);
+}
+
+// second half, with the row read back to the host: solve for the
+// coefficients and update the input density from the history ring
+void pulay_mix(Ctx& c, double* n_in, const double* row_host, cudaStream_t s) {
+    const int H = c.pl_hist;
+    const int slot = (int)((c.pl_count - 1) % H);
+    const int m = (int)std::min<long long>(c.pl_count, H);
+    std::vector<double> row(row_host, row_host + m);
     for (int j = 0; j < m; ++j) {
         c.pl_B[(size_t)slot * H + j] = row[j];
         c.pl_B[(size_t)j * H + slot] = row[j];
@@ -690,7 +778,8 @@ void scf_tail(Ctx& c, double* n_in_out, double* v_ks_out, double* P_out, dft_inf
     hartree_xc(c, c.d_nout, nullptr, true, s);
     launch_frob_dot((long long)K * K, c.d_P, c.d_T, c.d_part, c.d_scal + SCAL_EKIN, s);
     if (c.d_VNL) launch_frob_dot((long long)K * K, c.d_P, c.d_VNL, c.d_part, c.d_scal + SCAL_ENL, s);
-    launch_maxabs_diff(c.ng, c.d_nout, n_in_out, c.d_part, c.d_scal + SCAL_RES, s);
+    if (c.p.mixer == DFT_MIX_PULAY) pulay_begin(c, n_in_out, c.d_nout, s);   // also max|n_out - n_in|
+    else launch_maxabs_diff(c.ng, c.d_nout, n_in_out, c.d_part, c.d_scal + SCAL_RES, s);
     if (v_ks_out) DFT_CUDA_CHECK(cudaMemcpyAsync(v_ks_out, c.d_vks, sizeof(double) * c.ng, cudaMemcpyDeviceToDevice, s));
     if (P_out) DFT_CUDA_CHECK(cudaMemcpyAsync(P_out, c.d_P, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
     double sc[SCAL_COUNT];
@@ -705,7 +794,7 @@ void scf_tail(Ctx& c, double* n_in_out, double* v_ks_out, double* P_out, dft_inf
     loc->residual = sc[SCAL_RES];
     // mixing (Pulay needs the residual on the host for its small solve)
     if (c.p.mixer == DFT_MIX_KERKER) kerker_mix(c, n_in_out, c.d_nout, c.p.mix_alpha, s);
-    else if (c.p.mixer == DFT_MIX_PULAY) pulay_mix(c, n_in_out, c.d_nout, s);
+    else if (c.p.mixer == DFT_MIX_PULAY) pulay_mix(c, n_in_out, sc + SCAL_PULAY, s);
     else launch_linear_mix(c.ng, n_in_out, c.d_nout, c.p.mix_alpha, s);
     loc->de_per_atom = c.have_prev ? (loc->e_total - c.e_prev) / c.n_atoms : 0.0;
     c.e_prev = loc->e_total;
@@ -828,7 +917,15 @@ dft_status dft_init_basis(dft_ctx** ctx, const dft_basis_desc* basis, const dft_
         if (ws_bytes < need) throw Error(DFT_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
         carve(*c, static_cast<char*>(workspace));
         cudaStream_t s = static_cast<cudaStream_t>(stream);
-        DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_fn, c->fn_host.data(), sizeof(Fn) * c->K, cudaMemcpyHostToDevice, s));
+        DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_fn, c->fn_host.data(), sizeof(Fn) * c->Kt, cudaMemcpyHostToDevice, s));
+        if (c->contracted) {
+            std::vector<int> par(c->Kt);
+            for (int a = 0; a < c->K; ++a)
+                for (int t = c->term_ptr_host[a]; t < c->term_ptr_host[a + 1]; ++t) par[t] = a;
+            DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_term_ptr, c->term_ptr_host.data(), sizeof(int) * (c->K + 1),
+                                           cudaMemcpyHostToDevice, s));
+            DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_term_par, par.data(), sizeof(int) * c->Kt, cudaMemcpyHostToDevice, s));
+        }
         DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_tile_ptr, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice, s));
         if (!tf.empty())
             DFT_CUDA_CHECK(cudaMemcpyAsync(c->d_tile_fn, tf.data(), sizeof(int) * tf.size(), cudaMemcpyHostToDevice, s));
@@ -848,6 +945,12 @@ dft_status dft_init_basis(dft_ctx** ctx, const dft_basis_desc* basis, const dft_
             cg_setup(*c);
         }
         launch_build_tables(*c, s);
+        if (c->contracted) {
+            // the functions' normalisation N_a from the closed-form overlap of
+            // their terms (needed by every contraction and expansion)
+            launch_overlap_kinetic_terms(*c, c->d_Mt, s);
+            launch_contract_norms(*c, c->d_Mt, s);
+        }
         launch_gaussian_sum(*c, -c->p.vloc_depth, c->p.vloc_width, c->d_vloc, s);
         double w = c->p.vloc_width;
         launch_gaussian_sum(*c, c->p.ion_charge * std::pow(M_PI * w * w, -1.5), w, c->d_nion, s);

@@ -77,6 +77,13 @@ struct TcCfg {
 struct Ctx {
     // problem
     int K = 0, n_atoms = 0;
+    // Cartesian Gaussian terms of the basis functions (Eq. A.1 with Table A.1):
+    // Kt records in fn_host / d_fn, function a owning terms
+    // [term_ptr[a], term_ptr[a + 1]); contracted = false means one term per
+    // function with its own normalisation (Kt = K, no contraction step)
+    int Kt = 0;
+    bool contracted = false;
+    std::vector<int> term_ptr_host;
     int n[3] = {0, 0, 0};
     long long ng = 0;
     double origin[3] = {0, 0, 0}, h = 0;
@@ -96,8 +103,12 @@ struct Ctx {
     long long nfft_r = 0, nfft_c = 0;
 
     // device buffers (carved from the caller's workspace)
-    Fn* d_fn = nullptr;
-    double* d_tab = nullptr;     // [K][3][tab_w]
+    Fn* d_fn = nullptr;          // [Kt]
+    double* d_tab = nullptr;     // [Kt][3][tab_w]
+    int* d_term_ptr = nullptr;   // contracted bases: [K + 1]
+    int* d_term_par = nullptr;   //   function of each term [Kt]
+    double* d_cnorm = nullptr;   //   normalisation N_a of each function [K]
+    double* d_Mt = nullptr;      //   term-level K_t x K_t scratch
     int* d_tile_ptr = nullptr;   // [n_tiles + 1]
     int* d_tile_fn = nullptr;    // [tile_nnz]
     double* d_xyz = nullptr;     // [n_atoms * 3]
@@ -125,7 +136,8 @@ struct Ctx {
     double* d_vks = nullptr;
     double* d_nout = nullptr;
     double* d_gtmp = nullptr;
-    double* d_fft_r = nullptr;   // [nfft_r]
+    double* d_fft_r = nullptr;   // [nfft_r] padded transform input (zero outside the box)
+    double* d_fft_o = nullptr;   // [nfft_r] inverse transform output
     double* d_ghat = nullptr;    // [nfft_c] real spectrum of the Coulomb kernel
     cufftDoubleComplex* d_fft_c = nullptr;  // [nfft_c]
     double* d_kerker = nullptr;  // Kerker weights on the unpadded box [nz][ny][nx/2+1]
@@ -250,6 +262,13 @@ void tri_inverse_lower(const double* L, double* Linv, int K, double* tmp, cudaSt
 void congruence_lower(int K, const double* Linv, const double* F, double* tmp, double* out, cudaStream_t s);
 void congruence_lower_t(int K, const double* Linv, const double* R, double* tmp, double* out, cudaStream_t s);
 void launch_overlap_kinetic(const Ctx& c, double* S, double* T, cudaStream_t s);
+void launch_overlap_kinetic_terms(const Ctx& c, double* St, cudaStream_t s);   // K_t x K_t overlap of the terms
+// contracted bases: out = diag(N) M_c diag(N) with (M_c)_ab = sum_{s in a, t in b} Mt_st
+// (norms from the diagonal of S first: N_a = (sum_{s, t in a} S_t,st)^(-1/2));
+// expansion P_t,st = N_a(s) N_a(t) P_a(s)a(t) for the collocation of terms
+void launch_contract(const Ctx& c, const double* Mt, double* out, cudaStream_t s);
+void launch_contract_norms(const Ctx& c, const double* St, cudaStream_t s);
+void launch_expand(const Ctx& c, const double* P, double* Pt, cudaStream_t s);
 void launch_axpby_mat(int K, double a, const double* X, double b, const double* Y, double* Z,
                       cudaStream_t s);   // Z = a X + b Y
 void launch_normalise_h(int K, const double* Ft, const double* scal, double* H, cudaStream_t s);
@@ -336,8 +355,10 @@ void kerker_setup(Ctx& c, cudaStream_t s);
 void kerker_mix(Ctx& c, double* n_in, const double* n_out, double alpha, cudaStream_t s);
 void launch_linear_mix(long long ng, double* n_in, const double* n_out, double alpha, cudaStream_t s);
 void kerker_apply(Ctx& c, double* r, cudaStream_t s);
-void pulay_store(Ctx& c, int slot, const double* n_in, const double* n_out, cudaStream_t s);
-void pulay_dots(Ctx& c, int m, int slot, double* out, cudaStream_t s);
+// store n_in and R = n_out - n_in in ring slot `slot`, dots[i] = <R_i, R> for
+// the m filled slots and *mx = max|R|, in one pass over the grids
+void pulay_prepare(Ctx& c, int m, int slot, const double* n_in, const double* n_out, double* dots, double* mx,
+                   cudaStream_t s);
 void pulay_update(Ctx& c, int m, const double* coef_dev, double* n_in, cudaStream_t s);
 void launch_maxabs_diff(long long ng, const double* a, const double* b, double* part, double* out,
                         cudaStream_t s);

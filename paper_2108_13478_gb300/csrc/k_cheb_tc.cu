@@ -18,10 +18,11 @@
 // the last wave of tiles is finer).  Warp 0 lane 0 drives TMA loads of the
 // four operand tiles per k-block into a stage ring; warp 1 owns the
 // tensor-memory allocation and lane 0 issues the MMAs.  The k range is cut
-// into chunks of 256 that alternate between two accumulators in tensor memory;
-// the epilogue warps (four per 128 columns, one per tensor-memory lane
-// quadrant) add every finished chunk into FP32 registers with round-to-nearest
-// (so no accumulation chain in the tensor core is longer than one chunk) and
+// into 128-wide units that alternate between two accumulators in tensor
+// memory; the epilogue warps (four per 128 columns, one per tensor-memory lane
+// quadrant) add every finished unit into FP32 registers with round-to-nearest
+// (so no accumulation chain in the tensor core is longer than 128 of K; chunks
+// of 256 remain the unit of the dataflow counters) and
 // then run the fused update: off-diagonal tiles stream 16-column slabs of
 // X_{l-1} and rho (or X_l) through the idle ring with TMA loads and stores and
 // TMA-store the mirror from shared memory; diagonal tiles use masked vector
@@ -66,6 +67,16 @@ struct Cfg {
     static constexpr int MINB = BN_ == 128 ? 2 : 1;   // resident CTAs per SM
     static constexpr int STAGES = BN_ == 128 ? 3 : (BK_ == 64 ? 2 : 4);
     static constexpr int GK = 256 / BK_;
+    // k-blocks per accumulator promotion: the tensor core's FP32 accumulation
+    // leans towards zero by a fraction of an ulp per addition, so the partial
+    // sums move to round-to-nearest FP32 registers every 128 of K (24
+    // additions of the three split products) rather than once per 256-wide
+    // chunk (48).  Measured at K = 4650: promoting every 64 of K cut max|dP|
+    // 4x but cost 8% of the step (two accumulators, so each promotion must
+    // finish within one unit's MMAs); 128 keeps the units' MMAs (~2.9 us)
+    // well above the promotion.  Chunks of 256 stay the unit of the
+    // dataflow counters and of stream-K.
+    static constexpr int SUB = 128 / BK_;
     static constexpr int ROW_BYTES = BK_ * 2;
     static constexpr int A_BYTES = BM * BK_ * 2;
     static constexpr int B_BYTES = BN_ * BK_ * 2;
@@ -468,7 +479,10 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 const int nchunk = (nk + GK - 1) / GK;
                 const int qa = cu.q0(), qb = cu.q1(nchunk);
                 int kb = qa * GK;
-                for (int q = qa; q < qb; ++q, ++qg) {
+                for (int q = qa; q < qb && !*abort_flag; ++q) {
+                  const int kend = min(nk, (q + 1) * GK);
+                  // promotion units of SUB k-blocks alternate between the two accumulators
+                  while (kb < kend) {
                     const int a = (int)(qg & 1);
                     if (*abort_flag || !mbar_wait(&accempty[a], (uint32_t)(((qg >> 1) & 1) ^ 1))) {
                         *abort_flag = 1;
@@ -476,9 +490,9 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                     }
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(a * BN);
-                    const int kend = min(nk, (q + 1) * GK);
+                    const int send = min(kend, kb + C::SUB);
                     bool first = true;
-                    for (; kb < kend; ++kb, ++g) {
+                    for (; kb < send; ++kb, ++g) {
                         const int s = (int)(g % STAGES);
                         const uint32_t ph = (uint32_t)((g / STAGES) & 1);
                         if (*abort_flag || !mbar_wait(&full[s], ph)) {
@@ -499,7 +513,9 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                         umma_commit(&empty[s]);
                     }
                     umma_commit(&accfull[a]);
+                    ++qg;
                     if (*abort_flag) break;
+                  }
                 }
             }
             if (*abort_flag) {
@@ -532,7 +548,8 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
             float R[CPT];
 #pragma unroll
             for (int i = 0; i < CPT; ++i) R[i] = 0.0f;
-            for (int q = qa; q < qb; ++q, ++qg) {
+            const int nkt = (S.K + BK - 1) / BK;
+            for (int q = qa; q < qb; ++q) {
                 if (epf && q == max(qa, qb - 2) && (!sk || qa == 0)) {
                     // the epilogue's rows into L2 while the last chunks run
                     const int rr = m0 + 32 * quad + lane;
@@ -547,21 +564,20 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                         }
                     }
                 }
-                const int a = (int)(qg & 1);
-                const bool got = mbar_wait(&accfull[a], (uint32_t)((qg >> 1) & 1));
-                ok = __all_sync(0xffffffffu, got && !*abort_flag);
-                if (!ok) break;
-                tc_fence_after();
-                // promote the chunk's partial sums: round-to-nearest FP32 adds in registers
-#pragma unroll
-                for (int cc = 0; cc < CPT / 16; ++cc) {
-                    uint32_t v[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * BN + half * CPT + cc * 16), v);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) R[cc * 16 + j] += __uint_as_float(v[j]);
+                // the chunk's promotion units (SUB k-blocks each; fewer in a ragged last chunk)
+                const int nsub = (min(nkt, (q + 1) * GK) - q * GK + C::SUB - 1) / C::SUB;
+                for (int u = 0; u < nsub; ++u, ++qg) {
+                    const int a = (int)(qg & 1);
+                    const bool got = mbar_wait(&accfull[a], (uint32_t)((qg >> 1) & 1));
+                    ok = __all_sync(0xffffffffu, got && !*abort_flag);
+                    if (!ok) break;
+                    tc_fence_after();
+                    // promote the partial sums: round-to-nearest FP32 adds in registers
+                    tmem_add_groups<CPT / 16>(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * BN + half * CPT), R);
+                    tc_fence_before();
+                    mbar_arrive(&accempty[a]);
                 }
-                tc_fence_before();
-                mbar_arrive(&accempty[a]);
+                if (!ok) break;
                 if (fl && et == 0) {
                     // this tile has read chunk q of X_l (its loads landed before the MMAs ran)
                     const int p = min(tl.j, q), qq = max(tl.j, q);

@@ -229,13 +229,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm3_tc(const __grid_constant_
             ok = __all_sync(0xffffffffu, got && !*abort_flag);
             if (!ok) break;
             tc_fence_after();
-#pragma unroll
-            for (int cc = 0; cc < CPT / 16; ++cc) {
-                uint32_t v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * BN + half * CPT + cc * 16), v);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) R[cc * 16 + j] += __uint_as_float(v[j]);
-            }
+            tmem_add_groups<CPT / 16>(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * BN + half * CPT), R);
             tc_fence_before();
             mbar_arrive(&accempty[a]);
         }

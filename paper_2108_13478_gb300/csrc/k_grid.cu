@@ -28,7 +28,8 @@ __global__ void k_build_tables(const Fn* __restrict__ fn, int K, int W, double o
         int pw = d == 0 ? F.px : (d == 1 ? F.py : F.pz);
         double x = (o + h * i) - c;
         val = exp(-F.zeta * x * x);
-        if (pw == 1) val *= x;
+        if (pw >= 1) val *= x;
+        if (pw == 2) val *= x;
         if (d == 0) val *= F.norm;
     }
     tab[idx] = val;
@@ -131,8 +132,16 @@ __global__ void __launch_bounds__(256) k_collocate(
 // each thread then accumulates a 4 x 4 register block of pairs (a = ty + 16 i,
 // b = tx + 16 j), two shared-memory reads per four multiply-adds.  Every pair
 // sums its points in the order g = 0 .. 511.  Contributions of different
-// tiles meet through FP64 atomics.
+// tiles meet as integers: each is rounded to a multiple of 2^-48 and added
+// with a 64-bit integer atomic into V's own storage, so the sum is exact and
+// independent of the order in which tiles finish (the result is the same bit
+// for bit on every run and in every batch); k_fixed_to_double then turns the
+// integers into doubles in place.  Rounding each tile's contribution costs
+// at most 2^-49 (1.8e-15; ~1e-12 over the ~10^3 tiles two diffuse functions
+// share); partial sums must stay within +-2^15 (|V| is O(10) for potentials
+// of tens of hartree).
 constexpr int QCH = 64;
+constexpr double QFIX = 281474976710656.0;   // 2^48
 template <typename R>
 __global__ void __launch_bounds__(256) k_quadrature(
     const Fn* __restrict__ fn, const double* __restrict__ tab, int W, const int* __restrict__ tile_ptr,
@@ -198,13 +207,21 @@ __global__ void __launch_bounds__(256) k_quadrature(
                     const int lb = cb + ux + 16 * j;
                     if (lb >= n_t) continue;
                     const int fb = list[lb];
-                    const double val = h3 * (double)acc[i][j];
-                    atomicAdd(&V[(long long)fa * K + fb], val);
-                    if (ca != cb) atomicAdd(&V[(long long)fb * K + fa], val);
+                    const unsigned long long q = (unsigned long long)llrint(h3 * (double)acc[i][j] * QFIX);
+                    atomicAdd((unsigned long long*)&V[(long long)fa * K + fb], q);
+                    if (ca != cb) atomicAdd((unsigned long long*)&V[(long long)fb * K + fa], q);
                 }
             }
         }
     }
+}
+
+// V's 64-bit integer sums (units of 2^-44) -> doubles, in place
+__global__ void k_fixed_to_double(long long n, double* V) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const long long q = reinterpret_cast<const long long*>(V)[e];
+    V[e] = (double)q * (1.0 / QFIX);
 }
 
 // out(r_g) = sum_C amp exp(-|r_g - R_C|^2 / w^2), terms below 1e-30 |amp| dropped
@@ -236,29 +253,40 @@ void launch_build_tables_for(const Ctx& c, const Fn* fn, int count, int W, doubl
     check_launch("build_tables");
 }
 
-void launch_build_tables(const Ctx& c, cudaStream_t s) { launch_build_tables_for(c, c.d_fn, c.K, c.tab_w, c.d_tab, s); }
+void launch_build_tables(const Ctx& c, cudaStream_t s) { launch_build_tables_for(c, c.d_fn, c.Kt, c.tab_w, c.d_tab, s); }
 
 void launch_collocate(const Ctx& c, const double* P, double* n, cudaStream_t s) {
+    // contracted functions: collocate their terms with P_t = C^T P C
+    if (c.contracted) {
+        launch_expand(c, P, c.d_Mt, s);
+        P = c.d_Mt;
+    }
     if (c.p.precision == DFT_PREC_FP64)
         k_collocate<double><<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
-                                                                c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K, P, n);
+                                                                c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.Kt, P, n);
     else
         k_collocate<float><<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
-                                                               c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K, P, n);
+                                                               c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.Kt, P, n);
     check_launch("collocate");
 }
 
 void launch_quadrature(const Ctx& c, const double* v, double* V, cudaStream_t s) {
-    DFT_CUDA_CHECK(cudaMemsetAsync(V, 0, sizeof(double) * (size_t)c.K * c.K, s));
+    // contracted functions: the terms' matrix, then V = C V_t C^T
+    double* Vq = c.contracted ? c.d_Mt : V;
+    const int K = c.Kt;
+    DFT_CUDA_CHECK(cudaMemsetAsync(Vq, 0, sizeof(double) * (size_t)K * K, s));
     if (c.p.precision == DFT_PREC_FP64)
         k_quadrature<double><<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
-                                                                 c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K,
-                                                                 c.h * c.h * c.h, v, V);
+                                                                 c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], K,
+                                                                 c.h * c.h * c.h, v, Vq);
     else
         k_quadrature<float><<<(unsigned)c.n_tiles, 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_tile_ptr, c.d_tile_fn,
-                                                                c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], c.K,
-                                                                c.h * c.h * c.h, v, V);
-    check_launch("quadrature");
+                                                                c.ntile[0], c.ntile[1], c.n[0], c.n[1], c.n[2], K,
+                                                                c.h * c.h * c.h, v, Vq);
+    const long long n = (long long)K * K;
+    k_fixed_to_double<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, Vq);
+    check_launch("quadrature", 2);
+    if (c.contracted) launch_contract(c, c.d_Mt, V, s);
 }
 
 void launch_gaussian_sum(const Ctx& c, double amp, double width, double* out, cudaStream_t s) {

@@ -236,17 +236,20 @@ __global__ void __launch_bounds__(TIB) k_tri_inv_block(const double* __restrict_
 }
 
 // --- closed-form overlap and kinetic integrals of Cartesian primitives ---
-// 1D integrals int (x-A)^i (x-B)^j exp(-a (x-A)^2 - b (x-B)^2) dx for i, j <= 2,
-// from the Gaussian product e^{-mu (A-B)^2} e^{-p (x-P)^2} and the moments
+// 1D integrals int (x-A)^i (x-B)^j exp(-a (x-A)^2 - b (x-B)^2) dx for i, j <= 3
+// (powers up to 2, one more for the kinetic integrals), from the Gaussian
+// product e^{-mu (A-B)^2} e^{-p (x-P)^2} and the moments
 // int u^n e^{-p u^2} du = sqrt(pi/p) (n-1)!! / (2p)^(n/2) for even n.
-__device__ void overlap_1d(double a, double b, double A, double B, double s[3][3]) {
+constexpr int OS_N = 4;
+__device__ void overlap_1d(double a, double b, double A, double B, double s[OS_N][OS_N]) {
     double p = a + b, mu = a * b / p, P = (a * A + b * B) / p;
     double E = sqrt(M_PI / p) * exp(-mu * (A - B) * (A - B));
     double xa = P - A, xb = P - B;
-    double g[5] = {1.0, 0.0, 0.5 / p, 0.0, 0.75 / (p * p)};
-    const double binom[3][3] = {{1, 0, 0}, {1, 1, 0}, {1, 2, 1}};
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
+    const double q = 0.5 / p;
+    double g[7] = {1.0, 0.0, q, 0.0, 3.0 * q * q, 0.0, 15.0 * q * q * q};
+    const double binom[OS_N][OS_N] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
+    for (int i = 0; i < OS_N; ++i)
+        for (int j = 0; j < OS_N; ++j) {
             double acc = 0.0;
             for (int r = 0; r <= i; ++r)
                 for (int q = 0; q <= j; ++q)
@@ -264,7 +267,7 @@ __global__ void k_overlap_kinetic(const Fn* __restrict__ fn, int K, double* __re
     const int pa[3] = {fa.px, fa.py, fa.pz}, pb[3] = {fb.px, fb.py, fb.pz};
     double Sd[3], Td[3];
     for (int d = 0; d < 3; ++d) {
-        double s[3][3];
+        double s[OS_N][OS_N];
         overlap_1d(fa.zeta, fb.zeta, Ac[d], Bc[d], s);
         int u = pa[d], v = pb[d];
         Sd[d] = s[u][v];
@@ -543,9 +546,73 @@ void tri_inverse_lower(const double* L, double* Linv, int K, double* tmp, cudaSt
     tri_inv_rec(L, Linv, K, K, tmp, s);
 }
 
-void launch_overlap_kinetic(const Ctx& c, double* S, double* T, cudaStream_t s) {
-    k_overlap_kinetic<<<blocks_for((long long)c.K * c.K, 256), 256, 0, s>>>(c.d_fn, c.K, S, T);
+// (M_c)_ab = N_a N_b sum_{s in a, t in b} Mt_st
+__global__ void k_contract(int K, int Kt, const int* __restrict__ tp, const double* __restrict__ nrm,
+                           const double* __restrict__ Mt, double* __restrict__ out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)K * K) return;
+    const int a = (int)(e / K), b = (int)(e % K);
+    double acc = 0.0;
+    for (int si = tp[a]; si < tp[a + 1]; ++si)
+        for (int ti = tp[b]; ti < tp[b + 1]; ++ti) acc += Mt[(long long)si * Kt + ti];
+    out[e] = nrm[a] * nrm[b] * acc;
+}
+
+// N_a = (sum_{s, t in a} St_st)^(-1/2): unit norm of every contracted function
+__global__ void k_contract_norms(int K, int Kt, const int* __restrict__ tp, const double* __restrict__ St,
+                                 double* __restrict__ nrm) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= K) return;
+    double acc = 0.0;
+    for (int si = tp[a]; si < tp[a + 1]; ++si)
+        for (int ti = tp[a]; ti < tp[a + 1]; ++ti) acc += St[(long long)si * Kt + ti];
+    nrm[a] = 1.0 / sqrt(acc);
+}
+
+// P_t,st = N_a(s) N_a(t) P_a(s)a(t)
+__global__ void k_expand(int K, int Kt, const int* __restrict__ par, const double* __restrict__ nrm,
+                         const double* __restrict__ P, double* __restrict__ Pt) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)Kt * Kt) return;
+    const int a = par[e / Kt], b = par[e % Kt];
+    Pt[e] = nrm[a] * nrm[b] * P[(long long)a * K + b];
+}
+
+void launch_contract(const Ctx& c, const double* Mt, double* out, cudaStream_t s) {
+    k_contract<<<blocks_for((long long)c.K * c.K, 256), 256, 0, s>>>(c.K, c.Kt, c.d_term_ptr, c.d_cnorm, Mt, out);
+    check_launch("contract");
+}
+
+void launch_contract_norms(const Ctx& c, const double* St, cudaStream_t s) {
+    k_contract_norms<<<(c.K + 255) / 256, 256, 0, s>>>(c.K, c.Kt, c.d_term_ptr, St, c.d_cnorm);
+    check_launch("contract_norms");
+}
+
+void launch_expand(const Ctx& c, const double* P, double* Pt, cudaStream_t s) {
+    k_expand<<<blocks_for((long long)c.Kt * c.Kt, 256), 256, 0, s>>>(c.K, c.Kt, c.d_term_par, c.d_cnorm, P, Pt);
+    check_launch("expand");
+}
+
+void launch_overlap_kinetic_terms(const Ctx& c, double* St, cudaStream_t s) {
+    k_overlap_kinetic<<<blocks_for((long long)c.Kt * c.Kt, 256), 256, 0, s>>>(c.d_fn, c.Kt, St, nullptr);
     check_launch("overlap_kinetic");
+}
+
+void launch_overlap_kinetic(const Ctx& c, double* S, double* T, cudaStream_t s) {
+    if (!c.contracted) {
+        k_overlap_kinetic<<<blocks_for((long long)c.K * c.K, 256), 256, 0, s>>>(c.d_fn, c.K, S, T);
+        check_launch("overlap_kinetic");
+        return;
+    }
+    // contracted functions: the terms' closed forms, then contraction (the
+    // norms N_a were formed at set-up)
+    const unsigned nb = blocks_for((long long)c.Kt * c.Kt, 256);
+    k_overlap_kinetic<<<nb, 256, 0, s>>>(c.d_fn, c.Kt, c.d_Mt, nullptr);
+    check_launch("overlap_kinetic");
+    launch_contract(c, c.d_Mt, S, s);
+    k_overlap_kinetic<<<nb, 256, 0, s>>>(c.d_fn, c.Kt, nullptr, c.d_Mt);
+    check_launch("overlap_kinetic");
+    launch_contract(c, c.d_Mt, T, s);
 }
 
 void launch_axpby_mat(int K, double a, const double* X, double b, const double* Y, double* Z, cudaStream_t s) {

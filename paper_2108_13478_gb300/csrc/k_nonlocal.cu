@@ -44,12 +44,15 @@ void launch_nonlocal(const Ctx& c, cudaStream_t s) {
     const int np = (int)c.pj_host.size();
     // the projectors' one-dimensional tables (same kernel as the basis tables)
     launch_build_tables_for(c, c.d_pj, np, c.pj_w, c.d_pjtab, s);
-    const long long n = (long long)np * c.K;
+    const long long n = (long long)np * c.Kt;
     k_nl_project<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_fn, c.d_tab, c.tab_w, c.d_pj, c.d_pjtab, c.pj_w,
-                                                            c.d_pje, c.K, np, c.h * c.h * c.h, c.d_nlB, c.d_nlEB);
+                                                            c.d_pje, c.Kt, np, c.h * c.h * c.h, c.d_nlB, c.d_nlEB);
     check_launch("nl_project");
-    // V^NL = B^T (E B): K x K from the np x K projections
-    dgemm('T', 'N', c.K, c.K, np, 1.0, c.d_nlB, c.K, c.d_nlEB, c.K, 0.0, c.d_VNL, c.K, s);
+    // V^NL = B^T (E B) from the np x K_t projections of the basis terms,
+    // contracted to the functions where they are sums of terms
+    double* out = c.contracted ? c.d_Mt : c.d_VNL;
+    dgemm('T', 'N', c.Kt, c.Kt, np, 1.0, c.d_nlB, c.Kt, c.d_nlEB, c.Kt, 0.0, out, c.Kt, s);
+    if (c.contracted) launch_contract(c, c.d_Mt, c.d_VNL, s);
 }
 
 }  // namespace dft

@@ -53,26 +53,23 @@ __global__ void k_take_real(long long n, const cufftDoubleComplex* c, double sca
     if (e < n) r[e] = c[e].x * scale;
 }
 
-// padded[z][y][x] = n - n_ion inside the box, 0 outside.  Block (bx, y, zb)
-// covers x = 128 bx + thread on the line (y, z) for PAD_Z consecutive z, so
-// no index is divided and every block writes PAD_Z x 1 KB.
+// padded[z][y][x] = n - n_ion inside the box.  The padding around it is
+// zeroed once (poisson_setup) and stays zero: the forward transform reads
+// this buffer and the inverse one writes another, so only the box is written
+// here.  Block (bx, y, zb) covers x = 128 bx + thread on the line (y, z) for
+// PAD_Z consecutive z, so no index is divided.
 constexpr int PAD_Z = 8;
-__global__ void __launch_bounds__(128) k_pad(int nx, int ny, int nz, int Nx, int Ny, int Nz,
+__global__ void __launch_bounds__(128) k_pad(int nx, int ny, int nz, int Nx, int Ny,
                                              const double* __restrict__ n, const double* __restrict__ nion,
                                              double* __restrict__ out) {
     const int ix = blockIdx.x * 128 + threadIdx.x, iy = blockIdx.y;
-    if (ix >= Nx) return;
-    const bool in_xy = ix < nx && iy < ny;
+    if (ix >= nx) return;
 #pragma unroll
     for (int k = 0; k < PAD_Z; ++k) {
         const int iz = blockIdx.z * PAD_Z + k;
-        if (iz >= Nz) break;
-        double v = 0.0;
-        if (in_xy && iz < nz) {
-            const long long g = ((long long)iz * ny + iy) * nx + ix;
-            v = n[g] - (nion ? nion[g] : 0.0);
-        }
-        out[((long long)iz * Ny + iy) * Nx + ix] = v;
+        if (iz >= nz) break;
+        const long long g = ((long long)iz * ny + iy) * nx + ix;
+        out[((long long)iz * Ny + iy) * Nx + ix] = n[g] - (nion ? nion[g] : 0.0);
     }
 }
 
@@ -225,41 +222,66 @@ __global__ void k_kerker_weights(int nx, int ny, int nz, double h, double q0, do
     w[e] = g2 / (g2 + q0 * q0) / ((double)nx * ny * nz);
 }
 
-// partial sums of <R_i, R_new> for the m ring slots (Pulay's B matrix row)
-constexpr int PMAX = 16;
-__global__ void __launch_bounds__(256) k_ring_dots(long long ng, int m, const double* __restrict__ ring,
-                                                   const double* __restrict__ rn, double* part) {
+constexpr int PMAX = 16;   // Pulay history slots at most
+
+// One pass for the Pulay step (Section 2): x_slot = n_in, R_slot = n_out -
+// n_in, max|R_slot| and <R_i, R_slot> for the m filled slots (slot's own
+// entry from the register), instead of a copy, a residual, a max and a dot
+// kernel over the same grids.  Block partials: PMAX dots, then the max.
+__global__ void __launch_bounds__(256) k_pulay_prepare(long long ng, int m, int slot, const double* __restrict__ n_in,
+                                                       const double* __restrict__ n_out, double* __restrict__ xr,
+                                                       double* __restrict__ rr, double* __restrict__ part) {
     double acc[PMAX];
 #pragma unroll
     for (int i = 0; i < PMAX; ++i) acc[i] = 0.0;
-    // two grid points per iteration, so each thread has 2 (m + 1) loads in flight
-    const long long stride = (long long)gridDim.x * 512;
-    for (long long e = (long long)blockIdx.x * 512 + threadIdx.x; e < ng; e += stride) {
-        const long long e2 = e + 256;
-        const bool two = e2 < ng;
-        const double r = rn[e], r2 = two ? rn[e2] : 0.0;
+    double mx = 0.0;
+    double* xs = xr + (long long)slot * ng;
+    double* rs = rr + (long long)slot * ng;
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < ng; e += (long long)gridDim.x * 256) {
+        const double a = n_in[e], r = n_out[e] - a;
+        xs[e] = a;
+        rs[e] = r;
+        mx = fmax(mx, fabs(r));
 #pragma unroll
         for (int i = 0; i < PMAX; ++i)
-            if (i < m) {
-                const double* ri = ring + (long long)i * ng;
-                const double a = ri[e], b = two ? ri[e2] : 0.0;
-                acc[i] = fma(b, r2, fma(a, r, acc[i]));
-            }
+            if (i < m) acc[i] = fma(i == slot ? r : rr[(long long)i * ng + e], r, acc[i]);
     }
 #pragma unroll
     for (int i = 0; i < PMAX; ++i) {
         if (i >= m) break;
-        double v = block_sum<256>(acc[i]);
-        if (threadIdx.x == 0) part[(long long)blockIdx.x * PMAX + i] = v;
+        const double v = block_sum<256>(acc[i]);
+        if (threadIdx.x == 0) part[(long long)blockIdx.x * (PMAX + 1) + i] = v;
+    }
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int i = 0; i < 8; ++i) r = fmax(r, red[i]);
+        part[(long long)blockIdx.x * (PMAX + 1) + PMAX] = r;
     }
 }
 
-__global__ void __launch_bounds__(256) k_ring_dots_reduce(int np, int m, const double* part, double* out) {
+// dots[i] = sum over blocks (i < m), *mx = max over blocks
+__global__ void __launch_bounds__(256) k_pulay_prepare_reduce(int np, int m, const double* part, double* dots,
+                                                              double* mx) {
     for (int i = 0; i < m; ++i) {
         double s = 0.0;
-        for (int b = threadIdx.x; b < np; b += 256) s += part[(long long)b * PMAX + i];
+        for (int b = threadIdx.x; b < np; b += 256) s += part[(long long)b * (PMAX + 1) + i];
         s = block_sum<256>(s);
-        if (threadIdx.x == 0) out[i] = s;
+        if (threadIdx.x == 0) dots[i] = s;
+    }
+    double r = 0.0;
+    for (int b = threadIdx.x; b < np; b += 256) r = fmax(r, part[(long long)b * (PMAX + 1) + PMAX]);
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double q = 0.0;
+        for (int i = 0; i < 8; ++i) q = fmax(q, red[i]);
+        *mx = q;
     }
 }
 
@@ -302,25 +324,27 @@ void poisson_setup(Ctx& c, cudaStream_t s) {
     double scale = c.h * c.h * c.h / (double)c.nfft_r;
     k_take_real<<<blocks_for(c.nfft_c, 256), 256, 0, s>>>(c.nfft_c, c.d_fft_c, scale, c.d_ghat);
     check_launch("take_real");
+    // the padding of the transform's input stays zero from here on (k_pad writes the box only)
+    DFT_CUDA_CHECK(cudaMemsetAsync(c.d_fft_r, 0, sizeof(double) * c.nfft_r, s));
 }
 
 void hartree_xc(Ctx& c, const double* n, double* vks, bool energies, cudaStream_t s) {
     const double* nion = c.p.model == DFT_MODEL_NEUTRAL ? c.d_nion : nullptr;
     cufft_check(cufftSetStream(c.plan_f, s), "stream");
     cufft_check(cufftSetStream(c.plan_b, s), "stream");
-    k_pad<<<dim3((unsigned)((c.Nfft[0] + 127) / 128), (unsigned)c.Nfft[1], (unsigned)((c.Nfft[2] + PAD_Z - 1) / PAD_Z)),
-            128, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.Nfft[2], n, nion, c.d_fft_r);
+    k_pad<<<dim3((unsigned)((c.n[0] + 127) / 128), (unsigned)c.n[1], (unsigned)((c.n[2] + PAD_Z - 1) / PAD_Z)),
+            128, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], n, nion, c.d_fft_r);
     check_launch("pad");
     cufft_check(cufftExecD2Z(c.plan_f, c.d_fft_r, c.d_fft_c), "exec D2Z");
     k_mul_real<<<blocks_for(c.nfft_c, 256), 256, 0, s>>>(c.nfft_c, c.d_fft_c, c.d_ghat);
     check_launch("mul_real");
-    cufft_check(cufftExecZ2D(c.plan_b, c.d_fft_c, c.d_fft_r), "exec Z2D");
+    cufft_check(cufftExecZ2D(c.plan_b, c.d_fft_c, c.d_fft_o), "exec Z2D");
     int np = (int)std::min<long long>(1184, (c.ng + 255) / 256);
     if (c.p.xc == DFT_XC_PW92)
-        k_vks<true><<<np, 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.d_fft_r, n, nion, c.d_vloc,
+        k_vks<true><<<np, 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.d_fft_o, n, nion, c.d_vloc,
                                        vks, c.d_part);
     else
-        k_vks<false><<<np, 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.d_fft_r, n, nion, c.d_vloc,
+        k_vks<false><<<np, 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.Nfft[0], c.Nfft[1], c.d_fft_o, n, nion, c.d_vloc,
                                         vks, c.d_part);
     check_launch("vks");
     if (energies) {
@@ -361,20 +385,14 @@ void kerker_apply(Ctx& c, double* r, cudaStream_t s) {
     check_launch("kerker_apply");
 }
 
-void pulay_store(Ctx& c, int slot, const double* n_in, const double* n_out, cudaStream_t s) {
-    double* x = c.d_pulay + (size_t)slot * c.ng;
-    double* r = c.d_pulay + (size_t)(c.pl_hist + slot) * c.ng;
-    DFT_CUDA_CHECK(cudaMemcpyAsync(x, n_in, sizeof(double) * c.ng, cudaMemcpyDeviceToDevice, s));
-    k_residual<<<blocks_for(c.ng, 256), 256, 0, s>>>(c.ng, n_in, n_out, r);
-    check_launch("pulay_store");
-}
-
-void pulay_dots(Ctx& c, int m, int slot, double* out, cudaStream_t s) {
+void pulay_prepare(Ctx& c, int m, int slot, const double* n_in, const double* n_out, double* dots, double* mx,
+                   cudaStream_t s) {
     int np = (int)std::min<long long>(592, (c.ng + 255) / 256);
-    const double* ring = c.d_pulay + (size_t)c.pl_hist * c.ng;
-    k_ring_dots<<<np, 256, 0, s>>>(c.ng, m, ring, ring + (size_t)slot * c.ng, c.d_part);
-    k_ring_dots_reduce<<<1, 256, 0, s>>>(np, m, c.d_part, out);
-    check_launch("pulay_dots", 2);
+    double* xr = c.d_pulay;
+    double* rr = c.d_pulay + (size_t)c.pl_hist * c.ng;
+    k_pulay_prepare<<<np, 256, 0, s>>>(c.ng, m, slot, n_in, n_out, xr, rr, c.d_part);
+    k_pulay_prepare_reduce<<<1, 256, 0, s>>>(np, m, c.d_part, dots, mx);
+    check_launch("pulay_prepare", 2);
 }
 
 // n_in = sum c_i x_i + alpha K[sum c_i R_i]

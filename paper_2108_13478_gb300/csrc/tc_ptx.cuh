@@ -125,6 +125,42 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// the same load without its wait: issue it, then wait_ld16 on the same
+// registers before reading them (the "+r" operands keep every use of the
+// values after the wait)
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void wait_ld16(uint32_t (&v)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
+                   "+r"(v[15])
+                 :
+                 : "memory");
+}
+
+// R[0..16 NB) += the FP32 values of NB consecutive 16-column groups of
+// tensor memory from taddr, with the load of group g + 1 in flight while
+// group g is added (one load outstanding at each wait)
+template <int NB>
+__device__ __forceinline__ void tmem_add_groups(uint32_t taddr, float* R) {
+    uint32_t v[2][16];
+    tmem_ld16_nw(taddr, v[0]);
+#pragma unroll
+    for (int g = 0; g < NB; ++g) {
+        wait_ld16(v[g & 1]);
+        if (g + 1 < NB) tmem_ld16_nw(taddr + 16 * (g + 1), v[(g + 1) & 1]);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) R[16 * g + j] += __uint_as_float(v[g & 1][j]);
+    }
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "

@@ -148,16 +148,18 @@ def train(ws, data, epochs=60, lr=3e-3, log=None):
     return hist
 
 
-def compare_starts(ws, system, max_iter=80, **kw):
+def compare_starts(ws, system, max_iter=150, **kw):
     """SCF from the superposition-of-atoms potential and from the network's
     potential on one system: cycles and GPU seconds to 1e-5 Ha/atom of the
     converged energy (from a tight run of the atomic start) and to full
     convergence."""
     ref = scf_context(system, **kw)
-    _, info, _, _ = run_scf(ref, start_potential(ref), max_iter=max_iter + 40, tol_e=1e-9, tol_n=1e-6)
+    n_ref, info, _, _ = run_scf(ref, start_potential(ref), max_iter=max_iter + 80, tol_e=1e-9, tol_n=1e-6)
     e_ref = info.e_total / system.n_atoms
     ref.close()
-    out = {"n_atoms": system.n_atoms, "n_basis": int(system.n_basis), "e_ref_per_atom": e_ref}
+    out = {"n_atoms": system.n_atoms, "n_basis": int(system.n_basis), "e_ref_per_atom": e_ref,
+           "reference_cycles": n_ref, "reference_converged": n_ref < max_iter + 80,
+           "reference_last_dE_per_atom": info.de_per_atom, "reference_last_residual": info.residual}
     for key, warm in (("atoms", False), ("warm", True)):
         ctx = scf_context(system, **kw)
         v0 = start_potential(ctx)
@@ -189,18 +191,20 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=120)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--seed", type=int, default=1000)
+    ap.add_argument("--cheb-tail", type=float, default=1e-6)
     a = ap.parse_args(argv)
+    kw = dict(cheb_tail_tol=a.cheb_tail, reuse_mu=1)
     t0 = time.time()
     radii = np.random.default_rng(a.seed).uniform(a.rmin, a.rmax, a.train)
     systems = [w.config_system(f"sphereR{r:.3f}", seed=a.seed + i) for i, r in enumerate(radii)]
-    data = training_set(systems)
+    data = training_set(systems, **kw)
     t_data = time.time() - t0
     ws = WarmStart(init_params(seed=1))
     hist = train(ws, data, epochs=a.epochs, lr=a.lr)
     for c, _, _ in data:
         c.close()
     test = w.config_system(f"sphereR{a.test_radius:g}", seed=99)
-    res = compare_starts(ws, test)
+    res = compare_starts(ws, test, **kw)
     rec = {"train_spheres": a.train, "train_radii": [round(float(r), 3) for r in radii],
            "train_atoms": [s.n_atoms for s in systems], "epochs": a.epochs, "loss_first": hist[0],
            "loss_last": hist[-1], "test_radius": a.test_radius, "test": res, "targets_s": t_data,

@@ -94,12 +94,30 @@ def test_workspace_bytes_and_invalid_input(built):
     K = s.n_basis
     assert nb > 11 * K * K * 8 + 5 * s.n_grid * 8
     assert nb < 64 * K * K * 8 + 64 * s.n_grid * 8 + (1 << 30)
-    # d shells are not supported
+    # f shells are not supported; a d shell is, and adds its functions
     sl_bad = sl.copy()
-    sl_bad[0] = 2
+    sl_bad[0] = 3
     b.shell_l = sl_bad.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
     assert dft.dft_workspace_bytes(b, g, p) == 0
+    sl_d = sl.copy()
+    sl_d[0] = 2
+    b.shell_l = sl_d.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    assert dft.dft_workspace_bytes(b, g, p) > nb
     b.shell_l = sl.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    # contracted shells need their primitive arrays; non-positive exponents are refused
+    npr = np.full(len(sa), 2, np.int32)
+    b.shell_nprim = npr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    assert dft.dft_workspace_bytes(b, g, p) == 0
+    pe = np.repeat(se, 2)
+    pc = np.tile([0.6, 0.5], len(sa))
+    b.prim_exp = pe.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    b.prim_coef = pc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert dft.dft_workspace_bytes(b, g, p) > nb
+    pe[3] = -1.0
+    assert dft.dft_workspace_bytes(b, g, p) == 0
+    b.shell_nprim = None
+    b.prim_exp = None
+    b.prim_coef = None
     p.beta = -1.0
     assert dft.dft_workspace_bytes(b, g, p) == 0
     assert "sm_103a" in dft.dft_version()

@@ -65,14 +65,18 @@ def test_trained_start_needs_fewer_cycles():
     _, info, _, _ = gws.run_scf(ctx, v_sad, tol_e=1e-9, tol_n=1e-6)
     e_ref = info.e_total / test.n_atoms
     ctx_a = gws.scf_context(test)
-    n_sad, _, _, hit_sad = gws.run_scf(ctx_a, gws.start_potential(ctx_a), e_ref=e_ref)
+    tm_a, tm_b = {}, {}
+    n_sad, _, _, hit_sad = gws.run_scf(ctx_a, gws.start_potential(ctx_a), e_ref=e_ref, timings=tm_a)
     ctx_b = gws.scf_context(test)
     v0 = ws.potential(ctx_b, gws.start_potential(ctx_b))
-    n_warm, _, _, hit_warm = gws.run_scf(ctx_b, v0, e_ref=e_ref)
-    print(f"loss {hist[0]:.4e} -> {hist[-1]:.4e}; cycles to 1e-5 Ha/atom: atoms {hit_sad}, warm {hit_warm}; "
-          f"to convergence: atoms {n_sad}, warm {n_warm}")
+    n_warm, _, _, hit_warm = gws.run_scf(ctx_b, v0, e_ref=e_ref, timings=tm_b)
+    print(f"loss {hist[0]:.4e} -> {hist[-1]:.4e}; cycles to 1e-5 Ha/atom: atoms {hit_sad} ({tm_a['hit_s']:.2f} s), "
+          f"warm {hit_warm} ({tm_b['hit_s']:.2f} s); to convergence: atoms {n_sad}, warm {n_warm}")
     assert hit_warm is not None and hit_sad is not None
-    assert hit_warm <= hit_sad
+    # a real gain: at least 3 cycles fewer to 1e-5 Ha/atom (the trained start
+    # saved 8 of 43 cycles here; 3 leaves room for the cycle-to-cycle scatter
+    # of the split-FP16 arithmetic, which moves the hit by a cycle or two)
+    assert hit_warm + 3 <= hit_sad
     for c, _, _ in data:
         c.close()
     for c in (ctx, ctx_a, ctx_b):
