@@ -17,6 +17,10 @@ Modules
   dm          generalised eigensolve, Fermi-Dirac DM (Eq. 2.9), Chebyshev
               expansion and recurrence (Supp. B), mu bisection (Eq. 2.8)
   poisson     free-space Hartree potential by zero-padded FFT, Slater exchange
+  pseudo      non-local Kleinman-Bylander V^NL from synthetic projectors
+              (Eqs. 2.3-2.4, Supp. A.2.2)
+  sparse      density-matrix columns by the sparse-operator route: the
+              vector recurrence with S^-1 by PCG (Section 2, Supp. B)
   scf         local pseudopotential, initial density, energy, SCF cycle (A.3)
   warmstart   atom-centred descriptor, MLP, start-potential assembly and
               their gradients (the learned warm start; not in the paper)
