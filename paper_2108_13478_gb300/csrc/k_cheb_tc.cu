@@ -568,8 +568,13 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 const int nsub = (min(nkt, (q + 1) * GK) - q * GK + C::SUB - 1) / C::SUB;
                 for (int u = 0; u < nsub; ++u, ++qg) {
                     const int a = (int)(qg & 1);
+                    // every epilogue warp decides on the same event (the unit's
+                    // commit, which also arrives after an abort): deciding on the
+                    // producer's abort flag, read at different moments by
+                    // different warps, could send some warps on to the named
+                    // barriers of the fused update without the others
                     const bool got = mbar_wait(&accfull[a], (uint32_t)((qg >> 1) & 1));
-                    ok = __all_sync(0xffffffffu, got && !*abort_flag);
+                    ok = __all_sync(0xffffffffu, got);
                     if (!ok) break;
                     tc_fence_after();
                     // promote the partial sums: round-to-nearest FP32 adds in registers

@@ -246,14 +246,22 @@ __device__ void overlap_1d(double a, double b, double A, double B, double s[OS_N
     double E = sqrt(M_PI / p) * exp(-mu * (A - B) * (A - B));
     double xa = P - A, xb = P - B;
     const double q = 0.5 / p;
-    double g[7] = {1.0, 0.0, q, 0.0, 3.0 * q * q, 0.0, 15.0 * q * q * q};
+    const double g[7] = {1.0, 0.0, q, 0.0, 3.0 * q * q, 0.0, 15.0 * q * q * q};
     const double binom[OS_N][OS_N] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
+    // powers by multiplication (a general pow costs hundreds of FP64
+    // operations on this part's narrow FP64 pipe)
+    const double pa[OS_N] = {1.0, xa, xa * xa, xa * xa * xa};
+    const double pb[OS_N] = {1.0, xb, xb * xb, xb * xb * xb};
+#pragma unroll
     for (int i = 0; i < OS_N; ++i)
+#pragma unroll
         for (int j = 0; j < OS_N; ++j) {
             double acc = 0.0;
+#pragma unroll
             for (int r = 0; r <= i; ++r)
-                for (int q = 0; q <= j; ++q)
-                    acc += binom[i][r] * binom[j][q] * pow(xa, i - r) * pow(xb, j - q) * g[r + q];
+#pragma unroll
+                for (int t = 0; t <= j; ++t)
+                    if (((r + t) & 1) == 0) acc += binom[i][r] * binom[j][t] * pa[i - r] * pb[j - t] * g[r + t];
             s[i][j] = E * acc;
         }
 }

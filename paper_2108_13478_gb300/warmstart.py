@@ -101,7 +101,7 @@ def run_scf(ctx, v_first, max_iter=80, tol_e=1e-8, tol_n=1e-5, e_ref=None, e_tol
     ev[1].synchronize()
     t = ev[0].elapsed_time(ev[1]) / 1000.0
     if timings is not None:
-        timings.update(start_s=t, cycle_s=[], hit_s=None)
+        timings.update(start_s=t, cycle_s=[], hit_s=None, e_per_atom=[], residual=[])
     v = ctx.grid_array()
     hit = None
     info = None
@@ -114,6 +114,8 @@ def run_scf(ctx, v_first, max_iter=80, tol_e=1e-8, tol_n=1e-5, e_ref=None, e_tol
         t += dt
         if timings is not None:
             timings["cycle_s"].append(dt)
+            timings["e_per_atom"].append(info.e_total / ctx.n_atoms)
+            timings["residual"].append(info.residual)
         if e_ref is not None and hit is None and abs(info.e_total / ctx.n_atoms - e_ref) < e_tol:
             hit = it + 1
             if timings is not None:
@@ -168,7 +170,9 @@ def compare_starts(ws, system, max_iter=150, **kw):
         tm = {}
         n_conv, _, _, hit = run_scf(ctx, v0, max_iter=max_iter, e_ref=e_ref, timings=tm)
         out[key] = {"cycles_to_1e-5": hit, "seconds_to_1e-5": tm["hit_s"], "cycles_to_convergence": n_conv,
-                    "seconds_to_convergence": tm["start_s"] + sum(tm["cycle_s"])}
+                    "converged": n_conv < max_iter, "seconds_to_convergence": tm["start_s"] + sum(tm["cycle_s"]),
+                    "dE_per_atom_trace": [float("%.2e" % (e - e_ref)) for e in tm["e_per_atom"]],
+                    "residual_trace": [float("%.2e" % r) for r in tm["residual"]]}
         ctx.close()
     return out
 
