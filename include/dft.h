@@ -225,6 +225,53 @@ dft_status dft_nonlocal_matrix(dft_ctx* ctx, double* VNL, void* stream);
  * range (|x| >= 32768). */
 dft_status dft_density_matrix(dft_ctx* ctx, const double* F, double* P, dft_info* info, void* stream);
 
+/* Preconditioners of the sparse-operator route (dft_density_matrix_columns) */
+enum { DFT_PRECOND_BLOCK_JACOBI = 0, DFT_PRECOND_NONE = 1 };
+
+/* Results of dft_density_matrix_columns. */
+typedef struct dft_columns_info {
+    long long nnz_s, nnz_f;        /* entries kept in the sparse S and F */
+    long long pcg_solves;          /* S^-1 applications, one per column block and step */
+    long long pcg_iterations;      /* sum over solves of the slowest column's iteration count */
+    double max_rel_residual;       /* largest ||r|| / ||b|| at exit over all solves and columns */
+    int not_converged;             /* solves that stopped at pcg_maxit with a column above pcg_tol */
+    int block_cols;                /* columns advanced together */
+    float ms;                      /* CUDA-event time of the call */
+} dft_columns_info;
+
+/* Columns of the density matrix by the sparse-operator route of Section 2
+ * (the column-by-column traces, Eq. 2.10, and the passage after it):
+ * rho_alpha = P u_alpha = f_FD(S^-1 F) S^-1 u_alpha for alpha = cols[c], by
+ * the Chebyshev recurrence of Supp. B on vectors, U_0 = S^-1 u_alpha,
+ * U_1 = H_N U_0, U_{l+1} = 2 H_N U_l - U_{l-1}, rho = sum_l a_l(mu) U_l with
+ * H_N v = (S^-1 (F v) - Ebar v) / dE, every S^-1 by preconditioned conjugate
+ * gradients on the sparse S (the paper's footnote 2), starting from zero and
+ * stopping per column at ||r|| <= pcg_tol ||b||.  S (from
+ * dft_overlap_kinetic) and F are kept in CSR form with the entries
+ * |A_ij| > thresh (thresh = 0: every nonzero).  The preconditioner is
+ * block-Jacobi (the inverse of each atom's diagonal block of S; atoms of at
+ * most 48 functions) or none; the paper's incomplete Cholesky is not offered
+ * (its triangular solves are sequential).  FP64 throughout, whatever the
+ * context's precision.  The iterations run in groups of 8 (CUDA graphs), so
+ * a solve takes at most pcg_maxit rounded up to a multiple of 8.
+ *   F        device, K x K Fock matrix, row-major (symmetric)
+ *   cols     host, ncols column indices in [0, K) (repeats allowed)
+ *   mu       chemical potential (Ha), e.g. dft_info.mu of dft_density_matrix
+ *   e_min, e_max  the expansion interval (e.g. dft_info.e_min / e_max)
+ *   n_cheb   N_C, 2 .. the context's Chebyshev capacity
+ *   out      device, K x ncols row-major, written: column c is P u_{cols[c]}
+ *   info     host, may be NULL
+ * The call uses the context's K x K work matrices as scratch (a later
+ * dft_density_matrix or dft_scf_step recomputes what it needs) and works on
+ * blocks of at most min(K / 4, 1024) columns.  DFT_EINVAL for bad arguments
+ * or before dft_overlap_kinetic; DFT_ENOTCONV if an atom's block of S is not
+ * positive definite.  Columns still above pcg_tol after pcg_maxit
+ * iterations are reported in info->not_converged, not as an error. */
+dft_status dft_density_matrix_columns(dft_ctx* ctx, const double* F, const int* cols, int ncols, double mu,
+                                      double e_min, double e_max, int n_cheb, double thresh, int precond,
+                                      double pcg_tol, int pcg_maxit, double* out, dft_columns_info* info,
+                                      void* stream);
+
 /* n(r_g) = 2 sum_ab P_ab phi_a(r_g) phi_b(r_g) over the windows (Eq. 2.7,
  * Supp. A.1.2).  P device K x K; n_grid device [nz][ny][nx], overwritten. */
 dft_status dft_density_on_grid(dft_ctx* ctx, const double* P, double* n_grid, void* stream);

@@ -15,7 +15,7 @@ from . import _binding as B
 from ._binding import (  # noqa: F401
     DftError, dft_basis_desc, dft_grid_desc, dft_info, dft_params,
     DFT_PREC_FP64, DFT_PREC_BF16X3, DFT_PREC_FP16X3, DFT_MODEL_LITERAL, DFT_MODEL_NEUTRAL, DFT_MIX_LINEAR, DFT_MIX_KERKER, DFT_MIX_PULAY,
-    DFT_XC_SLATER, DFT_XC_PW92, dft_nonlocal_matrix,
+    DFT_XC_SLATER, DFT_XC_PW92, dft_nonlocal_matrix, DFT_PRECOND_BLOCK_JACOBI, DFT_PRECOND_NONE, dft_columns_info,
     dft_workspace_bytes, dft_init_basis, dft_overlap_kinetic, dft_density_matrix, dft_density_on_grid,
     dft_potential_matrix, dft_hartree_xc, dft_scf_step, dft_initial_density, dft_destroy, dft_last_error,
     dft_version, dft_kernel_launches, dft_spectral_bounds_static, dft_scf_step_batched,
@@ -155,6 +155,22 @@ class Context:
         P = self.matrix()
         info = dft_density_matrix(self.ctx, self._mat(F, "F"), P, stream)
         return P, info
+
+    def density_matrix_columns(self, F, cols, mu, e_min, e_max, n_cheb, thresh=0.0,
+                               precond=B.DFT_PRECOND_BLOCK_JACOBI, pcg_tol=1e-10, pcg_maxit=2000, stream=None):
+        """P[:, cols] (K x len(cols)) by the sparse-operator route: the
+        Chebyshev recurrence on the unit columns with S^-1 by PCG on the
+        thresholded sparse S (see include/dft.h)."""
+        torch = self.torch
+        cols = [int(x) for x in np.asarray(cols).ravel()]
+        if not cols:
+            raise ValueError("cols is empty")
+        if any(x < 0 or x >= self.K for x in cols):
+            raise ValueError(f"column indices must lie in [0, {self.K})")
+        out = torch.empty((self.K, len(cols)), dtype=torch.float64, device=self.device)
+        info = B.dft_density_matrix_columns(self.ctx, self._mat(F, "F"), cols, mu, e_min, e_max, n_cheb, thresh,
+                                            precond, pcg_tol, pcg_maxit, out, stream)
+        return out, info
 
     def nonlocal_matrix(self, stream=None):
         """V^NL (K x K), formed by overlap_kinetic (zeros without projectors)."""

@@ -20,6 +20,7 @@ DFT_PREC_FP64, DFT_PREC_BF16X3, DFT_PREC_FP16X3 = 0, 1, 2
 DFT_MODEL_LITERAL, DFT_MODEL_NEUTRAL = 0, 1
 DFT_MIX_LINEAR, DFT_MIX_KERKER, DFT_MIX_PULAY = 0, 1, 2
 DFT_XC_SLATER, DFT_XC_PW92 = 0, 1
+DFT_PRECOND_BLOCK_JACOBI, DFT_PRECOND_NONE = 0, 1
 
 
 class dft_basis_desc(C.Structure):
@@ -58,6 +59,15 @@ class dft_info(C.Structure):
         return d
 
 
+class dft_columns_info(C.Structure):
+    _fields_ = [("nnz_s", C.c_longlong), ("nnz_f", C.c_longlong), ("pcg_solves", C.c_longlong),
+                ("pcg_iterations", C.c_longlong), ("max_rel_residual", C.c_double), ("not_converged", C.c_int),
+                ("block_cols", C.c_int), ("ms", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # (name, restype, argtypes) for every entry point of include/dft.h
 _P = C.c_void_p
 SIGNATURES = [
@@ -67,6 +77,9 @@ SIGNATURES = [
     ("dft_overlap_kinetic", C.c_int, [_P, _P, _P, _P]),
     ("dft_density_matrix", C.c_int, [_P, _P, _P, C.POINTER(dft_info), _P]),
     ("dft_nonlocal_matrix", C.c_int, [_P, _P, _P]),
+    ("dft_density_matrix_columns", C.c_int, [_P, _P, C.POINTER(C.c_int), C.c_int, C.c_double, C.c_double,
+                                             C.c_double, C.c_int, C.c_double, C.c_int, C.c_double, C.c_int, _P,
+                                             C.POINTER(dft_columns_info), _P]),
     ("dft_density_on_grid", C.c_int, [_P, _P, _P, _P]),
     ("dft_potential_matrix", C.c_int, [_P, _P, _P, _P]),
     ("dft_hartree_xc", C.c_int, [_P, _P, _P, C.POINTER(C.c_double), _P]),
@@ -155,6 +168,17 @@ def dft_nonlocal_matrix(ctx, VNL, stream=None):
 def dft_density_matrix(ctx, F, P, stream=None) -> dft_info:
     info = dft_info()
     _check(ctx, lib.dft_density_matrix(ctx, _ptr(F), _ptr(P), C.byref(info), _stream(stream)))
+    return info
+
+
+def dft_density_matrix_columns(ctx, F, cols, mu, e_min, e_max, n_cheb, thresh, precond, pcg_tol, pcg_maxit, out,
+                               stream=None) -> dft_columns_info:
+    info = dft_columns_info()
+    n = len(cols)
+    carr = (C.c_int * n)(*[int(x) for x in cols])
+    _check(ctx, lib.dft_density_matrix_columns(ctx, _ptr(F), carr, n, float(mu), float(e_min), float(e_max),
+                                               int(n_cheb), float(thresh), int(precond), float(pcg_tol),
+                                               int(pcg_maxit), _ptr(out), C.byref(info), _stream(stream)))
     return info
 
 

@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libdft.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
-SOURCES = ["api.cu", "k_grid.cu", "k_linalg.cu", "k_cheb.cu", "k_cheb_tc.cu", "k_congr_tc.cu", "k_nonlocal.cu", "k_poisson.cu", "k_warm.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "k_grid.cu", "k_linalg.cu", "k_cheb.cu", "k_cheb_tc.cu", "k_congr_tc.cu", "k_nonlocal.cu", "k_sparse.cu", "k_poisson.cu", "k_warm.cu", "noalloc.cu"]
 
 
 def nvcc():

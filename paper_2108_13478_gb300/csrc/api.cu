@@ -122,6 +122,7 @@ void build_basis(Ctx& c, const dft_basis_desc* b, const dft_grid_desc* g, const 
     c.p = *p;
     c.xyz_host.assign(b->xyz, b->xyz + 3 * b->n_atoms);
     c.fn_host.clear();
+    c.fn_atom_host.clear();
     c.term_ptr_host.assign(1, 0);
     int wmax = 1;
     // Every basis function (Eq. A.1) is a sum of Cartesian Gaussian terms,
@@ -171,6 +172,7 @@ void build_basis(Ctx& c, const dft_basis_desc* b, const dft_grid_desc* g, const 
                     c.fn_host.push_back(f);
                 }
             c.term_ptr_host.push_back((int)c.fn_host.size());
+            c.fn_atom_host.push_back(a);
         }
     }
     c.K = (int)c.term_ptr_host.size() - 1;
@@ -992,6 +994,31 @@ dft_status dft_overlap_kinetic(dft_ctx* ctx, double* S, double* T, void* stream)
         if (flags[FLAG_CHOL]) throw Error(DFT_ENOTCONV, "overlap matrix is not positive definite");
         if (flags[FLAG_RANGE]) throw Error(DFT_EINTERNAL, "L^-1 is outside the range of the FP16 pair");
         c.have_chol = true;
+    });
+}
+
+dft_status dft_density_matrix_columns(dft_ctx* ctx, const double* F, const int* cols, int ncols, double mu,
+                                      double e_min, double e_max, int n_cheb, double thresh, int precond,
+                                      double pcg_tol, int pcg_maxit, double* out, dft_columns_info* info,
+                                      void* stream) {
+    if (!ctx) return DFT_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+        if (c.K == 0 || !F || !cols || !out) throw Error(DFT_EINVAL, "null argument");
+        if (!c.have_chol) throw Error(DFT_EINVAL, "call dft_overlap_kinetic first");
+        if (ncols < 1) throw Error(DFT_EINVAL, "ncols must be positive");
+        for (int i = 0; i < ncols; ++i)
+            if (cols[i] < 0 || cols[i] >= c.K) throw Error(DFT_EINVAL, "column index outside [0, K)");
+        if (n_cheb < 2 || n_cheb > c.cheb_cap) throw Error(DFT_EINVAL, "n_cheb outside [2, Chebyshev capacity]");
+        if (!(e_max > e_min) || !std::isfinite(e_min) || !std::isfinite(e_max) || !std::isfinite(mu))
+            throw Error(DFT_EINVAL, "need finite mu and e_min < e_max");
+        if (!(thresh >= 0.0)) throw Error(DFT_EINVAL, "thresh must be >= 0");
+        if (!(pcg_tol > 0.0) || pcg_maxit < 1) throw Error(DFT_EINVAL, "need pcg_tol > 0 and pcg_maxit >= 1");
+        if (precond != DFT_PRECOND_BLOCK_JACOBI && precond != DFT_PRECOND_NONE)
+            throw Error(DFT_EINVAL, "unknown preconditioner");
+        require_aligned16({F, out});
+        sparse_columns(c, F, cols, ncols, mu, e_min, e_max, n_cheb, thresh, precond, pcg_tol, pcg_maxit, out, info,
+                       static_cast<cudaStream_t>(stream));
     });
 }
 

@@ -89,6 +89,7 @@ struct Ctx {
     double origin[3] = {0, 0, 0}, h = 0;
     dft_params p{};
     std::vector<Fn> fn_host;
+    std::vector<int> fn_atom_host;   // atom of each basis function [K]
     std::vector<double> xyz_host;
     // non-local KB projectors (Supp. A.2.2): one Fn record per projector,
     // their energies, and the width of their 1D tables
@@ -255,7 +256,11 @@ void launch_gaussian_sum(const Ctx& c, double amp, double width, double* out, cu
 // C[M x N] = alpha op(A) op(B) + beta C, row-major, op = 'N' or 'T'
 void dgemm(char ta, char tb, int M, int N, int Kd, double alpha, const double* A, int lda,
            const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s);
-int cholesky_inplace(double* A, int K, int* d_flag, cudaStream_t s);   // lower L, upper zeroed
+int cholesky_inplace(double* A, int K, int* d_flag, cudaStream_t s);
+// dft_density_matrix_columns: the sparse-operator route (k_sparse.cu)
+void sparse_columns(Ctx& c, const double* F, const int* cols, int ncols, double mu, double e_min, double e_max,
+                    int n_c, double thresh, int precond, double tol, int maxit, double* out,
+                    dft_columns_info* info, cudaStream_t s);   // lower L, upper zeroed
 void tri_inverse_lower(const double* L, double* Linv, int K, double* tmp, cudaStream_t s);  // tmp: K^2 doubles
 // out = Linv F Linv^T and out = Linv^T R Linv for lower-triangular Linv and
 // symmetric F, R (FP64, k ranges cut to the triangle, upper tiles mirrored)

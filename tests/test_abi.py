@@ -54,9 +54,10 @@ def test_struct_sizes_match_header(built):
 #include <stdio.h>
 #include <stddef.h>
 #include "dft.h"
-int main(){printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dft_basis_desc), sizeof(dft_grid_desc),
+int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dft_basis_desc), sizeof(dft_grid_desc),
  sizeof(dft_params), sizeof(dft_info), offsetof(dft_params, seed), offsetof(dft_info, ms_stage),
- offsetof(dft_params, kerker_q0) + offsetof(dft_params, mix_history) * 1000);return 0;}
+ offsetof(dft_params, kerker_q0) + offsetof(dft_params, mix_history) * 1000, sizeof(dft_columns_info),
+ offsetof(dft_columns_info, ms));return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
@@ -66,7 +67,8 @@ int main(){printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dft_basis_desc), sizeo
         out = [int(x) for x in subprocess.check_output([exe]).split()]
     got = [ctypes.sizeof(B.dft_basis_desc), ctypes.sizeof(B.dft_grid_desc), ctypes.sizeof(B.dft_params),
            ctypes.sizeof(B.dft_info), B.dft_params.seed.offset, B.dft_info.ms_stage.offset,
-           B.dft_params.kerker_q0.offset + B.dft_params.mix_history.offset * 1000]
+           B.dft_params.kerker_q0.offset + B.dft_params.mix_history.offset * 1000,
+           ctypes.sizeof(B.dft_columns_info), B.dft_columns_info.ms.offset]
     assert got == out
 
 
@@ -281,3 +283,30 @@ def test_static_bounds_refuse_buffers_the_kernels_cannot_read(built, monkeypatch
     assert called == []
     c.spectral_bounds_static(Mat((4, 4)))
     assert len(called) == 1
+
+
+def test_columns_call_checks_its_arguments(built, monkeypatch):
+    """dft_density_matrix_columns refuses a null context in the library, and
+    the Context method refuses out-of-range columns and a wrong-size F
+    before the library is called."""
+    import torch
+    import paper_2108_13478_gb300 as dft
+    from paper_2108_13478_gb300 import _binding as B
+    lib = ctypes.CDLL(built)
+    lib.dft_density_matrix_columns.restype = ctypes.c_int
+    cols = (ctypes.c_int * 1)(0)
+    st = lib.dft_density_matrix_columns(None, None, cols, 1, ctypes.c_double(0.0), ctypes.c_double(-1.0),
+                                        ctypes.c_double(1.0), 8, ctypes.c_double(0.0), 0, ctypes.c_double(1e-10),
+                                        100, None, None, None)
+    assert st == B.DFT_EINVAL
+    c = object.__new__(dft.Context)
+    c.torch, c.device, c.K, c.grid_shape, c.ctx = torch, torch.device("cpu"), 4, (2, 3, 5), None
+    calls = []
+    monkeypatch.setattr(B, "dft_density_matrix_columns", lambda *a: calls.append(a))
+    with pytest.raises(ValueError, match="column"):
+        c.density_matrix_columns(Dev(16), [0, 4], 0.0, -1.0, 1.0, 8)
+    with pytest.raises(ValueError, match="empty"):
+        c.density_matrix_columns(Dev(16), [], 0.0, -1.0, 1.0, 8)
+    with pytest.raises(ValueError):
+        c.density_matrix_columns(Dev(30), [0], 0.0, -1.0, 1.0, 8)
+    assert calls == []
