@@ -59,6 +59,8 @@ def parse():
                          "1e-6 for the mixed precisions)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sparse", action="store_true",
+                    help="skip the sparse-operator route's sub-record (dft_density_matrix_columns)")
     ap.add_argument("--no-reuse-mu", action="store_true",
                     help="mixed precisions: run the moments pass on every SCF cycle (default: skip it while mu "
                          "has settled)")
@@ -513,6 +515,43 @@ def compare_precisions(dft, torch, local, tail, name="cluster64", steps=2):
     return out
 
 
+def sparse_route(dft, torch, local, tail, sm_mhz, name="cluster64", ncols=32, thresh=1e-8):
+    """The sparse-operator route (dft_density_matrix_columns) on the 64-atom
+    cluster: one block of columns P u_alpha by the vector recurrence with
+    block-Jacobi PCG solves on S and F without their entries below 1e-8, at
+    the mu, bounds and N_C of the FP64 dense route on the same Fock matrix.
+    P-columns/s, solver work, the FP64 rate of the sparse products (the
+    route's arithmetic) and the largest difference from the dense route's
+    columns."""
+    import workloads as w
+    sysm = w.config_system(name)
+    ctx = dft.Context(sysm, device=f"cuda:{local}", precision=dft.DFT_PREC_FP64, cheb_tail_tol=tail,
+                      model=dft.DFT_MODEL_NEUTRAL)
+    _, T = ctx.overlap_kinetic()
+    v, _ = ctx.hartree_xc(ctx.initial_density())
+    F = (ctx.potential_matrix(v) + T).contiguous()
+    P, info = ctx.density_matrix(F)
+    K = ctx.K
+    cols = [int(x) for x in np.linspace(0, K - 1, ncols).round()]
+    out, ci = ctx.density_matrix_columns(F, cols, info.mu, info.e_min, info.e_max, info.n_cheb, thresh=thresh,
+                                         pcg_tol=1e-10)
+    torch.cuda.synchronize()
+    dev = float((out - P[:, cols]).abs().max() / P.abs().max())
+    t = ci.ms / 1000.0
+    # sparse products: S p in every PCG iteration of the slowest column, F U once per step
+    flops = 2.0 * ncols * (ci.nnz_s * ci.pcg_iterations + ci.nnz_f * (info.n_cheb - 1))
+    peak = FP64_FLOP_PER_SM_CLK * N_SM * sm_mhz * 1e6 / 1e12
+    ctx.close()
+    return {"workload": name, "n_basis": K, "columns": ncols, "n_cheb": info.n_cheb, "value": ncols / t,
+            "unit": "P-columns/s (dft_density_matrix_columns)", "ms": ci.ms, "precond": "block-Jacobi",
+            "thresh": thresh, "pcg_tol": 1e-10, "pcg_iterations": ci.pcg_iterations, "pcg_solves": ci.pcg_solves,
+            "iterations_per_solve": ci.pcg_iterations / max(1, ci.pcg_solves), "not_converged": ci.not_converged,
+            "nnz_s": ci.nnz_s, "nnz_f": ci.nnz_f, "max_rel_dev_from_dense": dev,
+            "roofline": {"kernel": "k_spmm", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
+                         "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak,
+                         "note": "whole-call time; FP64 issue rate 4 flop/SM/clk x 152 SMs x median SM clock"}}
+
+
 def run_reference_batch(args, rank):
     """Oracle on a bounded sample of a ragged batch: the bounded one-step
     sample (cpu_baseline) of 8 systems spread over the size range, scaled to
@@ -773,6 +812,8 @@ def main():
 
     if rank == 0 and not args.no_compare:
         line["mixed_vs_fp64"] = compare_precisions(dft, torch, local, cheb_tail(args))
+    if rank == 0 and not args.no_sparse:
+        line["sparse_route"] = sparse_route(dft, torch, local, cheb_tail(args), sm_mhz)
     if rank == 0 and prec != dft.DFT_PREC_FP64 and args.accuracy_workload != "none":
         del flush
         torch.cuda.empty_cache()

@@ -11,7 +11,13 @@ namespace dft {
 namespace {
 
 __device__ __forceinline__ double fermi(double e, double mu, double beta) {
-    return 0.5 * (1.0 - tanh(0.5 * beta * (e - mu)));
+    const double t = 0.5 * beta * (e - mu);
+    // beyond |t| = 40, 1 - |tanh t| < 1e-34: f is 0 or 1 in FP64, and the
+    // tanh (dozens of operations on GB300's narrow FP64 pipe) is skipped for
+    // the many nodes far from mu
+    if (t > 40.0) return 0.0;
+    if (t < -40.0) return 1.0;
+    return 0.5 * (1.0 - tanh(t));
 }
 
 // cos_tab[j] = cos(pi j / (2M)), j < 4M: cos(l th_k) with th_k = pi (k + 1/2) / M
@@ -32,24 +38,25 @@ __global__ void k_fermi_nodes(int M, const double* __restrict__ c, const double*
     fk[k] = fermi(eb + de * c[2 * k + 1], mu, beta);
 }
 
-// a_l = (2 - delta_l0)/M sum_k f_k cos(l th_k)  (DCT-II of the node values)
+// a_l = (2 - delta_l0)/M sum_k f_k cos(l th_k)  (DCT-II of the node values);
+// one warp per coefficient, lanes over the nodes (cos(l th_k) is
+// cos_tab[(l (2k+1)) mod 4M])
 __global__ void k_dct_coeffs(int n_c, int M, const double* __restrict__ c, const double* __restrict__ fk,
                              double* __restrict__ a) {
-    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (l >= n_c) return;
-    long long m4 = 4LL * M;
-    long long idx = l % m4;            // l (2k+1) at k = 0
-    long long step = (2LL * l) % m4;
-    double s0 = 0.0, s1 = 0.0;
-    int k = 0;
-    for (; k + 1 < M; k += 2) {
-        s0 = fma(fk[k], c[idx], s0);
-        idx += step; if (idx >= m4) idx -= m4;
-        s1 = fma(fk[k + 1], c[idx], s1);
-        idx += step; if (idx >= m4) idx -= m4;
+    const long long m4 = 4LL * M;
+    long long idx = ((long long)l * (2 * lane + 1)) % m4;
+    const long long step = (64LL * l) % m4;
+    double s = 0.0;
+    for (int k = lane; k < M; k += 32) {
+        s = fma(fk[k], c[idx], s);
+        idx += step;
+        if (idx >= m4) idx -= m4;
     }
-    if (k < M) s0 = fma(fk[k], c[idx], s0);
-    a[l] = (l == 0 ? 1.0 : 2.0) / M * (s0 + s1);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) a[l] = (l == 0 ? 1.0 : 2.0) / M * s;
 }
 
 // w_k = (1/M) sum_l (2 - delta_l0) m_l cos(l th_k): N(mu) = 2 sum_k f(x_k; mu) w_k
@@ -238,7 +245,7 @@ void launch_cheb_coeffs(int n_c, int M, const double* cos_tab, const double* sca
                         double mu_override, bool use_override, double* coef, cudaStream_t s) {
     double* fk = coef + n_c;
     k_fermi_nodes<<<blocks_for(M, 256), 256, 0, s>>>(M, cos_tab, scal, beta, mu_override, use_override ? 1 : 0, fk);
-    k_dct_coeffs<<<blocks_for(n_c, 128), 128, 0, s>>>(n_c, M, cos_tab, fk, coef);
+    k_dct_coeffs<<<blocks_for(32LL * n_c, 256), 256, 0, s>>>(n_c, M, cos_tab, fk, coef);
     check_launch("cheb_coeffs", 2);
 }
 

@@ -441,36 +441,43 @@ __device__ int sturm_count(const double* al, const double* be, int m, double x) 
     return cnt;
 }
 
-// extreme eigenvalues of the Lanczos tridiagonal by bisection; the bounds are
-// padded by 2% of the width on each side (the paper does not say how E_min and
-// E_max are found)
-__global__ void k_tridiag_bounds(int m, double* scal) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// extreme eigenvalues of the Lanczos tridiagonal by multisection on the
+// Sturm count: warp 0 seeks the smallest, warp 1 the largest; every round
+// each lane counts the eigenvalues below one of 32 interior points and the
+// bracket shrinks 33-fold to the two points around the sought one.  The
+// bounds are padded by 2% of the width on each side (the paper does not say
+// how E_min and E_max are found).
+__global__ void __launch_bounds__(64) k_tridiag_bounds(int m, double* scal) {
     const double* al = scal + SCAL_ALPHA;
     const double* be = scal + SCAL_BETA;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double lo = 1e300, hi = -1e300;
     for (int i = 0; i < m; ++i) {
         double r = (i > 0 ? fabs(be[i]) : 0.0) + (i + 1 < m ? fabs(be[i + 1]) : 0.0);
         lo = fmin(lo, al[i] - r);
         hi = fmax(hi, al[i] + r);
     }
+    // invariant: count(a) < target <= count(b)
+    const int target = w == 0 ? 1 : m;
     double a = lo, b = hi;
-    for (int it = 0; it < 200; ++it) {
-        double mid = 0.5 * (a + b);
-        if (mid <= a || mid >= b) break;
-        if (sturm_count(al, be, m, mid) >= 1) b = mid; else a = mid;
+    for (int it = 0; it < 64; ++it) {
+        const double x = a + (b - a) * (double)(lane + 1) / 33.0;
+        const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(al, be, m, x) >= target);
+        const int j = ge ? __ffs(ge) - 1 : 32;
+        const double na = j == 0 ? a : a + (b - a) * (double)j / 33.0;
+        const double nb = j == 32 ? b : a + (b - a) * (double)(j + 1) / 33.0;
+        if (!(na > a || nb < b)) break;   // the bracket is at FP64 resolution
+        a = na;
+        b = nb;
     }
-    double emin = 0.5 * (a + b);
-    a = lo; b = hi;
-    for (int it = 0; it < 200; ++it) {
-        double mid = 0.5 * (a + b);
-        if (mid <= a || mid >= b) break;
-        if (sturm_count(al, be, m, mid) >= m) b = mid; else a = mid;
+    __shared__ double e[2];
+    if (lane == 0) e[w] = 0.5 * (a + b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double pad = 0.02 * (e[1] - e[0]) + 1e-3;
+        scal[SCAL_EMIN] = e[0] - pad;
+        scal[SCAL_EMAX] = e[1] + pad;
     }
-    double emax = 0.5 * (a + b);
-    double pad = 0.02 * (emax - emin) + 1e-3;
-    scal[SCAL_EMIN] = emin - pad;
-    scal[SCAL_EMAX] = emax + pad;
 }
 
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -666,7 +673,7 @@ void lanczos_bounds(const Ctx& c, const double* A, int steps, cudaStream_t s) {
         k_lanczos_update<<<1, 1024, 0, s>>>(K, j, w, vj, vjm1, vn, c.d_scal);
         check_launch("lanczos_step", 2);
     }
-    k_tridiag_bounds<<<1, 32, 0, s>>>(m, c.d_scal);
+    k_tridiag_bounds<<<1, 64, 0, s>>>(m, c.d_scal);
     check_launch("lanczos");
 }
 
@@ -687,7 +694,7 @@ void lanczos_bounds_at(int K, const double* A, int steps, unsigned long long see
         k_lanczos_update<<<1, 1024, 0, s>>>(K, j, w, vj, vjm1, vn, scal);
         check_launch("lanczos_step", 2);
     }
-    k_tridiag_bounds<<<1, 32, 0, s>>>(m, scal);
+    k_tridiag_bounds<<<1, 64, 0, s>>>(m, scal);
     check_launch("lanczos");
 }
 

@@ -225,30 +225,49 @@ __global__ void k_kerker_weights(int nx, int ny, int nz, double h, double q0, do
 constexpr int PMAX = 16;   // Pulay history slots at most
 
 // One pass for the Pulay step (Section 2): x_slot = n_in, R_slot = n_out -
-// n_in, max|R_slot| and <R_i, R_slot> for the m filled slots (slot's own
+// n_in, max|R_slot| and <R_i, R_slot> for the M filled slots (slot's own
 // entry from the register), instead of a copy, a residual, a max and a dot
-// kernel over the same grids.  Block partials: PMAX dots, then the max.
-__global__ void __launch_bounds__(256) k_pulay_prepare(long long ng, int m, int slot, const double* __restrict__ n_in,
+// kernel over the same grids.  M is a template parameter so that only M
+// accumulators occupy registers, and two grid points per thread per pass
+// keep 2 (M + 1) loads in flight.  Block partials: PMAX dots, then the max.
+template <int M>
+__global__ void __launch_bounds__(256) k_pulay_prepare(long long ng, int slot, const double* __restrict__ n_in,
                                                        const double* __restrict__ n_out, double* __restrict__ xr,
                                                        double* __restrict__ rr, double* __restrict__ part) {
-    double acc[PMAX];
+    double acc[M];
 #pragma unroll
-    for (int i = 0; i < PMAX; ++i) acc[i] = 0.0;
+    for (int i = 0; i < M; ++i) acc[i] = 0.0;
     double mx = 0.0;
     double* xs = xr + (long long)slot * ng;
     double* rs = rr + (long long)slot * ng;
-    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < ng; e += (long long)gridDim.x * 256) {
-        const double a = n_in[e], r = n_out[e] - a;
-        xs[e] = a;
-        rs[e] = r;
-        mx = fmax(mx, fabs(r));
+    const long long stride = (long long)gridDim.x * 512;
+    for (long long e0 = (long long)blockIdx.x * 512 + threadIdx.x; e0 < ng; e0 += stride) {
+        const long long e1 = e0 + 256;
+        const bool two = e1 < ng;
+        const double a0 = n_in[e0], b0 = n_out[e0];
+        const double a1 = two ? n_in[e1] : 0.0, b1 = two ? n_out[e1] : 0.0;
+        double h0[M], h1[M];
 #pragma unroll
-        for (int i = 0; i < PMAX; ++i)
-            if (i < m) acc[i] = fma(i == slot ? r : rr[(long long)i * ng + e], r, acc[i]);
+        for (int i = 0; i < M; ++i) {
+            h0[i] = i == slot ? 0.0 : rr[(long long)i * ng + e0];
+            h1[i] = (i == slot || !two) ? 0.0 : rr[(long long)i * ng + e1];
+        }
+        const double r0 = b0 - a0, r1 = b1 - a1;
+        xs[e0] = a0;
+        rs[e0] = r0;
+        if (two) {
+            xs[e1] = a1;
+            rs[e1] = r1;
+        }
+        mx = fmax(mx, fmax(fabs(r0), fabs(r1)));
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const double p0 = i == slot ? r0 : h0[i], p1 = i == slot ? r1 : h1[i];
+            acc[i] = fma(p1, r1, fma(p0, r0, acc[i]));
+        }
     }
 #pragma unroll
-    for (int i = 0; i < PMAX; ++i) {
-        if (i >= m) break;
+    for (int i = 0; i < M; ++i) {
         const double v = block_sum<256>(acc[i]);
         if (threadIdx.x == 0) part[(long long)blockIdx.x * (PMAX + 1) + i] = v;
     }
@@ -261,6 +280,18 @@ __global__ void __launch_bounds__(256) k_pulay_prepare(long long ng, int m, int 
         for (int i = 0; i < 8; ++i) r = fmax(r, red[i]);
         part[(long long)blockIdx.x * (PMAX + 1) + PMAX] = r;
     }
+}
+
+template <int M>
+void launch_pulay_prepare_m(int np, long long ng, int m, int slot, const double* n_in, const double* n_out,
+                            double* xr, double* rr, double* part, cudaStream_t s) {
+    if constexpr (M > 1) {
+        if (m < M) {
+            launch_pulay_prepare_m<M - 1>(np, ng, m, slot, n_in, n_out, xr, rr, part, s);
+            return;
+        }
+    }
+    k_pulay_prepare<M><<<np, 256, 0, s>>>(ng, slot, n_in, n_out, xr, rr, part);
 }
 
 // dots[i] = sum over blocks (i < m), *mx = max over blocks
@@ -390,7 +421,8 @@ void pulay_prepare(Ctx& c, int m, int slot, const double* n_in, const double* n_
     int np = (int)std::min<long long>(592, (c.ng + 255) / 256);
     double* xr = c.d_pulay;
     double* rr = c.d_pulay + (size_t)c.pl_hist * c.ng;
-    k_pulay_prepare<<<np, 256, 0, s>>>(c.ng, m, slot, n_in, n_out, xr, rr, c.d_part);
+    if (m < 1 || m > PMAX) throw Error(DFT_EINTERNAL, "Pulay history outside 1 .. 16");
+    launch_pulay_prepare_m<PMAX>(np, c.ng, m, slot, n_in, n_out, xr, rr, c.d_part, s);
     k_pulay_prepare_reduce<<<1, 256, 0, s>>>(np, m, c.d_part, dots, mx);
     check_launch("pulay_prepare", 2);
 }

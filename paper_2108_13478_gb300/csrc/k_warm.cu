@@ -25,27 +25,25 @@ constexpr int OW1 = 0, OB1 = OW1 + NH * ND, OW2 = OB1 + NH, OB2 = OW2 + NH * NH,
 
 __device__ __forceinline__ double width(int k) { return 0.5 * pow(6.0, k / 15.0); }
 
-__global__ void k_descriptors(const double* __restrict__ xyz, int n, double* __restrict__ G) {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= n) return;
-    double g[ND];
-#pragma unroll
-    for (int k = 0; k < ND; ++k) g[k] = 0.0;
+// one block of ND threads per atom, thread k summing component k over the
+// neighbours (distances and the cutoff function in FP64, the Gaussians in
+// FP32: GB300's FP64 pipe makes an FP64 exp cost hundreds of FP32 ones)
+__global__ void __launch_bounds__(ND) k_descriptors(const double* __restrict__ xyz, int n, double* __restrict__ G) {
+    const int a = blockIdx.x, k = threadIdx.x;
     const double s = RC / 31.0;
+    const double mu_k = RC * k / 31.0;
+    const float inv2s2 = (float)(1.0 / (2.0 * s * s));
+    double g = 0.0;
     for (int b = 0; b < n; ++b) {
         if (b == a) continue;
         double dx = xyz[3 * b] - xyz[3 * a], dy = xyz[3 * b + 1] - xyz[3 * a + 1], dz = xyz[3 * b + 2] - xyz[3 * a + 2];
         double r = sqrt(dx * dx + dy * dy + dz * dz);
         if (r >= RC) continue;
-        double fc = 0.5 * (cos(M_PI * r / RC) + 1.0);
-#pragma unroll
-        for (int k = 0; k < ND; ++k) {
-            double t = r - RC * k / 31.0;
-            g[k] += exp(-t * t / (2.0 * s * s)) * fc;
-        }
+        double fc = 0.5 * (cospi(r / RC) + 1.0);
+        const float t = (float)(r - mu_k);
+        g = fma((double)expf(-t * t * inv2s2), fc, g);
     }
-#pragma unroll
-    for (int k = 0; k < ND; ++k) G[(long long)a * ND + k] = g[k];
+    G[(long long)a * ND + k] = g;
 }
 
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
@@ -100,14 +98,22 @@ __global__ void k_assemble(const double* __restrict__ xyz, int n, const double* 
         double wk = width(k);
         inv_w2[k] = 1.0 / (wk * wk);
     }
+    // per atom the 16 Gaussians in FP32 (exp on the FP32 units), the sum over
+    // atoms in FP64
+    float iw2[NO];
+#pragma unroll
+    for (int k = 0; k < NO; ++k) iw2[k] = (float)inv_w2[k];
     double s = 0.0;
     for (int a = 0; a < n; ++a) {
         double dx = x - xyz[3 * a], dy = y - xyz[3 * a + 1], dz = z - xyz[3 * a + 2];
         double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= RCUT * RCUT) continue;
         const double* c = coef + (long long)a * NO;
+        const float r2f = (float)r2;
+        float sa = 0.0f;
 #pragma unroll
-        for (int k = 0; k < NO; ++k) s += c[k] * exp(-r2 * inv_w2[k]);
+        for (int k = 0; k < NO; ++k) sa = fmaf((float)c[k], expf(-r2f * iw2[k]), sa);
+        s += (double)sa;
     }
     v0[g] = (v_start ? v_start[g] : 0.0) + s;
 }
@@ -155,8 +161,9 @@ __global__ void __launch_bounds__(256) k_assemble_adjoint(const double* __restri
         double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= RCUT * RCUT) continue;
         double rv = resid[((long long)iz * ny + iy) * nx + ix];
+        const float r2f = (float)r2;
 #pragma unroll
-        for (int k = 0; k < NO; ++k) acc[k] = fma(rv, exp(-r2 * inv_w2[k]), acc[k]);
+        for (int k = 0; k < NO; ++k) acc[k] = fma(rv, (double)expf(-r2f * (float)inv_w2[k]), acc[k]);
     }
     for (int k = 0; k < NO; ++k) {
         double v = block_sum<256>(acc[k]);
@@ -282,7 +289,7 @@ void warm_params(const void* state, float* out, cudaStream_t s) {
 
 // v0 = v_start + network correction for the context's atoms
 void warm_forward(Ctx& c, const void* state, const double* v_start, double* v0, bool keep, cudaStream_t s) {
-    k_descriptors<<<blocks_for(c.n_atoms, 128), 128, 0, s>>>(c.d_xyz, c.n_atoms, c.d_wdesc);
+    k_descriptors<<<c.n_atoms, ND, 0, s>>>(c.d_xyz, c.n_atoms, c.d_wdesc);
     k_mlp_forward<<<c.n_atoms, NH, 0, s>>>(c.d_wdesc, c.n_atoms, st_w16(const_cast<void*>(state)), c.d_wcoef,
                                            keep ? c.d_wz : nullptr);
     k_assemble<<<blocks_for(c.ng, 256), 256, 0, s>>>(c.d_xyz, c.n_atoms, c.d_wcoef, c.n[0], c.n[1], c.n[2],
