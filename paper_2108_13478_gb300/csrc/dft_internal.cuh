@@ -50,7 +50,7 @@ struct TcTile {
 };
 constexpr int TC_MAX_SYS = 64;
 constexpr int TC_SK_MAX_CTAS = 256;   // stream-K grid bound (one 128 KB partial-sum slot per CTA)
-constexpr int TC_MAPS_PER_SYS = 26;   // H, X (k-block 32 / 64), X 128-row, rho, spare, X mirror and slab boxes
+constexpr int TC_MAPS_PER_SYS = 32;   // H, X (k-block 32 / 64), X 128-row, rho, spare, X mirror and slab boxes, H, X (k-block 16)
 constexpr int TC_LISTS = 3;           // tile lists: 256-wide, 128-wide, 256-wide in block order (dataflow)
 
 // Dataflow pass: steps l0 .. l0 + nsteps - 1 in one persistent launch; X_l is
@@ -66,7 +66,7 @@ struct TcFlow {
 
 // launch configuration of the tensor-core step (chosen by the autotuner)
 struct TcCfg {
-    int bk = 32;        // k-block width: 32 or 64 (64 only with 256-wide tiles)
+    int bk = 32;        // k-block width: 32, 64 or 16 (64 and 16 only with 256-wide tiles)
     int persist = 0;    // 0: one CTA per tile; p > 0: p CTAs per SM, strided tile loop
     int bn = 256;       // output tile width: 256 (one CTA per SM) or 128 (two CTAs per SM)
     int streamk = 0;    // 1: cooperative grid, equal chunk ranges per CTA (256-wide tiles, one system)
@@ -160,8 +160,8 @@ struct Ctx {
     void* d_h16[2] = {nullptr, nullptr};   // H_N hi, lo  [Kp x Kp] 16-bit
     void* d_x16[4] = {nullptr, nullptr, nullptr, nullptr};  // X pairs (hi, lo) x 2
     float2* d_rho_tc = nullptr;  // [Kp x Kp] compensated FP32 pairs (hi + lo), upper triangle accumulated
-    CUtensorMap tm_h[2][2];      // host copies of this system's tensor maps,
-    CUtensorMap tm_x[2][4];      // per k-block variant (32 or 64 wide)
+    CUtensorMap tm_h[3][2];      // host copies of this system's tensor maps,
+    CUtensorMap tm_x[3][4];      // per k-block variant (32, 64 or 16 wide)
     CUtensorMap tm_xn[4];        // X maps with 128-row boxes (128-wide tiles, 32-wide k-blocks; epilogue slabs)
     CUtensorMap tm_rho;          // rho pairs as FP32, 32 x 128 boxes (16 pairs per row), 128-byte swizzle
     CUtensorMap tm_xm[4];        // X maps with 64 x 16 boxes, 128-byte swizzle (mirror of an epilogue slab)

@@ -54,18 +54,23 @@ namespace tc {
 constexpr int BM = 128;
 constexpr int CPT = 128;   // accumulator columns held by one epilogue thread
 // Launch variants.  256-wide tiles: k-blocks 32 wide (64-byte rows and
-// swizzle, 4 stages) or 64 wide (128-byte rows and swizzle, 2 stages), a
-// 192 KB operand ring, 512 tensor-memory columns, one CTA per SM.  128-wide
-// tiles: 32-wide k-blocks in a 3-stage 96 KB ring and 256 columns, so two
-// CTAs share an SM.  Chunks of 256 of K between promotions throughout.
+// swizzle, 4 stages of 48 KB), 64 wide (128-byte rows and swizzle, 2 stages
+// of 96 KB) or 16 wide (32-byte rows and swizzle, 9 stages of 24 KB: the
+// same bytes in flight, a stage reloaded 8 stages (1.6 us of MMAs) after its
+// use instead of 3; measured slower at K = 4650, 0.378 against 0.282 ms per
+// step, as twice the stages cost the MMA and producer threads more waits),
+// 512 tensor-memory columns, one CTA per SM.  128-wide tiles: 32-wide
+// k-blocks in a 3-stage 96 KB ring and 256 columns, so two CTAs share an SM.
+// Chunks of 256 of K are the unit of the dataflow counters throughout.
 template <int BK_, int BN_>
 struct Cfg {
     static_assert(BN_ == 256 || (BN_ == 128 && BK_ == 32), "unsupported tile shape");
+    static_assert(BK_ == 16 || BK_ == 32 || BK_ == 64, "unsupported k-block width");
     static constexpr int BK = BK_, BN = BN_;
     static constexpr int NEPI = BN_;                  // epilogue threads: 4 warps per 128 columns
     static constexpr int NTHREADS = 64 + NEPI;        // + producer warp + MMA warp
     static constexpr int MINB = BN_ == 128 ? 2 : 1;   // resident CTAs per SM
-    static constexpr int STAGES = BN_ == 128 ? 3 : (BK_ == 64 ? 2 : 4);
+    static constexpr int STAGES = BN_ == 128 ? 3 : (BK_ == 64 ? 2 : (BK_ == 32 ? 4 : 9));
     static constexpr int GK = 256 / BK_;
     // k-blocks per accumulator promotion: the tensor core's FP32 accumulation
     // leans towards zero by a fraction of an ulp per addition, so the partial
@@ -81,8 +86,10 @@ struct Cfg {
     static constexpr int A_BYTES = BM * BK_ * 2;
     static constexpr int B_BYTES = BN_ * BK_ * 2;
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-    // 256-wide tiles: two 16 KB mirror buffers of the off-diagonal epilogue
-    static constexpr int MIR_BYTES = BN_ == 256 ? 2 * 16384 : 0;
+    // 256-wide tiles: four 8 KB mirror buffers of the off-diagonal epilogue;
+    // with 16-wide k-blocks three of them sit in the ring stage of the tile's
+    // last k-block (idle during the epilogue) and only one outside the ring
+    static constexpr int MIR_BYTES = BN_ == 256 ? (BK_ == 16 ? 8192 : 4 * 8192) : 0;
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + MIR_BYTES + 1024 + 512;
     static constexpr int TMEM_COLS = 2 * BN_;         // two chunk accumulators
 };
@@ -329,8 +336,9 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
     uint64_t* ebar = epi_done + 1;    // [8] epilogue slab loads (off-diagonal tiles)
     uint32_t* tmem_slot = (uint32_t*)(ebar + 8);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    double* red = (double*)(mirbuf + C::MIR_BYTES + 256);   // 2 x 8 moment partials + 1 flag
-    static_assert((2 * STAGES + 14) * 8 + 8 <= 256, "barriers overlap the reduction slots");
+    double* red = (double*)(mirbuf + C::MIR_BYTES + 320);   // 2 x 8 moment partials + 1 flag
+    static_assert((2 * STAGES + 14) * 8 + 8 <= 320, "barriers overlap the reduction slots");
+    static_assert(320 + 17 * 8 <= 512, "reduction slots exceed the barrier area");
     // staged FP32 sums of a finished tile, over the operand ring
     static_assert(BM * BN * 4 <= STAGES * STAGE_BYTES, "staged tile does not fit the ring");
     static_assert(!PAIR || (BN == 256 && BK == 32), "paired tiles need 256-wide tiles and 32-wide k-blocks");
@@ -387,7 +395,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 const TcSys& S = sys[tl.sys];
                 const int l = cu.l, cur = cu.cur;
                 if (l >= S.lim) continue;
-                const CUtensorMap* mp = maps + TC_MAPS_PER_SYS * tl.sys + (BK == 64 ? 6 : 0);
+                const CUtensorMap* mp = maps + TC_MAPS_PER_SYS * tl.sys + (BK == 64 ? 6 : (BK == 16 ? 26 : 0));
                 // X operand maps: 256-row boxes beside the H maps, or the 128-row set
                 const CUtensorMap* mb = BN == 128 ? maps + TC_MAPS_PER_SYS * tl.sys + 12 : mp + 2;
                 const int m0 = tl.i * BM, n0 = tl.j * BN;
@@ -748,7 +756,12 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
 #pragma unroll 1
                 for (int sl = 0; sl < 8; ++sl) {
                     uint8_t* bf = slab_buf<STAGES, STAGE_BYTES>(smem, gend, 4 * half + (sl & 3));
-                    uint8_t* mb = mirbuf + (2 * half + (sl & 1)) * 8192;
+                    const int mi = 2 * half + (sl & 1);
+                    uint8_t* mb;
+                    if constexpr (BK == 16)
+                        mb = mi < 3 ? smem + (int)((gend + STAGES - 1) % STAGES) * STAGE_BYTES + mi * 8192 : mirbuf;
+                    else
+                        mb = mirbuf + mi * 8192;
                     uint8_t* mbt = mb + (r_loc >> 6) * 2048;
                     got_all &= mbar_wait(&ebar[4 * half + (sl & 3)], (uint32_t)((sl >> 2) & 1));
                     uint32_t av[16];
@@ -1252,8 +1265,8 @@ void tc_setup(Ctx& c) {
     // one 16-bit type for the bit patterns; BF16 maps are encoded as FLOAT16 of
     // the same width (TMA moves bytes; the MMA's instruction descriptor decides
     // how they are read)
-    for (int v = 0; v < 2; ++v) {
-        const int bk = v ? 64 : 32;
+    for (int v = 0; v < 3; ++v) {
+        const int bk = v == 0 ? 32 : (v == 1 ? 64 : 16);
         tc::make_map(&c.tm_h[v][0], c.d_h16[0], c.Kp, tc::BM, bk);
         tc::make_map(&c.tm_h[v][1], c.d_h16[1], c.Kp, tc::BM, bk);
         for (int q = 0; q < 4; ++q) tc::make_map(&c.tm_x[v][q], c.d_x16[q], c.Kp, 256, bk);
@@ -1271,6 +1284,8 @@ void tc_setup(Ctx& c) {
         attr(tc::k_cheb_step_tc<true, 32, 256>, tc::Cfg<32, 256>::SMEM_BYTES);
         attr(tc::k_cheb_step_tc<false, 64, 256>, tc::Cfg<64, 256>::SMEM_BYTES);
         attr(tc::k_cheb_step_tc<true, 64, 256>, tc::Cfg<64, 256>::SMEM_BYTES);
+        attr(tc::k_cheb_step_tc<false, 16, 256>, tc::Cfg<16, 256>::SMEM_BYTES);
+        attr(tc::k_cheb_step_tc<true, 16, 256>, tc::Cfg<16, 256>::SMEM_BYTES);
         attr(tc::k_cheb_step_tc<false, 32, 128>, tc::Cfg<32, 128>::SMEM_BYTES);
         attr(tc::k_cheb_step_tc<true, 32, 128>, tc::Cfg<32, 128>::SMEM_BYTES);
         attr(tc::k_cheb_step_tc<false, 32, 256, true>, tc::Cfg<32, 256>::SMEM_BYTES);
@@ -1347,10 +1362,11 @@ TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const i
         tab[q] = sys_entry(c, lim[q], mom_last[q]);
         b.macc[q] = c.d_macc;
         CUtensorMap* m = &maps[TC_MAPS_PER_SYS * (size_t)q];
-        for (int v = 0; v < 2; ++v) {
-            m[6 * v + 0] = c.tm_h[v][0];
-            m[6 * v + 1] = c.tm_h[v][1];
-            for (int k = 0; k < 4; ++k) m[6 * v + 2 + k] = c.tm_x[v][k];
+        for (int v = 0; v < 3; ++v) {
+            const int b0 = v == 2 ? 26 : 6 * v;   // k-block 32, 64, 16
+            m[b0 + 0] = c.tm_h[v][0];
+            m[b0 + 1] = c.tm_h[v][1];
+            for (int k = 0; k < 4; ++k) m[b0 + 2 + k] = c.tm_x[v][k];
         }
         for (int k = 0; k < 4; ++k) m[12 + k] = c.tm_xn[k];
         m[16] = c.tm_rho;
@@ -1479,6 +1495,9 @@ void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s) {
         if (b.cfg.bk == 64) {
             if (b.bf) go(tc::k_cheb_step_tc<true, 64, 256>, tc::Cfg<64, 256>{});
             else go(tc::k_cheb_step_tc<false, 64, 256>, tc::Cfg<64, 256>{});
+        } else if (b.cfg.bk == 16) {
+            if (b.bf) go(tc::k_cheb_step_tc<true, 16, 256>, tc::Cfg<16, 256>{});
+            else go(tc::k_cheb_step_tc<false, 16, 256>, tc::Cfg<16, 256>{});
         } else {
             if (b.bf) go(tc::k_cheb_step_tc<true, 32, 256>, tc::Cfg<32, 256>{});
             else go(tc::k_cheb_step_tc<false, 32, 256>, tc::Cfg<32, 256>{});
@@ -1499,6 +1518,9 @@ void tc_step_batch(const TcBatch& b, int l, int cur, int mode, cudaStream_t s) {
     } else if (b.cfg.bk == 64) {
         if (b.bf) go(tc::k_cheb_step_tc<true, 64, 256>, tc::Cfg<64, 256>{});
         else go(tc::k_cheb_step_tc<false, 64, 256>, tc::Cfg<64, 256>{});
+    } else if (b.cfg.bk == 16) {
+        if (b.bf) go(tc::k_cheb_step_tc<true, 16, 256>, tc::Cfg<16, 256>{});
+        else go(tc::k_cheb_step_tc<false, 16, 256>, tc::Cfg<16, 256>{});
     } else {
         if (b.bf) go(tc::k_cheb_step_tc<true, 32, 256>, tc::Cfg<32, 256>{});
         else go(tc::k_cheb_step_tc<false, 32, 256>, tc::Cfg<32, 256>{});
@@ -1578,6 +1600,9 @@ void tc_run_flow(const TcBatch& b, int l0, int nsteps, int cshift, int mode, cud
     if (b.cfg.bk == 64) {
         if (b.bf) go(tc::k_cheb_step_tc<true, 64, 256>, tc::Cfg<64, 256>{});
         else go(tc::k_cheb_step_tc<false, 64, 256>, tc::Cfg<64, 256>{});
+    } else if (b.cfg.bk == 16) {
+        if (b.bf) go(tc::k_cheb_step_tc<true, 16, 256>, tc::Cfg<16, 256>{});
+        else go(tc::k_cheb_step_tc<false, 16, 256>, tc::Cfg<16, 256>{});
     } else {
         if (b.bf) go(tc::k_cheb_step_tc<true, 32, 256>, tc::Cfg<32, 256>{});
         else go(tc::k_cheb_step_tc<false, 32, 256>, tc::Cfg<32, 256>{});
@@ -1666,7 +1691,7 @@ void tune_load() {
         if (n == 2) c.bn = 256;
         if (n < 4) c.streamk = 0;
         if (n < 5) c.flow = 0;
-        if (n >= 2 && (c.bk == 32 || c.bk == 64) && c.persist >= 0 && c.persist <= 2 &&
+        if (n >= 2 && (c.bk == 32 || c.bk == 64 || (c.bk == 16 && c.bn == 256)) && c.persist >= 0 && c.persist <= 2 &&
             (c.bn == 256 || (c.bn == 128 && c.bk == 32)) && (c.streamk == 0 || (c.streamk == 1 && c.bn == 256)) &&
             (c.flow == 0 || c.flow == 1 || (c.flow == 2 && c.bk == 32 && c.bn == 256)))
             g_tuned[line.substr(q0 + 1, q1 - q0 - 1)] = c;
@@ -1724,7 +1749,7 @@ static bool forced_shape(TcCfg& c) {
     if (n <= 6) f.flow = 0;
     if (f.pf < 0 || f.pf > 64 || f.epf < 0 || f.epf > 1 || f.flow < 0 || f.flow > 2) return false;
     if (f.flow == 2 && (f.bk != 32 || f.pf != 0 || f.epf != 0)) return false;
-    if (!((f.bk == 32 || f.bk == 64) && f.persist >= 0 && f.persist <= 2 &&
+    if (!((f.bk == 32 || f.bk == 64 || (f.bk == 16 && f.bn == 256)) && f.persist >= 0 && f.persist <= 2 &&
           (f.bn == 256 || (f.bn == 128 && f.bk == 32)) && (f.streamk == 0 || (f.streamk == 1 && f.bn == 256)) &&
           (f.flow == 0 || (f.bn == 256 && f.streamk == 0))))
         return false;

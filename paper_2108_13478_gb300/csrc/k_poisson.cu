@@ -418,7 +418,7 @@ void kerker_apply(Ctx& c, double* r, cudaStream_t s) {
 
 void pulay_prepare(Ctx& c, int m, int slot, const double* n_in, const double* n_out, double* dots, double* mx,
                    cudaStream_t s) {
-    int np = (int)std::min<long long>(592, (c.ng + 255) / 256);
+    int np = (int)std::min<long long>(1184, (c.ng + 511) / 512);   // 8 CTAs per SM, two points per thread per pass
     double* xr = c.d_pulay;
     double* rr = c.d_pulay + (size_t)c.pl_hist * c.ng;
     if (m < 1 || m > PMAX) throw Error(DFT_EINTERNAL, "Pulay history outside 1 .. 16");

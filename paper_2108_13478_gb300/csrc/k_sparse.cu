@@ -104,7 +104,11 @@ __global__ void __launch_bounds__(32 * ROWS) k_spmm(int K, int B, const int* __r
     const int c0 = blockIdx.y * 128;
     const bool live = row < K;
     const int beg = live ? ptr[row] : 0, end = live ? ptr[row + 1] : 0;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    // four nonzeros at a time: their X rows are loaded together (the rows
+    // come from L2, so the latency, not the FP64 pipe, sets the pace), and
+    // even and odd nonzeros feed two accumulator chains
+    const int nu = min(4, max(0, (B - c0 - lane + 31) / 32));   // this lane's live column slots
+    double acc[2][4] = {{0.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
     for (int p0 = beg; p0 < end; p0 += 32) {
         const int pp = p0 + lane;
         int jj = 0;
@@ -114,22 +118,35 @@ __global__ void __launch_bounds__(32 * ROWS) k_spmm(int K, int B, const int* __r
             vv = val[pp];
         }
         const int n = min(32, end - p0);
-        for (int t = 0; t < n; ++t) {
-            const int j = __shfl_sync(0xffffffffu, jj, t);
-            const double v = __shfl_sync(0xffffffffu, vv, t);
-            const double* xr = X + (size_t)j * B + c0 + lane;
+        for (int t = 0; t < n; t += 4) {
+            int j[4];
+            double v[4], x[4][4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (c0 + lane + 32 * u < B) acc[u] = fma(v, xr[32 * u], acc[u]);
+            for (int q = 0; q < 4; ++q) {
+                j[q] = __shfl_sync(0xffffffffu, jj, (t + q) & 31);
+                v[q] = __shfl_sync(0xffffffffu, vv, (t + q) & 31);
+                if (t + q >= n) v[q] = 0.0;   // past the row's end (j is a valid row, x is not loaded)
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double* xr = X + (size_t)j[q] * B + c0 + lane;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[q][u] = (u < nu && t + q < n) ? xr[32 * u] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[q & 1][u] = fma(v[q], x[q][u], acc[q & 1][u]);
         }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
+        acc[0][u] += acc[1][u];
         const int c = c0 + lane + 32 * u;
         double d = 0.0;
         if (live && c < B) {
-            Y[(size_t)row * B + c] = acc[u];
-            if (D) d = D[(size_t)row * B + c] * acc[u];
+            Y[(size_t)row * B + c] = acc[0][u];
+            if (D) d = D[(size_t)row * B + c] * acc[0][u];
         }
         red[w][lane + 32 * u] = d;
     }
@@ -152,13 +169,32 @@ struct Cols {
 
 enum { CS_INIT_B = 0, CS_INIT_RZ = 1, CS_ALPHA = 2, CS_CHECK = 3, CS_BETA = 4 };
 
-// sums of the per-block partials, column by column in block order, and the
-// solver's scalar step that uses them
-__global__ void k_colsum(int nblk, int B, const double* __restrict__ part, int mode, double tol2, Cols cs) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= B) return;
+// sums of the per-block partials of 32 columns per block: thread (x, y)
+// adds the partials of blocks y, y + 32, ... of column x (independent loads
+// in flight), then the 32 sums are added in order of y, so the result does
+// not depend on scheduling; then the solver's scalar step that uses them
+constexpr int CS_Y = 32;
+__global__ void __launch_bounds__(32 * CS_Y) k_colsum(int nblk, int B, const double* __restrict__ part, int mode,
+                                                      double tol2, Cols cs) {
+    __shared__ double red[CS_Y][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * B + c];
+    if (c < B) {
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        int b = threadIdx.y;
+        for (; b + 3 * CS_Y < nblk; b += 4 * CS_Y) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s4[u] += part[(size_t)(b + u * CS_Y) * B + c];
+        }
+        for (int u = 0; b < nblk; b += CS_Y, ++u) s4[u & 3] += part[(size_t)b * B + c];
+        s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+    }
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y != 0 || c >= B) return;
+    s = 0.0;
+#pragma unroll
+    for (int y = 0; y < CS_Y; ++y) s += red[y][threadIdx.x];
     switch (mode) {
     case CS_INIT_B:   // ||b||^2; a zero right-hand side is solved by x = 0
         cs.bn2[c] = s;
@@ -551,15 +587,15 @@ void sparse_columns(Ctx& c, const double* F, const int* cols, int ncols, double 
     const dim3 eb2(32, ROWS);
     auto iterations = [&](int Bb, cudaStream_t st) {
         const long long n = (long long)K * Bb;
-        const unsigned cb = nblocks(Bb, 128);
+        const unsigned cb = nblocks(Bb, 32);
         const dim3 gs(nrb, nblocks(Bb, 128));
         for (int it = 0; it < PCG_GRAPH; ++it) {
             k_spmm<<<gs, 32 * ROWS, 0, st>>>(K, Bb, mS.ptr, mS.idx, mS.val, p, q, p, part);
-            k_colsum<<<cb, 128, 0, st>>>(nrb, Bb, part, CS_ALPHA, tol2, cs);
+            k_colsum<<<cb, dim3(32, CS_Y), 0, st>>>(nrb, Bb, part, CS_ALPHA, tol2, cs);
             k_pcg_xr<<<nrb, eb2, 0, st>>>(K, Bb, cs.alpha, p, q, Xs, r, part);
-            k_colsum<<<cb, 128, 0, st>>>(nrb, Bb, part, CS_CHECK, tol2, cs);
+            k_colsum<<<cb, dim3(32, CS_Y), 0, st>>>(nrb, Bb, part, CS_CHECK, tol2, cs);
             k_pcg_precond<<<nrb, eb2, 0, st>>>(K, Bb, bj, r, z, part);
-            k_colsum<<<cb, 128, 0, st>>>(nrb, Bb, part, CS_BETA, tol2, cs);
+            k_colsum<<<cb, dim3(32, CS_Y), 0, st>>>(nrb, Bb, part, CS_BETA, tol2, cs);
             k_pcg_p<<<nblocks(n, 256), 256, 0, st>>>(n, Bb, cs.beta, z, p, 0);
             check_launch("pcg_iter", 7);
         }
@@ -592,11 +628,11 @@ void sparse_columns(Ctx& c, const double* F, const int* cols, int ncols, double 
     // S^-1 of the block in q (the right-hand sides) into Xs
     auto solve = [&](int Bb) {
         const long long n = (long long)K * Bb;
-        const unsigned cb = nblocks(Bb, 128);
+        const unsigned cb = nblocks(Bb, 32);
         k_pcg_init<<<nrb, eb2, 0, s>>>(K, Bb, q, Xs, r, part);
-        k_colsum<<<cb, 128, 0, s>>>(nrb, Bb, part, CS_INIT_B, tol2, cs);
+        k_colsum<<<cb, dim3(32, CS_Y), 0, s>>>(nrb, Bb, part, CS_INIT_B, tol2, cs);
         k_pcg_precond<<<nrb, eb2, 0, s>>>(K, Bb, bj, r, z, part);
-        k_colsum<<<cb, 128, 0, s>>>(nrb, Bb, part, CS_INIT_RZ, tol2, cs);
+        k_colsum<<<cb, dim3(32, CS_Y), 0, s>>>(nrb, Bb, part, CS_INIT_RZ, tol2, cs);
         k_pcg_p<<<nblocks(n, 256), 256, 0, s>>>(n, Bb, cs.beta, z, p, 1);
         check_launch("pcg_init", 5);
         capture(Bb);

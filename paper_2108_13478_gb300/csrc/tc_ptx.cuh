@@ -89,12 +89,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 
 // shared-memory matrix descriptor of a K-major operand whose rows are one
 // swizzle atom wide (ROW_BYTES): 8-row core groups 8 * ROW_BYTES apart;
-// layout type 2 = 128-byte swizzle, 4 = 64-byte swizzle
+// layout type 2 = 128-byte swizzle, 4 = 64-byte swizzle, 6 = 32-byte swizzle
 template <int ROW_BYTES>
 __device__ __forceinline__ uint64_t smem_desc(const void* p) {
+    static_assert(ROW_BYTES == 32 || ROW_BYTES == 64 || ROW_BYTES == 128, "unsupported swizzle width");
     uint64_t addr = (uint64_t)(smem_u32(p) & 0x3FFFF) >> 4;
     const uint64_t sbo = (uint64_t)(8 * ROW_BYTES) >> 4;
-    const uint64_t layout = ROW_BYTES == 128 ? 2ull : 4ull;
+    const uint64_t layout = ROW_BYTES == 128 ? 2ull : (ROW_BYTES == 64 ? 4ull : 6ull);
     return addr | (1ull << 16) | (sbo << 32) | (1ull << 46) | (layout << 61);
 }
 

@@ -86,7 +86,8 @@ def test_mixed_grid_kernels_fp32():
 
 
 SHAPES = ["32,0,256", "64,0,256", "32,1,256", "64,1,256", "32,0,128", "32,2,128", "32,0,256,1", "64,0,256,1",
-          "32,0,256,0,0,0,1", "64,0,256,0,0,0,1", "32,0,256,0,0,0,2"]
+          "32,0,256,0,0,0,1", "64,0,256,0,0,0,1", "32,0,256,0,0,0,2", "16,0,256", "16,0,256,1",
+          "16,0,256,0,0,0,1"]
 
 
 @pytest.mark.parametrize("name", ["tiny37", "cluster64"])
@@ -102,7 +103,9 @@ def test_mixed_launch_shapes(name, monkeypatch):
     consecutive steps at once, so almost every chunk load waits on the block
     counters of the step before and every epilogue on the readers of the
     block it overwrites.  The paired shape runs the two tiles of each
-    256 x 256 block on a two-CTA cluster that shares the X k-blocks."""
+    256 x 256 block on a two-CTA cluster that shares the X k-blocks; the
+    16-wide k-block shapes use a 9-stage ring with 32-byte swizzled operands
+    and keep three of their four mirror buffers inside the ring."""
     s, st, F, lo, hi, n_c, ref = case(name)
     Ps = []
     for shape in SHAPES:
