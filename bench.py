@@ -56,7 +56,7 @@ def parse():
                     help="density mixing (linear 0.3 diverges for the neutral model on the R = 25 sphere)")
     ap.add_argument("--cheb-tail", type=float, default=None,
                     help="tail tolerance that fixes the Chebyshev order N_C (default: 1e-10 for fp64, "
-                         "1e-6 for the mixed precisions)")
+                         "1e-5 for the mixed precisions)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sparse", action="store_true",
@@ -76,13 +76,15 @@ def parse():
 
 def cheb_tail(args):
     """Tail tolerance of the Chebyshev order: sum_{l >= N_C} |a_l| < tol.  The
-    FP64 path keeps 1e-10 (P to 1e-9).  The mixed path takes 1e-6: measured
-    with the oracle on the 64- and 465-atom workloads, its truncation error is
-    ~1e-10 Ha/atom, four orders below what the split-FP16 products already
-    cost (~4e-6 Ha/atom), for 40% fewer recurrence steps than 1e-10."""
+    FP64 path keeps 1e-10 (P to 1e-9).  The mixed path takes 1e-5: measured
+    with the oracle (truncated against exact Fermi-Dirac density matrix, same
+    padded bounds), the truncation error is 1.1e-8 Ha/atom on the 64-atom
+    cluster and 9e-10 on the 465-atom sphere, two orders below what the
+    split-FP16 products already cost (2-4e-6 Ha/atom), for 17% fewer
+    recurrence steps than 1e-6 and half those of 1e-10."""
     if args.cheb_tail is not None:
         return args.cheb_tail
-    return 1e-10 if args.precision == "fp64" else 1e-6
+    return 1e-10 if args.precision == "fp64" else 1e-5
 
 
 class ClockSampler:

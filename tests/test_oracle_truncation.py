@@ -3,8 +3,9 @@
 N_C is the smallest order whose coefficient tail sum_{l >= N_C} |a_l| is
 below a tolerance (Supp. B's expansion; the paper's own rule is
 N_C ~ 2 beta dE).  The FP64 path uses 1e-10 so that P matches to 1e-9; the
-mixed path's products already cost ~4e-6 Ha/atom, and at 1e-6 the truncation
-adds orders of magnitude less than that while the order drops by ~40%.  On
+mixed path's products already cost ~4e-6 Ha/atom, and at 1e-5 (the bench's
+default for the mixed path) or 1e-6 the truncation adds orders of magnitude
+less than that while the order drops by half or by 40%.  On
 the 64-atom cluster's first Fock matrix: the truncated density matrix of
 each tolerance (same padded bounds as the library: 2% of the width + 1e-3
 Ha each side) against the exact Fermi-Dirac one.
@@ -62,3 +63,11 @@ def test_truncation_error_falls_with_the_tolerance(cluster):
     e5 = max(_truncated(cluster, 1e-5)[1:])
     e6 = max(_truncated(cluster, 1e-6)[1:])
     assert e5 > e6 and e5 < 1e-6
+
+
+def test_bench_default_tolerance_stays_two_orders_below_the_arithmetic(cluster):
+    # 1e-5: 17% fewer steps than 1e-6, truncation ~1e-8 Ha/atom
+    n6 = _truncated(cluster, 1e-6)[0]
+    n5, k5, b5 = _truncated(cluster, 1e-5)
+    assert n5 < 0.85 * n6
+    assert k5 < 5e-8 and b5 < 5e-8
