@@ -147,11 +147,9 @@ def peaks():
 
 
 def tc_tiles(K, bm=128, bn=256):
-    """Output tiles of the tensor-core step's dataflow list: both 128-row
-    tiles of every 256 x 256 block on or above the diagonal (the last one may
-    be all padding)."""
-    nb = -(-K // bn)
-    return nb * (nb + 1)
+    """Output tiles of the tensor-core step that reach the upper triangle."""
+    mt, nt = -(-K // bm), -(-K // bn)
+    return sum(1 for i in range(mt) for j in range(nt) if j * bn + bn - 1 >= i * bm)
 
 
 def cpu_baseline(sysm, budget_s):

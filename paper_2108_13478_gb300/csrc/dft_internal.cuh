@@ -72,8 +72,7 @@ struct TcCfg {
     int streamk = 0;    // 1: cooperative grid, equal chunk ranges per CTA (256-wide tiles, one system)
     int pf = 0;         // L2 prefetch distance in k-blocks (0: none)
     int epf = 0;        // 1: prefetch the epilogue's rows into L2 before the last chunks
-    int flow = 0;       // 1: one cooperative launch per pass, tiles wait on block counters (256-wide tiles);
-                        // 2: the same as two-CTA clusters sharing each X k-block (32-wide k-blocks)
+    int flow = 0;       // 1: one cooperative launch per pass, tiles wait on block counters (256-wide tiles)
 };
 struct Ctx {
     // problem

@@ -294,22 +294,8 @@ __device__ bool wait_count(const int* c, int need, int* flags) {
 // store until every reader of the pair it overwrites has finished reading it
 // at step s - 1, and counts its own pair written (W) at the end.  Moment sums
 // go to fixed-point accumulators (integer adds: order-independent).
-//
-// PAIR (dataflow launch, 32-wide k-blocks, 256-wide tiles): the grid runs as
-// two-CTA clusters, and the dataflow list pairs the two 128-row tiles of a
-// 256 x 256 block at consecutive positions, so the CTAs of a cluster work on
-// the two tiles of one block together.  Both read the same X panel: each CTA
-// loads one 128-row half of every X k-block and multicasts it into both
-// CTAs' rings, which cuts the operand stream per SM from 48 to 32 KB per
-// k-block.  A ring stage is refilled only when the MMAs of both CTAs have
-// released it (each MMA issuer's commit arrives on both CTAs' empty
-// barrier), and the next tile's loads wait for both CTAs' epilogues (each
-// epilogue thread arrives on both CTAs' epi_done), since the partner's
-// multicast writes into this CTA's ring.  A cluster barrier at the start
-// (barrier initialisation) and at the end (no CTA exits while the other may
-// still write into its shared memory) brackets the kernel; every other wait
-// stays bounded.
-template <bool BF, int BKV, int BNV, bool PAIR = false>
+
+template <bool BF, int BKV, int BNV>
 __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) k_cheb_step_tc(const TcSys* __restrict__ sys,
                                                               const CUtensorMap* __restrict__ maps,
                                                               const TcTile* __restrict__ tiles, int ntiles, int l_arg,
@@ -341,10 +327,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
     static_assert(320 + 17 * 8 <= 512, "reduction slots exceed the barrier area");
     // staged FP32 sums of a finished tile, over the operand ring
     static_assert(BM * BN * 4 <= STAGES * STAGE_BYTES, "staged tile does not fit the ring");
-    static_assert(!PAIR || (BN == 256 && BK == 32), "paired tiles need 256-wide tiles and 32-wide k-blocks");
     float* Rs = (float*)smem;
-    // the other CTA of the cluster (paired launch)
-    const uint32_t peer = PAIR ? (cluster_ctarank() ^ 1u) : 0u;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool do_rho = (mode & 1) != 0, do_mom = (mode & 2) != 0;
@@ -352,14 +335,14 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], PAIR ? 2 : 1);
+            mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&accfull[a], 1);
             mbar_init(&accempty[a], NEPI);
         }
         mbar_init(drain, 1);
-        mbar_init(epi_done, PAIR ? 2 * NEPI : NEPI);
+        mbar_init(epi_done, NEPI);
         for (int b = 0; b < 8; ++b) mbar_init(&ebar[b], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -373,8 +356,6 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
     }
     tc_fence_before();
     __syncthreads();
-    // the partner's barriers are initialised before any multicast or remote arrival
-    if constexpr (PAIR) cluster_sync_all();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -460,17 +441,8 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                     mbar_expect_tx(&full[s], STAGE_BYTES);
                     tma_load_2d(sAh(s), mp + 0, kb * BK, m0, &full[s]);
                     tma_load_2d(sAl(s), mp + 1, kb * BK, m0, &full[s]);
-                    if constexpr (PAIR) {
-                        // this CTA's 128-row half of the shared X k-block, into both rings
-                        const uint32_t r = peer ^ 1u;
-                        const CUtensorMap* mh = maps + TC_MAPS_PER_SYS * tl.sys + 12;   // X pairs, 128-row boxes
-                        const int hb = (int)r * (B_BYTES / 2);
-                        tma_load_2d_mc(sBh(s) + hb, mh + 2 * cur, kb * BK, n0 + 128 * (int)r, &full[s], 3);
-                        tma_load_2d_mc(sBl(s) + hb, mh + 1 + 2 * cur, kb * BK, n0 + 128 * (int)r, &full[s], 3);
-                    } else {
-                        tma_load_2d(sBh(s), mb + 2 * cur, kb * BK, n0, &full[s]);
-                        tma_load_2d(sBl(s), mb + 1 + 2 * cur, kb * BK, n0, &full[s]);
-                    }
+                    tma_load_2d(sBh(s), mb + 2 * cur, kb * BK, n0, &full[s]);
+                    tma_load_2d(sBl(s), mb + 1 + 2 * cur, kb * BK, n0, &full[s]);
                 }
                 if (!sk && BN == 256 && (tl.i >> 1) != tl.j && !(do_rho && do_mom) && nchunk >= 2 && !*abort_flag) {
                     // the first slab of every epilogue buffer, each as soon as the
@@ -547,8 +519,7 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                             umma_f16(d, al + off, bh + off, idesc, 1u);
                             first = false;
                         }
-                        if constexpr (PAIR) umma_commit_mc(&empty[s], 3);
-                        else umma_commit(&empty[s]);
+                        umma_commit(&empty[s]);
                     }
                     umma_commit(&accfull[a]);
                     ++qg;
@@ -869,7 +840,6 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 if (*abort_flag) ok = false;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(epi_done);
-                if constexpr (PAIR) mbar_arrive_cluster(epi_done, peer);
             } else {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 {
@@ -1027,7 +997,6 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                 // next asynchronous writes)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(epi_done);
-                if constexpr (PAIR) mbar_arrive_cluster(epi_done, peer);
             }
             if (do_mom) {
                 double s_nn = (double)snn_h + (double)snn_l, s_nc = (double)snc_h + (double)snc_l;
@@ -1068,8 +1037,6 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
     }
     tc_fence_before();
     __syncthreads();
-    // no CTA leaves while its partner may still write into its shared memory
-    if constexpr (PAIR) cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -1288,8 +1255,6 @@ void tc_setup(Ctx& c) {
         attr(tc::k_cheb_step_tc<true, 16, 256>, tc::Cfg<16, 256>::SMEM_BYTES);
         attr(tc::k_cheb_step_tc<false, 32, 128>, tc::Cfg<32, 128>::SMEM_BYTES);
         attr(tc::k_cheb_step_tc<true, 32, 128>, tc::Cfg<32, 128>::SMEM_BYTES);
-        attr(tc::k_cheb_step_tc<false, 32, 256, true>, tc::Cfg<32, 256>::SMEM_BYTES);
-        attr(tc::k_cheb_step_tc<true, 32, 256, true>, tc::Cfg<32, 256>::SMEM_BYTES);
         attr_done = true;
     }
 }
@@ -1308,11 +1273,7 @@ TcSys sys_entry(const Ctx& c, int lim, int mom_last) {
     e.coef = c.d_coef;
     e.mom = c.d_mom;
     e.nb = c.Kp / 256;
-    // 128-row tiles of the dataflow list: every 256 x 256 block row holds
-    // two, the second of the last one possibly all padding (rows >= K, which
-    // it reads as zeros and does not store), so that the two tiles of a block
-    // always sit together at an even position (paired launch)
-    e.mt = c.Kp / tc::BM;
+    e.mt = (c.K + tc::BM - 1) / tc::BM;
     e.npair = e.nb * (e.nb + 1) / 2;
     e.cnt_off = 0;
     e.macc = c.d_macc;
@@ -1412,11 +1373,9 @@ TcBatch tc_batch(Ctx& leader, Ctx* const* sys, int nsys, const int* lim, const i
         b.tile_off[2] = (int)tiles.size();
         size_t longest = 0;
         for (auto& x : per) longest = std::max(longest, x.size() / 2);
-        // systems interleaved block by block (the two tiles of a block stay adjacent)
-        for (size_t t = 0; t < longest; t += 2)
+        for (size_t t = 0; t < longest; ++t)
             for (int q = 0; q < nsys; ++q)
-                for (size_t u = t; u < t + 2; ++u)
-                    if (u < per[q].size() / 2) tiles.push_back(TcTile{q, per[q][2 * u], per[q][2 * u + 1], (int)u});
+                if (t < per[q].size() / 2) tiles.push_back(TcTile{q, per[q][2 * t], per[q][2 * t + 1], (int)t});
         b.ntiles[2] = (int)tiles.size() - b.tile_off[2];
     }
     if ((int)tiles.size() > leader.tile_cap) throw Error(DFT_ENOMEM, "batch tile list exceeds the leader's capacity");
@@ -1544,40 +1503,6 @@ void tc_run_flow(const TcBatch& b, int l0, int nsteps, int cshift, int mode, cud
     // more than any tile makes, so it runs out (FLAG_TIMEOUT, DFT_ETIMEOUT)
     f.bias = std::getenv("DFT_TEST_EXPIRE_WAITS") ? 1 : 0;
     const TcTile* tiles = L.d_tiles + b.tile_off[2];
-    if (b.cfg.flow == 2 && b.cfg.bk == 32) {
-        // paired launch: two-CTA clusters over the (even) dataflow list, as
-        // many as can be resident together (cooperative)
-        auto gop = [&](auto kern) {
-            using C = tc::Cfg<32, 256>;
-            cudaLaunchConfig_t lc = {};
-            lc.blockDim = dim3(C::NTHREADS);
-            lc.dynamicSmemBytes = C::SMEM_BYTES;
-            lc.stream = s;
-            cudaLaunchAttribute at[2];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = 2;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            at[1].id = cudaLaunchAttributeCooperative;
-            at[1].val.cooperative = 1;
-            lc.attrs = at;
-            lc.numAttrs = 1;
-            lc.gridDim = dim3(2 * (unsigned)num_sms());
-            int ncl = 0;
-            DFT_CUDA_CHECK(cudaOccupancyMaxActiveClusters(&ncl, kern, &lc));
-            if (ncl < 1) throw Error(DFT_ECUDA, "no two-CTA cluster of the tensor-core step fits");
-            if (nt % 2 != 0) throw Error(DFT_EINTERNAL, "paired dataflow list of odd length");
-            lc.gridDim = dim3((unsigned)std::min<long long>(2LL * ncl, (long long)nt * nsteps));
-            lc.numAttrs = 2;
-            DFT_CUDA_CHECK(cudaLaunchKernelEx(&lc, kern, (const TcSys*)L.d_systab, (const CUtensorMap*)L.d_maps, tiles,
-                                              nt, l0, 0, mode, L.d_part, L.d_flags, (const int*)nullptr, 0LL,
-                                              (float*)nullptr, (int*)nullptr, 0, 0, f));
-        };
-        if (b.bf) gop(tc::k_cheb_step_tc<true, 32, 256, true>);
-        else gop(tc::k_cheb_step_tc<false, 32, 256, true>);
-        check_launch("cheb_step_tc", 1);
-        return;
-    }
     auto go = [&](auto kern, auto cfg) {
         using C = decltype(cfg);
         int occ = 0;
@@ -1693,7 +1618,7 @@ void tune_load() {
         if (n < 5) c.flow = 0;
         if (n >= 2 && (c.bk == 32 || c.bk == 64 || (c.bk == 16 && c.bn == 256)) && c.persist >= 0 && c.persist <= 2 &&
             (c.bn == 256 || (c.bn == 128 && c.bk == 32)) && (c.streamk == 0 || (c.streamk == 1 && c.bn == 256)) &&
-            (c.flow == 0 || c.flow == 1 || (c.flow == 2 && c.bk == 32 && c.bn == 256)))
+            (c.flow == 0 || c.flow == 1))
             g_tuned[line.substr(q0 + 1, q1 - q0 - 1)] = c;
     }
 }
@@ -1747,8 +1672,7 @@ static bool forced_shape(TcCfg& c) {
     if (n <= 4) f.pf = 0;
     if (n <= 5) f.epf = TcCfg{}.epf;
     if (n <= 6) f.flow = 0;
-    if (f.pf < 0 || f.pf > 64 || f.epf < 0 || f.epf > 1 || f.flow < 0 || f.flow > 2) return false;
-    if (f.flow == 2 && (f.bk != 32 || f.pf != 0 || f.epf != 0)) return false;
+    if (f.pf < 0 || f.pf > 64 || f.epf < 0 || f.epf > 1 || f.flow < 0 || f.flow > 1) return false;
     if (!((f.bk == 32 || f.bk == 64 || (f.bk == 16 && f.bn == 256)) && f.persist >= 0 && f.persist <= 2 &&
           (f.bn == 256 || (f.bn == 128 && f.bk == 32)) && (f.streamk == 0 || (f.streamk == 1 && f.bn == 256)) &&
           (f.flow == 0 || (f.bn == 256 && f.streamk == 0))))
