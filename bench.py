@@ -804,6 +804,10 @@ def main():
             "mu_reused_steps": int(sum(i.mu_reused for i in infos)),
             "energy_per_atom": infos[-1].e_total / sysm.n_atoms}
     shape = tuned_shape()
+    if prec != dft.DFT_PREC_FP64:
+        # which source of the tensor-core step this line measured (and the key of
+        # its DRAM traffic record)
+        line["roofline"]["kernel_source_sha16"] = kernel_sha16()
     if shape is not None and prec != dft.DFT_PREC_FP64:
         line["roofline"]["launch_shape"] = shape
         shapes = {(v.get("flow", 0), v.get("bk", 32)) for v in shape.values()}
