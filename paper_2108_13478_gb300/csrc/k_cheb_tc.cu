@@ -147,6 +147,18 @@ __device__ __forceinline__ int rs_swz(int lr) { return ((lr ^ (lr >> 2)) & 7) <<
 // running their own loops)
 template <int N>
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
+// the same barrier, returning whether any of the N threads passed true
+template <int N>
+__device__ __forceinline__ bool epi_sync_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(N)
+        : "memory");
+    return r != 0;
+}
 
 // The pieces of work of one CTA.  Tile mode: whole tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...  Stream-K mode (one system, cooperative grid):
@@ -836,8 +848,10 @@ __global__ void __launch_bounds__(Cfg<BKV, BNV>::NTHREADS, Cfg<BKV, BNV>::MINB) 
                     if (!war_ok) *abort_flag = 1;
                 }
                 if (!got_all) atomicExch(&flags[FLAG_TIMEOUT], 1);
-                epi_sync<NEPI>();
-                if (*abort_flag) ok = false;
+                // one decision for all epilogue warps: flag reads apart from the
+                // barrier could differ (another role may set the flag between
+                // them) and send some warps on to the next tile's barriers alone
+                if (epi_sync_or<NEPI>(*abort_flag != 0)) ok = false;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(epi_done);
             } else {
