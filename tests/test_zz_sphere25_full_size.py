@@ -115,14 +115,16 @@ def test_density_matrix(sphere, ctx):
 
 @pytest.mark.parametrize("skip", [0, 1])
 def test_density_matrix_at_the_benchmark_order(sphere, skip):
-    """The benchmark runs the mixed path with the Chebyshev tail 1e-6 (about
-    40% fewer steps than 1e-10; the oracle puts its truncation error near
-    1e-10 Ha/atom here): the same gates hold, with the FP64 electron-count
-    correction after the recurrence (skip = 0, the default) and without it."""
+    """The benchmark runs the mixed path with the Chebyshev tail 1e-5 (about
+    half the steps of 1e-10; the oracle's truncated expansion against its
+    exact eigensolve gives 9e-10 Ha/atom here, and the K = 640 case is
+    pinned in tests/test_oracle_truncation.py): the same gates hold, with
+    the FP64 electron-count correction after the recurrence (skip = 0, the
+    default) and without it."""
     s, ex, F, T = sphere["s"], sphere["ex"], sphere["F"], sphere["T"]
     mp = pytest.MonkeyPatch()
     mp.setenv("DFT_TC_SHAPE", FLOW)
-    c = dft.Context(s, precision=dft.DFT_PREC_FP16X3, model=dft.DFT_MODEL_NEUTRAL, cheb_tail_tol=1e-6,
+    c = dft.Context(s, precision=dft.DFT_PREC_FP16X3, model=dft.DFT_MODEL_NEUTRAL, cheb_tail_tol=1e-5,
                     skip_correction=skip)
     try:
         c.overlap_kinetic()
@@ -136,7 +138,7 @@ def test_density_matrix_at_the_benchmark_order(sphere, skip):
     e_kin = abs(2 * np.sum(dP * T)) / s.n_atoms
     e_band = abs(2 * np.sum(dP * F)) / s.n_atoms
     n_e = 2 * np.sum(P * sphere["S"])
-    print(f"sphere25 fp16x3 tail 1e-6 {'without' if skip else 'with'} correction: N_C {info.n_cheb}  "
+    print(f"sphere25 fp16x3 tail 1e-5 {'without' if skip else 'with'} correction: N_C {info.n_cheb}  "
           f"max|dP| {err:.3e}  dEkin/atom {e_kin:.3e}  dEband/atom {e_band:.3e}  2Tr[PS] {n_e:.6f}  "
           f"dmu {info.mu_correction:+.3e}  stages {[round(x, 1) for x in info.ms_stage]}")
     assert info.spectrum_ok == 1
