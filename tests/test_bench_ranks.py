@@ -105,3 +105,36 @@ def test_chebyshev_tail_defaults():
     assert bench.cheb_tail(ns("fp64")) == 1e-10
     assert bench.cheb_tail(ns("fp16x3")) == 1e-5 and bench.cheb_tail(ns("bf16x3")) == 1e-5
     assert bench.cheb_tail(ns("fp16x3", 1e-8)) == 1e-8
+
+
+def test_clock_samples_summarised():
+    """The clock record of the bench line from nvidia-smi's CSV rows (index,
+    clocks.sm, clocks.max.sm, power.draw, active-reasons mask, then the
+    hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown and sw_power_cap
+    flags): median SM clock under load, the maximum clock, and every reason
+    seen Active in any sample; short or non-numeric rows are skipped."""
+    rows = ["0, 2070, 2070, 1180.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 1995, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 1950, 2070, 1398.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, [N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage"]
+    c = bench.ClockSampler.summarise(rows)
+    assert c == {"sm_mhz": 1995.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = bench.ClockSampler.summarise(["0, 1500, 2070, 900, 0x8, Not Active, Active, Not Active, Not Active"])
+    assert hot["reasons"] == ["hw_thermal_slowdown"] and hot["sm_mhz"] == 1500.0
+    assert bench.ClockSampler.summarise([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_upper_triangle_tile_count():
+    """Tiles of the tensor-core step: 128 x 256 output tiles that reach the
+    upper triangle, counted against a brute-force scan of their elements."""
+    import numpy as np
+    for K in (80, 370, 640, 1000):
+        mt, nt = -(-K // 128), -(-K // 256)
+        brute = 0
+        for i in range(mt):
+            for j in range(nt):
+                r = np.arange(i * 128, i * 128 + 128)[:, None]
+                c = np.arange(j * 256, j * 256 + 256)[None, :]
+                brute += bool(np.any(c >= r))
+        assert bench.tc_tiles(K) == brute
