@@ -523,6 +523,8 @@ void sparse_columns(Ctx& c, const double* F, const int* cols, int ncols, double 
         int* d_bjidx = (int*)take(sizeof(int) * K);
         long long* d_bjoff = (long long*)take(sizeof(long long) * nbj);
         double* d_inv = (double*)take(sizeof(double) * inv_len);
+        // before the first copy into the scratch (checked again below, with the column state)
+        if (used > K2 * sizeof(double)) throw Error(DFT_EINVAL, "basis too small for the sparse-operator scratch");
         DFT_CUDA_CHECK(cudaMemcpyAsync(d_fnblk, fn_blk.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
         DFT_CUDA_CHECK(cudaMemcpyAsync(d_fnpos, fn_pos.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
         DFT_CUDA_CHECK(cudaMemcpyAsync(d_bjptr, blk_ptr.data(), sizeof(int) * (nbj + 1), cudaMemcpyHostToDevice, s));
