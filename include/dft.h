@@ -263,9 +263,10 @@ typedef struct dft_columns_info {
  *   info     host, may be NULL
  * The call uses the context's K x K work matrices as scratch (a later
  * dft_density_matrix or dft_scf_step recomputes what it needs) and works on
- * blocks of at most min(K / 4, 1024) columns.  DFT_EINVAL for bad arguments
- * or before dft_overlap_kinetic; DFT_ENOTCONV if an atom's block of S is not
- * positive definite.  Columns still above pcg_tol after pcg_maxit
+ * blocks of at most min(K / 4, 1024) columns.  DFT_EINVAL for bad arguments,
+ * before dft_overlap_kinetic, or for K > 46340 (the CSR offsets are 32-bit
+ * and a dense K x K would overflow them); DFT_ENOTCONV if an atom's block of
+ * S is not positive definite.  Columns still above pcg_tol after pcg_maxit
  * iterations are reported in info->not_converged, not as an error. */
 dft_status dft_density_matrix_columns(dft_ctx* ctx, const double* F, const int* cols, int ncols, double mu,
                                       double e_min, double e_max, int n_cheb, double thresh, int precond,

@@ -1006,6 +1006,8 @@ dft_status dft_density_matrix_columns(dft_ctx* ctx, const double* F, const int* 
         Ctx& c = *reinterpret_cast<Ctx*>(ctx);
         if (c.K == 0 || !F || !cols || !out) throw Error(DFT_EINVAL, "null argument");
         if (!c.have_chol) throw Error(DFT_EINVAL, "call dft_overlap_kinetic first");
+        // 32-bit CSR row offsets: at most K^2 kept entries must stay below 2^31
+        if ((long long)c.K * c.K > 2147483647LL) throw Error(DFT_EINVAL, "K too large for 32-bit CSR offsets");
         if (ncols < 1) throw Error(DFT_EINVAL, "ncols must be positive");
         for (int i = 0; i < ncols; ++i)
             if (cols[i] < 0 || cols[i] >= c.K) throw Error(DFT_EINVAL, "column index outside [0, K)");
