@@ -167,8 +167,9 @@ class Context:
             raise ValueError("cols is empty")
         if any(x < 0 or x >= self.K for x in cols):
             raise ValueError(f"column indices must lie in [0, {self.K})")
+        F = self._mat(F, "F").reshape(self.K, self.K)
         out = torch.empty((self.K, len(cols)), dtype=torch.float64, device=self.device)
-        info = B.dft_density_matrix_columns(self.ctx, self._mat(F, "F"), cols, mu, e_min, e_max, n_cheb, thresh,
+        info = B.dft_density_matrix_columns(self.ctx, F, cols, mu, e_min, e_max, n_cheb, thresh,
                                             precond, pcg_tol, pcg_maxit, out, stream)
         return out, info
 

@@ -171,10 +171,31 @@ def dft_density_matrix(ctx, F, P, stream=None) -> dft_info:
     return info
 
 
+def _square_f64(F, name):
+    import torch
+    if not getattr(F, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if F.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64, not {F.dtype}")
+    if F.dim() != 2 or F.shape[0] != F.shape[1]:
+        raise ValueError(f"{name} must be a square matrix")
+    if not F.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
 def dft_density_matrix_columns(ctx, F, cols, mu, e_min, e_max, n_cheb, thresh, precond, pcg_tol, pcg_maxit, out,
                                stream=None) -> dft_columns_info:
-    info = dft_columns_info()
+    """The kernels read K x K doubles from F's pointer and write K x len(cols)
+    doubles to out's: both must be contiguous float64 CUDA tensors of those
+    sizes (Context.density_matrix_columns also checks that F is K x K)."""
+    import torch
+    _square_f64(F, "F")
     n = len(cols)
+    if not getattr(out, "is_cuda", False) or out.dtype != torch.float64 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 CUDA tensor")
+    if out.numel() != F.shape[0] * n:
+        raise ValueError(f"out has {out.numel()} elements, expected {F.shape[0]} x {n}")
+    info = dft_columns_info()
     carr = (C.c_int * n)(*[int(x) for x in cols])
     _check(ctx, lib.dft_density_matrix_columns(ctx, _ptr(F), carr, n, float(mu), float(e_min), float(e_max),
                                                int(n_cheb), float(thresh), int(precond), float(pcg_tol),
@@ -286,15 +307,7 @@ def dft_spectral_bounds_static(ctx, F, stream=None):
     (K <= 768); returns (E_min, E_max).  F must be a contiguous square
     float64 CUDA matrix (Context.spectral_bounds_static also checks that it
     is K x K): the kernels read K x K doubles from its pointer."""
-    import torch
-    if not getattr(F, "is_cuda", False):
-        raise ValueError("F must be a CUDA tensor")
-    if F.dtype != torch.float64:
-        raise ValueError(f"F must be float64, not {F.dtype}")
-    if F.dim() != 2 or F.shape[0] != F.shape[1]:
-        raise ValueError("F must be a square matrix")
-    if not F.is_contiguous():
-        raise ValueError("F must be contiguous")
+    _square_f64(F, "F")
     b = (C.c_double * 2)()
     _check(ctx, lib.dft_spectral_bounds_static(ctx, _ptr(F), b, _stream(stream)))
     return b[0], b[1]

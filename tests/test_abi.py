@@ -310,3 +310,39 @@ def test_columns_call_checks_its_arguments(built, monkeypatch):
     with pytest.raises(ValueError):
         c.density_matrix_columns(Dev(30), [0], 0.0, -1.0, 1.0, 8)
     assert calls == []
+
+
+def test_columns_binding_refuses_buffers_the_kernels_cannot_use(built, monkeypatch):
+    """The low-level column-route binding reads K x K doubles from F and
+    writes K x len(cols) doubles to out: host, non-float64, non-square or
+    non-contiguous F, and an out of the wrong type or size, are refused
+    before the library is called."""
+    import torch
+    from paper_2108_13478_gb300 import _binding as B
+
+    class Mat(Dev):
+        def __init__(self, shape, dtype=None, contiguous=True):
+            super().__init__(int(np.prod(shape)), dtype, contiguous)
+            self.shape = shape
+
+        def dim(self):
+            return len(self.shape)
+
+    called = []
+    monkeypatch.setattr(B, "lib", types.SimpleNamespace(
+        dft_density_matrix_columns=lambda *a: called.append(a) or 0, dft_last_error=lambda c: b""))
+    monkeypatch.setattr(B, "_stream", lambda s=None: None)
+    monkeypatch.setattr(B, "_ptr", lambda t: None)
+    args = (0.0, -1.0, 1.0, 8, 0.0, B.DFT_PRECOND_BLOCK_JACOBI, 1e-10, 100)
+    good_F, good_out = Mat((4, 4)), Mat((4, 2))
+    for F, out, msg in ((torch.zeros((4, 4), dtype=torch.float64), good_out, "CUDA"),
+                        (Mat((4, 4), torch.float32), good_out, "float64"),
+                        (Mat((4, 5)), good_out, "square"),
+                        (Mat((4, 4), contiguous=False), good_out, "contiguous"),
+                        (good_F, Mat((4, 2), torch.float32), "out must be"),
+                        (good_F, Mat((4, 3)), "elements")):
+        with pytest.raises(ValueError, match=msg):
+            B.dft_density_matrix_columns(None, F, [0, 3], *args, out)
+    assert called == []
+    B.dft_density_matrix_columns(None, good_F, [0, 3], *args, good_out)
+    assert len(called) == 1
